@@ -1,0 +1,173 @@
+/*
+ * peers.h -- C ABI of the B300 library for exact effective resistance by the implicit-inverse
+ * query sweep (PEERS, arXiv 2606.31535).
+ *
+ * Problem (PEERS §II-A, eq. 1-4; §IV-A, eq. 15-18).  For an undirected graph G = (V, E, w)
+ * with positive conductances, L_G = D - W is its Laplacian (eq. 1).  Grounding a node g and
+ * deleting its row and column gives the SPD reduced Laplacian L_r.  The effective resistance
+ * of a pair (s, t) is R_st = (e_s - e_t)^T L_r^{-1} (e_s - e_t) (eq. 2, eq. 15), with the unit
+ * vector of g dropped when an endpoint is g (eq. 4).  The library factors L_r = L D L^T (unit
+ * lower L; the paper's eq. 3 writes the equivalent L L^T) and returns
+ *     R_st = sum_k y_k^2 / d_k,   L y = e_s - e_t          (eq. 16-18),
+ * walking for each query only the elimination-tree path(s) on which y is non-zero (Lemma 1),
+ * never forming L^{-1}.
+ *
+ * Call sequence: peers_create -> peers_analyze (host) -> peers_factor (device) ->
+ * peers_query (device sweep) -> peers_free_* / peers_destroy.
+ *
+ * Conventions shared by all calls:
+ *   - Every function returns PEERS_OK (0) or a negative PEERS_E* status; peers_strerror()
+ *     names it.  On error no output handle is created and *out is set to NULL.
+ *   - Callers own every array they pass in; the library copies what it keeps.  Handles are
+ *     owned by the library until freed with their peers_free_* / peers_destroy call.
+ *   - Device work is issued on the context's CUDA stream; calls return after that work has
+ *     finished unless stated otherwise.
+ *   - One context per host thread; handles may be shared read-only between contexts on the
+ *     same device.
+ */
+#ifndef PEERS_H
+#define PEERS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define PEERS_OK 0
+#define PEERS_EINVAL (-1)        /* malformed input: asymmetric CSR, self-loop, duplicate edge,
+                                    w <= 0 or not finite, index out of range, bad argument */
+#define PEERS_ENOTCONNECTED (-2) /* the graph is not connected (L_r would be singular) */
+#define PEERS_ENOTSPD (-3)       /* a pivot d_k <= 0 or not finite during the factorization */
+#define PEERS_ENOMEM (-4)        /* host or device allocation failed */
+#define PEERS_ECUDA (-5)         /* a CUDA runtime call failed (device lost, bad stream, ...) */
+#define PEERS_ETIMEOUT (-6)      /* a bounded device-side wait ran out */
+#define PEERS_ENOTREADY (-7)     /* result not available yet (non-blocking calls) */
+
+/* ---- flags ----------------------------------------------------------------------------- */
+#define PEERS_OUT_DEVICE 1  /* peers_query: R is a device pointer (else a host pointer) */
+
+typedef struct peers_ctx peers_ctx;           /* device + CUDA stream + scratch */
+typedef struct peers_symbolic peers_symbolic; /* host plan: ordering, etree, supernodes,
+                                                 query grouping (no device memory) */
+typedef struct peers_numeric peers_numeric;   /* device-resident L panels, D, plan copy */
+
+/* Options of peers_analyze.  Zero-initialise and set what you need; NULL means defaults. */
+typedef struct peers_options {
+  int32_t ordering;     /* 0 = auto (coordinate nested dissection when coords are given,
+                           else BFS level-structure nested dissection); 1 = coordinate ND;
+                           2 = BFS ND; 3 = natural order (tests only) */
+  int32_t nd_leaf;      /* nested-dissection leaf size (0 = default 32) */
+  int32_t relax_small;  /* amalgamate supernodes up to this many columns (0 = default 8) */
+  int32_t relax_max;    /* amalgamate up to this many columns when extra zeros <= relax_frac
+                           (0 = default 32) */
+  double relax_frac;    /* tolerated fraction of explicit zeros in an amalgamated supernode
+                           (0 = default 0.15) */
+  int64_t reserved[8];
+} peers_options;
+
+/* Statistics of an analysis (all counts exact). */
+typedef struct peers_info {
+  int64_t n;              /* graph nodes */
+  int64_t n_reduced;      /* n - 1 (ground removed) */
+  int64_t nnz_a;          /* strictly-lower entries of L_r */
+  int64_t nnz_l;          /* stored entries of the supernodal L incl. diagonal and
+                             explicit zeros: sum over supernodes of (n_c+n_b)*n_c */
+  int64_t nsuper;         /* supernodes */
+  int64_t levels;         /* supernodal etree height + 1 (one sweep launch per level) */
+  int64_t max_nc, max_nb; /* largest supernode width and below-diagonal row count */
+  int64_t nq;             /* queries */
+  int64_t nq_trivial;     /* queries with u == v (R = 0, no work) */
+  int64_t nq_two_branch;  /* listed pairs whose two etree paths merge above the start */
+  int64_t walk_entries;   /* W = sum_q sum_{s on path(q)} (n'(n'-1)/2 + n_b n' + n'), the
+                             per-query walk's factor entries (n' = columns of s at or after
+                             the query's first non-zero); bytes streamed = 8 W */
+  int64_t walk_fma;       /* FMAs the sweep kernels execute (block-aligned; >= useful work) */
+  int64_t factor_fma;     /* FMAs of the numeric factorization (dense blocks) */
+  int64_t device_bytes;   /* device memory of peers_factor + peers_query (footprint) */
+  double t_order, t_symbolic, t_queries; /* host seconds of the analysis phases */
+} peers_info;
+
+/* ---- context --------------------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to issue all
+ * work on (the caller keeps ownership), or NULL for a library-owned non-blocking stream.
+ * Errors: PEERS_EINVAL (no such device), PEERS_ECUDA. */
+int peers_create(peers_ctx **out, int device, void *cuda_stream);
+void peers_destroy(peers_ctx *ctx);
+
+/* ---- analysis (host only; PEERS Alg. 8 step 1: ground, fill-reducing order, structure) -- */
+
+/* Builds the plan for graph (n nodes; symmetric CSR indptr[n+1] int64, indices[nnz] int32,
+ * w[nnz] conductance of each stored entry, both directions equal) grounded at node `ground`,
+ * for the queries (qu[i], qv[i]), i < nq.  nq < 0 or qu == NULL selects all edges, in the
+ * order "u ascending, then each CSR neighbour v > u in CSR order".  `coords` (n x dim, row
+ * major, may be NULL) only guides the ordering.  `ctx` may be NULL: no device is touched.
+ * Queries with u == v give R = 0; a query touching the ground follows eq. 4.
+ * Errors: PEERS_EINVAL, PEERS_ENOTCONNECTED, PEERS_ENOMEM. */
+int peers_analyze(peers_ctx *ctx, int64_t n, const int64_t *indptr, const int32_t *indices,
+                  const double *w, int32_t ground, int64_t nq, const int32_t *qu,
+                  const int32_t *qv, const double *coords, int dim, const peers_options *opt,
+                  peers_symbolic **out);
+int peers_symbolic_info(const peers_symbolic *sym, peers_info *info);
+/* Number of queries of the plan (the length of R in peers_query). */
+int64_t peers_num_queries(const peers_symbolic *sym);
+/* Device bytes that peers_factor + peers_query will hold for this plan. */
+int64_t peers_footprint_bytes(const peers_symbolic *sym);
+void peers_free_symbolic(peers_symbolic *sym);
+
+/* Structure export for tests (host arrays sized by peers_info):
+ *   perm[n_reduced]      graph node (ground excluded) eliminated k-th
+ *   sn_first[nsuper+1]   first column of each supernode (columns are contiguous)
+ *   sn_parent[nsuper]    parent supernode (-1 for a root)
+ *   sn_nb[nsuper]        below-diagonal row count n_b
+ *   sn_level[nsuper]     height above the leaves
+ * Any pointer may be NULL. */
+int peers_symbolic_export(const peers_symbolic *sym, int32_t *perm, int32_t *sn_first,
+                          int32_t *sn_parent, int32_t *sn_nb, int32_t *sn_level);
+
+/* ---- numeric factorization (device) ------------------------------------------------------ */
+
+/* Numeric supernodal L D L^T of the grounded Laplacian on the context's device (multifrontal,
+ * one level of the supernodal etree at a time).  `w` (same layout as in peers_analyze, may be
+ * NULL) replaces the conductances for a refactorization on the same pattern; NULL reuses the
+ * ones given to peers_analyze.  The result stays resident in device memory.
+ * Errors: PEERS_ENOTSPD, PEERS_ENOMEM, PEERS_ECUDA, PEERS_EINVAL. */
+int peers_factor(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peers_numeric **out);
+/* Copies the diagonal D (n_reduced entries, elimination order) to host memory. */
+int peers_numeric_diag(peers_ctx *ctx, const peers_numeric *num, double *d_host);
+void peers_free_numeric(peers_numeric *num);
+
+/* ---- the sweep (device) ------------------------------------------------------------------ */
+
+/* Effective resistance of every query of the plan into R[0 .. peers_num_queries(sym)), in the
+ * plan's query order.  R is a device pointer when flags has PEERS_OUT_DEVICE, else a host
+ * pointer.  One launch per level of the supernodal etree walks every query from its starting
+ * supernode to the root (eq. 16-18 over the etree path of Lemma 1).
+ * Errors: PEERS_EINVAL, PEERS_ENOMEM, PEERS_ECUDA. */
+int peers_query(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num, double *R,
+                int flags);
+
+/* Device seconds of the last peers_query / peers_factor on this context, split per kernel
+ * class: out[0] = sweep total, out[1] = largest single sweep launch, out[2] = factor total.
+ * Filled only when timing was enabled with peers_set_timing(ctx, 1). */
+int peers_set_timing(peers_ctx *ctx, int enable);
+int peers_last_timing(const peers_ctx *ctx, double out[3]);
+
+/* Device milliseconds of each sweep launch (one per etree level) of the last timed
+ * peers_query, summed over waves, into ms[0 .. min(levels, cap)).  Returns the level count or
+ * a negative status. */
+int peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap);
+
+/* ---- misc ------------------------------------------------------------------------------- */
+const char *peers_strerror(int status);
+/* Message of the last failed call on this host thread ("" if none). */
+const char *peers_last_error(void);
+/* Library version string. */
+const char *peers_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEERS_H */

@@ -1,0 +1,852 @@
+// Host analysis of the PEERS library: validation, grounding, fill-reducing ordering,
+// elimination tree, supernodes, factorization schedule and query grouping.
+//
+// Paper correspondence (PEERS, arXiv 2606.31535):
+//   - grounding and the reduced Laplacian: §II-A (eq. 1, and the text after it), §IV-A;
+//   - fill-reducing ordering (the paper uses AMD in Alg. 8 step 1 and nested dissection in
+//     its analysis, Def. 1-2, Lemma 2): nested dissection here, by coordinates or by BFS
+//     level structures;
+//   - elimination tree (Lemma 1: y = L^{-1} b is non-zero only on etree paths);
+//   - query graph (§III-G): each query is mapped to its permuted endpoints and grouped by the
+//     supernode where its etree path starts.
+// Everything here is integer work on the CPU; no device is touched.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace peers {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+double since(Clock::time_point t0) {
+  return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+// ------------------------------------------------------------------------- validation
+
+int validate(int64_t n, const int64_t *indptr, const int32_t *indices, const double *w,
+             int32_t ground, std::string &err) {
+  if (n < 2) { err = "a graph needs at least two nodes"; return PEERS_EINVAL; }
+  if (n > INT32_MAX - 1) { err = "more than 2^31-2 nodes"; return PEERS_EINVAL; }
+  if (!indptr || !indices || !w) { err = "null graph array"; return PEERS_EINVAL; }
+  if (ground < 0 || ground >= n) { err = "ground node out of range"; return PEERS_EINVAL; }
+  if (indptr[0] != 0) { err = "indptr[0] must be 0"; return PEERS_EINVAL; }
+  for (int64_t i = 0; i < n; ++i)
+    if (indptr[i + 1] < indptr[i]) { err = "indptr is not non-decreasing"; return PEERS_EINVAL; }
+  const int64_t nnz = indptr[n];
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
+      int64_t j = indices[p];
+      if (j < 0 || j >= n) { err = "column index out of range"; return PEERS_EINVAL; }
+      if (j == i) { err = "self-loop at node " + std::to_string(i); return PEERS_EINVAL; }
+      if (!(w[p] > 0.0) || !std::isfinite(w[p])) {
+        err = "conductance must be positive and finite (entry " + std::to_string(p) + ")";
+        return PEERS_EINVAL;
+      }
+    }
+  }
+  // per-row sorted copies for duplicate and symmetry checks
+  std::vector<std::pair<int32_t, double>> srt(static_cast<size_t>(nnz));
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) srt[p] = {indices[p], w[p]};
+    std::sort(srt.begin() + indptr[i], srt.begin() + indptr[i + 1]);
+    for (int64_t p = indptr[i] + 1; p < indptr[i + 1]; ++p)
+      if (srt[p].first == srt[p - 1].first) {
+        err = "duplicate edge in row " + std::to_string(i);
+        return PEERS_EINVAL;
+      }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
+      const int32_t j = srt[p].first;
+      auto b = srt.begin() + indptr[j], e = srt.begin() + indptr[j + 1];
+      auto it = std::lower_bound(b, e, std::make_pair(static_cast<int32_t>(i), -1.0));
+      if (it == e || it->first != i) { err = "CSR is not symmetric"; return PEERS_EINVAL; }
+      if (it->second != srt[p].second) {
+        err = "conductances of (u,v) and (v,u) differ";
+        return PEERS_EINVAL;
+      }
+    }
+  }
+  // connectivity (the reduced Laplacian is SPD exactly when G is connected)
+  std::vector<int32_t> queue(static_cast<size_t>(n));
+  std::vector<char> seen(static_cast<size_t>(n), 0);
+  int64_t head = 0, tail = 0;
+  queue[tail++] = 0;
+  seen[0] = 1;
+  while (head < tail) {
+    int32_t v = queue[head++];
+    for (int64_t p = indptr[v]; p < indptr[v + 1]; ++p)
+      if (!seen[indices[p]]) { seen[indices[p]] = 1; queue[tail++] = indices[p]; }
+  }
+  if (tail != n) { err = "graph is not connected"; return PEERS_ENOTCONNECTED; }
+  return PEERS_OK;
+}
+
+// Adjacency of the reduced graph (ground removed, no diagonal), reduced numbering.
+struct Adj {
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> idx;
+};
+
+Adj reduced_adjacency(int64_t n, const int64_t *indptr, const int32_t *indices, int32_t g) {
+  Adj A;
+  const int64_t nr = n - 1;
+  A.ptr.assign(static_cast<size_t>(nr + 1), 0);
+  for (int64_t i = 0; i < n; ++i) {
+    if (i == g) continue;
+    int64_t c = 0;
+    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) c += indices[p] != g;
+    A.ptr[(i > g ? i - 1 : i) + 1] = c;
+  }
+  for (int64_t r = 0; r < nr; ++r) A.ptr[r + 1] += A.ptr[r];
+  A.idx.resize(static_cast<size_t>(A.ptr[nr]));
+  for (int64_t i = 0; i < n; ++i) {
+    if (i == g) continue;
+    int64_t q = A.ptr[i > g ? i - 1 : i];
+    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
+      int32_t j = indices[p];
+      if (j != g) A.idx[q++] = j > g ? j - 1 : j;
+    }
+  }
+  return A;
+}
+
+// ------------------------------------------------------------------------- orderings
+//
+// Both nested-dissection variants order in place: the task [lo, hi) of `work` is rewritten
+// as [part A | part B | separator] and A and B become new tasks; the separator stays last
+// (it is eliminated after both halves, the structure behind Def. 1 / Lemma 2).
+
+struct NdTask { int64_t lo, hi; };
+
+// Coordinate bisection: split at the median of the widest axis; the separator is the set of
+// upper-side nodes with a lower-side neighbour.
+void order_coordinate_nd(const Adj &A, const double *xy, int dim, int leaf,
+                         std::vector<int32_t> &work) {
+  const int64_t nr = static_cast<int64_t>(A.ptr.size()) - 1;
+  work.resize(static_cast<size_t>(nr));
+  std::iota(work.begin(), work.end(), 0);
+  std::vector<int8_t> side(static_cast<size_t>(nr), -1);
+  std::vector<std::pair<double, int32_t>> keys;
+  std::vector<int32_t> tmp;
+  std::vector<NdTask> stack{{0, nr}};
+  while (!stack.empty()) {
+    NdTask t = stack.back();
+    stack.pop_back();
+    const int64_t cnt = t.hi - t.lo;
+    if (cnt <= leaf) continue;
+    int axis = -1;
+    double width = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      double mn = INFINITY, mx = -INFINITY;
+      for (int64_t i = t.lo; i < t.hi; ++i) {
+        double c = xy[static_cast<int64_t>(work[i]) * dim + a];
+        mn = std::min(mn, c);
+        mx = std::max(mx, c);
+      }
+      if (mx - mn > width) { width = mx - mn; axis = a; }
+    }
+    if (axis < 0) continue;   // all nodes coincide: keep as one block
+    keys.resize(static_cast<size_t>(cnt));
+    for (int64_t i = 0; i < cnt; ++i)
+      keys[i] = {xy[static_cast<int64_t>(work[t.lo + i]) * dim + axis], work[t.lo + i]};
+    std::nth_element(keys.begin(), keys.begin() + cnt / 2, keys.end());
+    const double pivot = keys[cnt / 2].first;
+    int64_t nlow = 0;
+    for (auto &k : keys) nlow += k.first < pivot;
+    const bool strict = nlow > 0;
+    for (auto &k : keys) side[k.second] = (strict ? k.first < pivot : k.first <= pivot) ? 0 : 1;
+    int64_t na = 0, nbu = 0, ns = 0;
+    for (int64_t i = t.lo; i < t.hi; ++i) {
+      int32_t v = work[i];
+      if (side[v] == 1) {
+        for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p)
+          if (side[A.idx[p]] == 0) { side[v] = 2; break; }
+      }
+    }
+    for (int64_t i = t.lo; i < t.hi; ++i) {
+      int s = side[work[i]];
+      na += s == 0;
+      nbu += s == 1;
+      ns += s == 2;
+    }
+    if (na == 0 || nbu == 0) {   // no proper split
+      for (int64_t i = t.lo; i < t.hi; ++i) side[work[i]] = -1;
+      continue;
+    }
+    tmp.assign(work.begin() + t.lo, work.begin() + t.hi);
+    int64_t a = t.lo, b = t.lo + na, c = t.lo + na + nbu;
+    for (int32_t v : tmp) {
+      int s = side[v];
+      (s == 0 ? work[a++] : s == 1 ? work[b++] : work[c++]) = v;
+      side[v] = -1;
+    }
+    stack.push_back({t.lo + na, t.lo + na + nbu});
+    stack.push_back({t.lo, t.lo + na});
+  }
+}
+
+// BFS level-structure bisection for graphs without coordinates: from a pseudo-peripheral
+// node, the level that splits the node count in half is the separator.  Disconnected task
+// sets are split into their components first.
+void order_bfs_nd(const Adj &A, int leaf, std::vector<int32_t> &work) {
+  const int64_t nr = static_cast<int64_t>(A.ptr.size()) - 1;
+  work.resize(static_cast<size_t>(nr));
+  std::iota(work.begin(), work.end(), 0);
+  std::vector<int64_t> stamp(static_cast<size_t>(nr), -1);
+  std::vector<int32_t> lev(static_cast<size_t>(nr), -1);
+  std::vector<int32_t> q(static_cast<size_t>(nr)), tmp;
+  int64_t cur = 0;
+  auto bfs = [&](int32_t src, int64_t st, int64_t &count) -> int32_t {
+    // BFS within nodes stamped st; returns the last node reached, fills lev[]
+    int64_t head = 0, tail = 0;
+    q[tail++] = src;
+    lev[src] = 0;
+    stamp[src] = st + 1;   // visited marker: st + 1
+    while (head < tail) {
+      int32_t v = q[head++];
+      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+        int32_t u = A.idx[p];
+        if (stamp[u] == st) { stamp[u] = st + 1; lev[u] = lev[v] + 1; q[tail++] = u; }
+      }
+    }
+    count = tail;
+    for (int64_t i = 0; i < tail; ++i) stamp[q[i]] = st;   // unvisit
+    return q[tail - 1];
+  };
+  std::vector<NdTask> stack{{0, nr}};
+  while (!stack.empty()) {
+    NdTask t = stack.back();
+    stack.pop_back();
+    const int64_t cnt = t.hi - t.lo;
+    if (cnt <= leaf) continue;
+    const int64_t st = cur;
+    cur += 2;
+    for (int64_t i = t.lo; i < t.hi; ++i) stamp[work[i]] = st;
+    int64_t reached = 0;
+    int32_t far = bfs(work[t.lo], st, reached);
+    if (reached < cnt) {   // split off the component of work[lo]
+      tmp.assign(work.begin() + t.lo, work.begin() + t.hi);
+      for (int64_t i = 0; i < reached; ++i) stamp[q[i]] = st + 1;
+      int64_t a = t.lo, b = t.lo + reached;
+      for (int32_t v : tmp) (stamp[v] == st + 1 ? work[a++] : work[b++]) = v;
+      for (int32_t v : tmp) stamp[v] = -1;
+      stack.push_back({t.lo + reached, t.hi});
+      stack.push_back({t.lo, t.lo + reached});
+      continue;
+    }
+    int32_t ecc = lev[far];
+    for (int it = 0; it < 3; ++it) {   // pseudo-peripheral node
+      int32_t nf = bfs(far, st, reached);
+      if (lev[nf] <= ecc) break;
+      ecc = lev[nf];
+      far = nf;
+    }
+    bfs(far, st, reached);
+    ecc = 0;
+    for (int64_t i = t.lo; i < t.hi; ++i) ecc = std::max(ecc, lev[work[i]]);
+    std::vector<int64_t> per(static_cast<size_t>(ecc + 2), 0);
+    for (int64_t i = t.lo; i < t.hi; ++i) per[lev[work[i]]]++;
+    int32_t k = 0;
+    int64_t acc = 0;
+    for (; k <= ecc; ++k) {
+      acc += per[k];
+      if (2 * acc >= cnt) break;
+    }
+    int64_t na = 0, nbu = 0;
+    for (int64_t i = t.lo; i < t.hi; ++i) {
+      int32_t l = lev[work[i]];
+      na += l < k;
+      nbu += l > k;
+    }
+    if (na == 0 || nbu == 0) {
+      for (int64_t i = t.lo; i < t.hi; ++i) stamp[work[i]] = -1;
+      continue;
+    }
+    tmp.assign(work.begin() + t.lo, work.begin() + t.hi);
+    int64_t a = t.lo, b = t.lo + na, c = t.lo + na + nbu;
+    for (int32_t v : tmp) {
+      int32_t l = lev[v];
+      (l < k ? work[a++] : l > k ? work[b++] : work[c++]) = v;
+      stamp[v] = -1;
+    }
+    stack.push_back({t.lo + na, t.lo + na + nbu});
+    stack.push_back({t.lo, t.lo + na});
+  }
+}
+
+// ------------------------------------------------------------------------- etree
+
+// Elimination tree of the permuted pattern by Liu's ancestor path compression.
+void etree(const Adj &A, const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm,
+           std::vector<int32_t> &parent) {
+  const int64_t nr = static_cast<int64_t>(perm.size());
+  parent.assign(static_cast<size_t>(nr), -1);
+  std::vector<int32_t> anc(static_cast<size_t>(nr), -1);
+  for (int64_t k = 0; k < nr; ++k) {
+    const int32_t v = perm[k];
+    for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+      int32_t i = iperm[A.idx[p]];
+      while (i != -1 && i < k) {
+        int32_t next = anc[i];
+        anc[i] = static_cast<int32_t>(k);
+        if (next == -1) { parent[i] = static_cast<int32_t>(k); break; }
+        i = next;
+      }
+    }
+  }
+}
+
+int64_t tri(int64_t a) { return a * (a + 1) / 2; }
+
+}  // namespace
+
+// ------------------------------------------------------------------------- assembly values
+
+void assembly_values(const Symbolic &S, const double *w, std::vector<double> &vals) {
+  vals.resize(S.a_dest.size());
+  for (int64_t e = 0; e < S.nnz_lower; ++e) vals[e] = -w[S.a_src[e]];
+  for (int64_t k = 0; k < S.nr; ++k) {
+    const int64_t r = S.perm[k];
+    const int64_t gnode = r + (r >= S.ground);
+    double deg = 0.0;
+    for (int64_t p = S.csr_indptr[gnode]; p < S.csr_indptr[gnode + 1]; ++p) deg += w[p];
+    vals[S.nnz_lower + k] = deg;
+  }
+}
+
+// ------------------------------------------------------------------------- analyze
+
+int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indices,
+            const double *w, int32_t ground, int64_t nq, const int32_t *qu, const int32_t *qv,
+            const double *coords, int dim, const peers_options &opt, std::string &err) {
+  int st = validate(n, indptr, indices, w, ground, err);
+  if (st != PEERS_OK) return st;
+  auto t0 = Clock::now();
+  S.n = n;
+  S.nr = n - 1;
+  S.ground = ground;
+  S.nnz_csr = indptr[n];
+  S.csr_indptr.assign(indptr, indptr + n + 1);
+  S.w0.assign(w, w + indptr[n]);
+  const int64_t nr = S.nr;
+  const int leaf = opt.nd_leaf > 0 ? opt.nd_leaf : 32;
+  Adj A = reduced_adjacency(n, indptr, indices, ground);
+
+  // ---- ordering ----
+  std::vector<int32_t> perm;
+  int mode = opt.ordering;
+  if (mode == 0) mode = (coords && dim > 0) ? 1 : 2;
+  if (mode == 1) {
+    if (!coords || dim <= 0) { err = "coordinate ordering needs coords"; return PEERS_EINVAL; }
+    std::vector<double> xy(static_cast<size_t>(nr) * dim);
+    for (int64_t i = 0; i < n; ++i) {
+      if (i == ground) continue;
+      const int64_t r = i > ground ? i - 1 : i;
+      for (int a = 0; a < dim; ++a) xy[r * dim + a] = coords[i * dim + a];
+    }
+    order_coordinate_nd(A, xy.data(), dim, leaf, perm);
+  } else if (mode == 2) {
+    order_bfs_nd(A, leaf, perm);
+  } else if (mode == 3) {
+    perm.resize(static_cast<size_t>(nr));
+    std::iota(perm.begin(), perm.end(), 0);
+  } else {
+    err = "unknown ordering";
+    return PEERS_EINVAL;
+  }
+  std::vector<int32_t> iperm(static_cast<size_t>(nr));
+  for (int64_t k = 0; k < nr; ++k) iperm[perm[k]] = static_cast<int32_t>(k);
+
+  // ---- etree, postorder ----
+  std::vector<int32_t> par;
+  etree(A, perm, iperm, par);
+  {
+    std::vector<int32_t> head(static_cast<size_t>(nr), -1), next(static_cast<size_t>(nr), -1);
+    for (int64_t k = nr - 1; k >= 0; --k)
+      if (par[k] != -1) { next[k] = head[par[k]]; head[par[k]] = static_cast<int32_t>(k); }
+    std::vector<int32_t> post(static_cast<size_t>(nr)), stk;
+    int64_t cnt = 0;
+    for (int64_t r = 0; r < nr; ++r) {
+      if (par[r] != -1) continue;
+      stk.push_back(static_cast<int32_t>(r));
+      while (!stk.empty()) {
+        int32_t v = stk.back();
+        if (head[v] != -1) {       // descend into the next unvisited child
+          int32_t c = head[v];
+          head[v] = next[c];
+          stk.push_back(c);
+        } else {
+          post[v] = static_cast<int32_t>(cnt++);
+          stk.pop_back();
+        }
+      }
+    }
+    std::vector<int32_t> perm2(static_cast<size_t>(nr)), par2(static_cast<size_t>(nr));
+    for (int64_t k = 0; k < nr; ++k) {
+      perm2[post[k]] = perm[k];
+      par2[post[k]] = par[k] == -1 ? -1 : post[par[k]];
+    }
+    perm.swap(perm2);
+    par.swap(par2);
+    for (int64_t k = 0; k < nr; ++k) iperm[perm[k]] = static_cast<int32_t>(k);
+  }
+  S.t_order = since(t0);
+  auto t1 = Clock::now();
+
+  // ---- column counts (strictly lower) by row-subtree traversal ----
+  std::vector<int64_t> cc(static_cast<size_t>(nr), 0);
+  std::vector<int32_t> nchild(static_cast<size_t>(nr), 0);
+  {
+    std::vector<int32_t> mark(static_cast<size_t>(nr), -1);
+    for (int64_t i = 0; i < nr; ++i) {
+      mark[i] = static_cast<int32_t>(i);
+      const int32_t v = perm[i];
+      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+        int32_t j = iperm[A.idx[p]];
+        if (j >= i) continue;
+        while (mark[j] != i) { cc[j]++; mark[j] = static_cast<int32_t>(i); j = par[j]; }
+      }
+      if (par[i] != -1) nchild[par[i]]++;
+    }
+  }
+
+  // ---- fundamental supernodes ----
+  std::vector<int32_t> ffirst;
+  for (int64_t k = 0; k < nr; ++k) {
+    bool join = k > 0 && par[k - 1] == k && cc[k - 1] == cc[k] + 1 && nchild[k] == 1;
+    if (!join) ffirst.push_back(static_cast<int32_t>(k));
+  }
+  const int32_t nf = static_cast<int32_t>(ffirst.size());
+  ffirst.push_back(static_cast<int32_t>(nr));
+  std::vector<int32_t> fcol2sn(static_cast<size_t>(nr));
+  for (int32_t s = 0; s < nf; ++s)
+    for (int32_t k = ffirst[s]; k < ffirst[s + 1]; ++k) fcol2sn[k] = s;
+  std::vector<int32_t> fparent(static_cast<size_t>(nf));
+  for (int32_t s = 0; s < nf; ++s) {
+    int32_t last = ffirst[s + 1] - 1;
+    fparent[s] = par[last] == -1 ? -1 : fcol2sn[par[last]];
+  }
+  // row structure B_s of the fundamental supernodes, bottom-up
+  std::vector<int64_t> frows_off(static_cast<size_t>(nf) + 1, 0);
+  std::vector<int32_t> frows;
+  {
+    std::vector<int32_t> fhead(static_cast<size_t>(nf), -1), fnext(static_cast<size_t>(nf), -1);
+    for (int32_t s = nf - 1; s >= 0; --s)
+      if (fparent[s] != -1) { fnext[s] = fhead[fparent[s]]; fhead[fparent[s]] = s; }
+    std::vector<int32_t> mk(static_cast<size_t>(nr), -1), buf;
+    int64_t total = 0;
+    for (int32_t s = 0; s < nf; ++s) total += cc[ffirst[s + 1] - 1];
+    frows.reserve(static_cast<size_t>(total));
+    for (int32_t s = 0; s < nf; ++s) {
+      const int32_t last = ffirst[s + 1] - 1;
+      buf.clear();
+      for (int32_t k = ffirst[s]; k <= last; ++k) {
+        const int32_t v = perm[k];
+        for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+          int32_t i = iperm[A.idx[p]];
+          if (i > last && mk[i] != s) { mk[i] = s; buf.push_back(i); }
+        }
+      }
+      for (int32_t c = fhead[s]; c != -1; c = fnext[c])
+        for (int64_t p = frows_off[c]; p < frows_off[c + 1]; ++p) {
+          int32_t i = frows[p];
+          if (i > last && mk[i] != s) { mk[i] = s; buf.push_back(i); }
+        }
+      std::sort(buf.begin(), buf.end());
+      if (static_cast<int64_t>(buf.size()) != cc[last]) {
+        err = "internal: supernode structure disagrees with the column counts";
+        return PEERS_EINVAL;
+      }
+      frows.insert(frows.end(), buf.begin(), buf.end());
+      frows_off[s + 1] = static_cast<int64_t>(frows.size());
+    }
+  }
+
+  // ---- relaxed amalgamation: a supernode whose columns end right before its parent's
+  //      (its parent's last child) joins the parent when the merge is small or adds few
+  //      explicit zeros ----
+  const int relax_small = opt.relax_small > 0 ? opt.relax_small : 8;
+  const int relax_max = opt.relax_max > 0 ? opt.relax_max : 32;
+  const double relax_frac = opt.relax_frac > 0 ? opt.relax_frac : 0.15;
+  std::vector<int32_t> into(static_cast<size_t>(nf), -1), cfirst(ffirst.begin(), ffirst.end() - 1),
+      ncols(static_cast<size_t>(nf));
+  std::vector<int64_t> zeros(static_cast<size_t>(nf), 0);
+  for (int32_t s = 0; s < nf; ++s) ncols[s] = ffirst[s + 1] - ffirst[s];
+  for (int32_t s = 0; s < nf; ++s) {
+    const int32_t p = fparent[s];
+    if (p == -1 || cfirst[s] + ncols[s] != cfirst[p]) continue;
+    const int64_t a = ncols[s], b = ncols[p];
+    const int64_t nbs = frows_off[s + 1] - frows_off[s], nbp = frows_off[p + 1] - frows_off[p];
+    const int64_t em = tri(a + b) + (a + b) * nbp;
+    const int64_t zm = zeros[s] + zeros[p] + a * (b + nbp - nbs);
+    if (a + b <= relax_small || (a + b <= relax_max && zm <= relax_frac * em)) {
+      into[s] = p;
+      cfirst[p] = cfirst[s];
+      ncols[p] += static_cast<int32_t>(a);
+      zeros[p] = zm;
+    }
+  }
+  std::vector<int32_t> fin(static_cast<size_t>(nf), -1);   // fundamental -> final id
+  int32_t ns = 0;
+  for (int32_t s = 0; s < nf; ++s)
+    if (into[s] == -1) fin[s] = ns++;
+  S.nsuper = ns;
+  S.first.assign(static_cast<size_t>(ns) + 1, 0);
+  S.parent.assign(static_cast<size_t>(ns), -1);
+  S.nb.assign(static_cast<size_t>(ns), 0);
+  S.rows_off.assign(static_cast<size_t>(ns) + 1, 0);
+  S.rows.clear();
+  for (int32_t s = 0; s < nf; ++s) {
+    if (into[s] != -1) continue;
+    const int32_t f = fin[s];
+    S.first[f] = cfirst[s];
+    int32_t p = fparent[s];
+    while (p != -1 && into[p] != -1) p = into[p];
+    S.parent[f] = p == -1 ? -1 : fin[p];
+    S.nb[f] = static_cast<int32_t>(frows_off[s + 1] - frows_off[s]);
+    S.rows.insert(S.rows.end(), frows.begin() + frows_off[s], frows.begin() + frows_off[s + 1]);
+    S.rows_off[f + 1] = static_cast<int64_t>(S.rows.size());
+  }
+  S.first[ns] = static_cast<int32_t>(nr);
+  S.col2sn.assign(static_cast<size_t>(nr), 0);
+  for (int32_t s = 0; s < ns; ++s)
+    for (int32_t k = S.first[s]; k < S.first[s + 1]; ++k) S.col2sn[k] = s;
+  S.perm = perm;
+  S.iperm = iperm;
+
+  // relative maps into the parent front: rows of s (C_s then B_s) -> local index in parent
+  S.rmap.assign(S.rows.size(), -1);
+  for (int32_t s = 0; s < ns; ++s) {
+    const int32_t p = S.parent[s];
+    if (p == -1) continue;
+    const int32_t pf = S.first[p], pnc = sn_nc(S, p);
+    auto pb = S.rows.begin() + S.rows_off[p], pe = S.rows.begin() + S.rows_off[p + 1];
+    for (int64_t t = S.rows_off[s]; t < S.rows_off[s + 1]; ++t) {
+      const int32_t r = S.rows[t];
+      if (r < pf) { err = "internal: row below the parent's first column"; return PEERS_EINVAL; }
+      if (r < pf + pnc) { S.rmap[t] = r - pf; continue; }
+      auto it = std::lower_bound(pb, pe, r);
+      if (it == pe || *it != r) { err = "internal: child row missing from parent"; return PEERS_EINVAL; }
+      S.rmap[t] = pnc + static_cast<int32_t>(it - pb);
+    }
+  }
+
+  // children, subtree starts, levels (height above the leaves)
+  S.child_ptr.assign(static_cast<size_t>(ns) + 1, 0);
+  for (int32_t s = 0; s < ns; ++s)
+    if (S.parent[s] != -1) S.child_ptr[S.parent[s] + 1]++;
+  for (int32_t s = 0; s < ns; ++s) S.child_ptr[s + 1] += S.child_ptr[s];
+  S.child_list.assign(static_cast<size_t>(S.child_ptr[ns]), 0);
+  {
+    std::vector<int32_t> fill(S.child_ptr.begin(), S.child_ptr.end() - 1);
+    for (int32_t s = 0; s < ns; ++s)
+      if (S.parent[s] != -1) S.child_list[fill[S.parent[s]]++] = s;
+  }
+  S.fdesc.assign(static_cast<size_t>(ns), 0);
+  S.level.assign(static_cast<size_t>(ns), 0);
+  for (int32_t s = 0; s < ns; ++s) {
+    S.fdesc[s] = s;
+    for (int32_t c = S.child_ptr[s]; c < S.child_ptr[s + 1]; ++c) {
+      const int32_t ch = S.child_list[c];
+      S.fdesc[s] = std::min(S.fdesc[s], S.fdesc[ch]);
+      S.level[s] = std::max(S.level[s], S.level[ch] + 1);
+    }
+  }
+  S.nlevels = 0;
+  for (int32_t s = 0; s < ns; ++s) S.nlevels = std::max(S.nlevels, S.level[s] + 1);
+  S.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+  for (int32_t s = 0; s < ns; ++s) S.level_ptr[S.level[s] + 1]++;
+  for (int32_t l = 0; l < S.nlevels; ++l) S.level_ptr[l + 1] += S.level_ptr[l];
+  S.level_sn.assign(static_cast<size_t>(ns), 0);
+  {
+    std::vector<int32_t> fill(S.level_ptr.begin(), S.level_ptr.end() - 1);
+    for (int32_t s = 0; s < ns; ++s) S.level_sn[fill[S.level[s]]++] = s;
+    for (int32_t l = 0; l < S.nlevels; ++l)
+      std::stable_sort(S.level_sn.begin() + S.level_ptr[l], S.level_sn.begin() + S.level_ptr[l + 1],
+                       [&](int32_t a, int32_t b) { return sn_nc(S, a) > sn_nc(S, b); });
+  }
+
+  // ---- device layout ----
+  S.panel_off.assign(static_cast<size_t>(ns) + 1, 0);
+  S.tinv_off.assign(static_cast<size_t>(ns) + 1, 0);
+  S.u_off.assign(static_cast<size_t>(ns) + 1, 0);
+  S.nbmax = 0;
+  S.factor_fma = 0;
+  for (int32_t s = 0; s < ns; ++s) {
+    const int64_t nc = sn_nc(S, s), nbv = S.nb[s], N = nc + nbv;
+    S.panel_off[s + 1] = S.panel_off[s] + N * nc;
+    const int64_t nblk = (nc + kBlock - 1) / kBlock, bwl = nc - (nblk - 1) * kBlock;
+    S.tinv_off[s + 1] = S.tinv_off[s] + (nblk - 1) * kBlock * kBlock + bwl * bwl;
+    S.u_off[s + 1] = S.u_off[s] + nbv * nbv;
+    S.nbmax = std::max<int32_t>(S.nbmax, static_cast<int32_t>(nbv));
+    // dense partial LDL^T of an N x nc front: sum over columns k of (N-k-1)(N-k)/2
+    for (int64_t k = 0; k < nc; ++k) S.factor_fma += (N - k - 1) * (N - k) / 2;
+  }
+  S.panel_total = S.panel_off[ns];
+  S.tinv_total = S.tinv_off[ns];
+  S.u_total = S.u_off[ns];
+
+  // ---- assembly map of L_r into the panels ----
+  {
+    auto local_row = [&](int32_t s, int32_t i) -> int64_t {
+      const int32_t f = S.first[s], nc = sn_nc(S, s);
+      if (i < f + nc) return i - f;
+      auto b = S.rows.begin() + S.rows_off[s], e = S.rows.begin() + S.rows_off[s + 1];
+      auto it = std::lower_bound(b, e, i);
+      if (it == e || *it != i) return -1;
+      return nc + (it - b);
+    };
+    S.a_dest.clear();
+    S.a_src.clear();
+    for (int64_t gi = 0; gi < n; ++gi) {
+      if (gi == ground) continue;
+      const int32_t i = iperm[gi > ground ? gi - 1 : gi];
+      for (int64_t p = indptr[gi]; p < indptr[gi + 1]; ++p) {
+        const int32_t gj = indices[p];
+        if (gj == ground) continue;
+        const int32_t j = iperm[gj > ground ? gj - 1 : gj];
+        if (i <= j) continue;   // lower entry (row i > column j)
+        const int32_t s = S.col2sn[j];
+        const int64_t N = sn_nc(S, s) + S.nb[s];
+        const int64_t lr = local_row(s, i);
+        if (lr < 0) { err = "internal: matrix entry outside the supernode structure"; return PEERS_EINVAL; }
+        S.a_dest.push_back(S.panel_off[s] + static_cast<int64_t>(j - S.first[s]) * N + lr);
+        S.a_src.push_back(p);
+      }
+    }
+    S.nnz_lower = static_cast<int64_t>(S.a_dest.size());
+    for (int64_t k = 0; k < nr; ++k) {
+      const int32_t s = S.col2sn[k];
+      const int64_t N = sn_nc(S, s) + S.nb[s];
+      const int64_t c = k - S.first[s];
+      S.a_dest.push_back(S.panel_off[s] + c * N + c);
+    }
+  }
+
+  // ---- factorization schedule ----
+  S.level_nblocks.assign(static_cast<size_t>(S.nlevels), 0);
+  S.trail_base.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+  S.trail_off.clear();
+  S.trail_na.clear();
+  S.trail_prefix.clear();
+  for (int32_t l = 0; l < S.nlevels; ++l) {
+    const int32_t *ls = S.level_sn.data() + S.level_ptr[l];
+    const int32_t cnt = S.level_ptr[l + 1] - S.level_ptr[l];
+    const int32_t nblk = (sn_nc(S, ls[0]) + kBlock - 1) / kBlock;
+    S.level_nblocks[l] = nblk;
+    S.trail_base[l + 1] = S.trail_base[l] + nblk;
+    for (int32_t J = 0; J < nblk; ++J) {
+      int32_t na = 0;
+      while (na < cnt && sn_nc(S, ls[na]) > J * kBlock) ++na;
+      S.trail_off.push_back(static_cast<int64_t>(S.trail_prefix.size()));
+      S.trail_na.push_back(na);
+      int64_t acc = 0;
+      S.trail_prefix.push_back(0);
+      for (int32_t i = 0; i < na; ++i) {
+        const int32_t s = ls[i];
+        const int64_t nc = sn_nc(S, s), N = nc + S.nb[s];
+        const int64_t t0 = std::min<int64_t>(nc, (J + 1) * kBlock);
+        const int64_t T = (N - t0 + kTile - 1) / kTile;
+        acc += T * (T + 1) / 2;
+        S.trail_prefix.push_back(acc);
+      }
+    }
+  }
+  S.ea_base.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+  S.ea_off.clear();
+  S.ea_pairs.clear();
+  for (int32_t l = 0; l < S.nlevels; ++l) {
+    int32_t maxc = 0;
+    for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
+      const int32_t s = S.level_sn[i];
+      maxc = std::max(maxc, S.child_ptr[s + 1] - S.child_ptr[s]);
+    }
+    S.ea_base[l + 1] = S.ea_base[l] + maxc;
+    for (int32_t r = 0; r < maxc; ++r) {
+      S.ea_off.push_back(static_cast<int64_t>(S.ea_pairs.size() / 2));
+      for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
+        const int32_t s = S.level_sn[i];
+        if (S.child_ptr[s] + r < S.child_ptr[s + 1]) {
+          S.ea_pairs.push_back(s);
+          S.ea_pairs.push_back(S.child_list[S.child_ptr[s] + r]);
+        }
+      }
+    }
+  }
+  S.ea_off.push_back(static_cast<int64_t>(S.ea_pairs.size() / 2));
+  S.t_symbolic = since(t1);
+  auto t2 = Clock::now();
+
+  // ---- queries (§III-G: each query mapped to permuted endpoints, grouped by start) ----
+  std::vector<int32_t> eu, ev;
+  const int32_t *QU = qu, *QV = qv;
+  if (nq < 0 || !qu || !qv) {
+    for (int64_t u = 0; u < n; ++u)
+      for (int64_t p = indptr[u]; p < indptr[u + 1]; ++p)
+        if (indices[p] > u) { eu.push_back(static_cast<int32_t>(u)); ev.push_back(indices[p]); }
+    nq = static_cast<int64_t>(eu.size());
+    QU = eu.data();
+    QV = ev.data();
+  }
+  S.nq = nq;
+  struct Rec { int32_t s0, a, b; int64_t idx; };
+  std::vector<Rec> recs;
+  recs.reserve(static_cast<size_t>(nq));
+  S.nq_trivial = 0;
+  S.nq_two = 0;
+  auto pos = [&](int64_t u) -> int32_t {
+    return u == ground ? -1 : iperm[u > ground ? u - 1 : u];
+  };
+  for (int64_t i = 0; i < nq; ++i) {
+    const int64_t u = QU[i], v = QV[i];
+    if (u < 0 || u >= n || v < 0 || v >= n) { err = "query node out of range"; return PEERS_EINVAL; }
+    if (u == v) { S.nq_trivial++; continue; }
+    int32_t pu = pos(u), pv = pos(v), lo, hi;
+    if (pu < 0 || pv < 0) { lo = std::max(pu, pv); hi = -1; }
+    else { lo = std::min(pu, pv); hi = std::max(pu, pv); }
+    const int32_t s0 = S.col2sn[lo];
+    const int32_t f = S.first[s0], nc = sn_nc(S, s0);
+    int32_t b = -1;
+    if (hi >= 0) {
+      if (hi < f + nc) {
+        b = hi - f;
+      } else {
+        auto rb = S.rows.begin() + S.rows_off[s0], re = S.rows.begin() + S.rows_off[s0 + 1];
+        auto it = std::lower_bound(rb, re, hi);
+        if (it == re || *it != hi) {
+          S.nq_two++;
+          continue;
+        }
+        b = nc + static_cast<int32_t>(it - rb);
+      }
+    }
+    recs.push_back({s0, lo - f, b, i});
+  }
+  if (S.nq_two > 0) {
+    err = std::to_string(S.nq_two) +
+          " queries are pairs whose etree paths only meet above their starting supernode; "
+          "this build walks single paths (every graph edge and every pair touching the "
+          "ground qualifies)";
+    return PEERS_EINVAL;
+  }
+  std::sort(recs.begin(), recs.end(), [](const Rec &x, const Rec &y) {
+    if (x.s0 != y.s0) return x.s0 < y.s0;
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    return x.idx < y.idx;
+  });
+  S.nsorted = static_cast<int64_t>(recs.size());
+  S.qorig.resize(recs.size());
+  S.qa.resize(recs.size());
+  S.qb.resize(recs.size());
+  S.qbeg.assign(static_cast<size_t>(ns) + 1, 0);
+  for (size_t k = 0; k < recs.size(); ++k) {
+    S.qorig[k] = recs[k].idx;
+    S.qa[k] = recs[k].a;
+    S.qb[k] = recs[k].b;
+    S.qbeg[recs[k].s0 + 1]++;
+  }
+  for (int32_t s = 0; s < ns; ++s) S.qbeg[s + 1] += S.qbeg[s];
+
+  // tile sizes: as many queries as fit the shared-memory budget, up to kQMax
+  S.qtile.assign(static_cast<size_t>(ns), 1);
+  for (int32_t s = 0; s < ns; ++s) {
+    const int64_t N = sn_nc(S, s) + S.nb[s];
+    int64_t q = kSweepSmemBudget / (8 * (N + 2 * kBlock));
+    if (q >= 4) q -= q % 4;
+    S.qtile[s] = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(kQMax, q)));
+    if (sweep_smem_bytes(N, S.qtile[s]) > kMaxSmem) {
+      err = "supernode front of " + std::to_string(N) + " rows exceeds one CTA's shared memory";
+      return PEERS_ENOMEM;
+    }
+  }
+
+  // waves: bound the carry buffer (one slot of nbmax doubles per query in flight)
+  int64_t budget = opt.reserved[0] > 0 ? opt.reserved[0] : (int64_t(48) << 30);
+  const int64_t slot_bytes = std::max<int64_t>(8, int64_t(8) * S.nbmax);
+  int64_t per_wave = std::max<int64_t>(1, budget / slot_bytes);
+  if (per_wave > INT32_MAX) per_wave = INT32_MAX;
+  S.waves.clear();
+  S.carry_slots = 0;
+  S.walk_entries = 0;
+  S.walk_fma = 0;
+  auto item_fma = [&](int32_t s, int32_t j0) -> int64_t {
+    const int64_t nc = sn_nc(S, s), N = nc + S.nb[s];
+    int64_t f = 0;
+    for (int64_t J = j0; J < nc; J += kBlock) {
+      const int64_t bw = std::min<int64_t>(kBlock, nc - J);
+      f += bw * (bw - 1) / 2 + (N - J - bw) * bw + bw;
+    }
+    return f;
+  };
+  auto entries = [&](int32_t s, int64_t first_col) -> int64_t {
+    const int64_t np = sn_nc(S, s) - first_col;
+    return np * (np - 1) / 2 + int64_t(S.nb[s]) * np + np;
+  };
+  for (int64_t w0 = 0; w0 < std::max<int64_t>(S.nsorted, 1); w0 += per_wave) {
+    SweepWave W;
+    W.q_begin = w0;
+    W.q_end = std::min<int64_t>(S.nsorted, w0 + per_wave);
+    if (W.q_end <= W.q_begin && S.nsorted > 0) break;
+    S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
+    W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+    std::vector<std::pair<int64_t, SweepItem>> lv;
+    for (int32_t l = 0; l < S.nlevels; ++l) {
+      lv.clear();
+      for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
+        const int32_t p = S.level_sn[i];
+        const int32_t tile = S.qtile[p];
+        auto emit = [&](int32_t src, int64_t b, int64_t e) {
+          b = std::max(b, W.q_begin);
+          e = std::min(e, W.q_end);
+          for (int64_t q = b; q < e; q += tile) {
+            SweepItem it{};
+            it.s = p;
+            it.src = src;
+            it.q0 = static_cast<int32_t>(q);
+            it.nq = static_cast<int32_t>(std::min<int64_t>(tile, e - q));
+            int32_t j0;
+            if (src >= 0) {
+              j0 = S.rmap[S.rows_off[src]];
+              S.walk_entries += it.nq * entries(p, j0);
+            } else {
+              j0 = S.qa[q];
+              for (int64_t k = q; k < q + it.nq; ++k) S.walk_entries += entries(p, S.qa[k]);
+            }
+            it.j0 = (j0 / kBlock) * kBlock;
+            const int64_t f = it.nq * item_fma(p, it.j0);
+            S.walk_fma += f;
+            lv.push_back({f, it});
+          }
+        };
+        for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
+          const int32_t ch = S.child_list[c];
+          emit(ch, S.qbeg[S.fdesc[ch]], S.qbeg[ch + 1]);
+        }
+        emit(-1, S.qbeg[p], S.qbeg[p + 1]);
+      }
+      std::stable_sort(lv.begin(), lv.end(),
+                       [](const auto &x, const auto &y) { return x.first > y.first; });
+      int64_t smem = 0;
+      for (auto &x : lv) {
+        W.items.push_back(x.second);
+        const int32_t s = x.second.s;
+        smem = std::max(smem, sweep_smem_bytes(sn_nc(S, s) + S.nb[s], x.second.nq));
+      }
+      W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
+      W.level_smem.push_back(smem);
+    }
+    S.waves.push_back(std::move(W));
+    if (S.nsorted == 0) break;
+  }
+  S.t_queries = since(t2);
+  return PEERS_OK;
+}
+
+}  // namespace peers

@@ -1,0 +1,67 @@
+// Device-side declarations shared by the factorization and the sweep (library-internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "internal.h"
+
+#define CUDA_TRY(x)                                                            \
+  do {                                                                         \
+    cudaError_t e_ = (x);                                                      \
+    if (e_ != cudaSuccess) {                                                   \
+      err = std::string(#x) + ": " + cudaGetErrorString(e_);                   \
+      return PEERS_ECUDA;                                                      \
+    }                                                                          \
+  } while (0)
+
+namespace peers {
+
+constexpr int kErrNotSpd = 1;
+
+// Records the first error code and where it happened; later errors are dropped.
+__device__ inline void flag_error(int *status, int code, int where) {
+  if (atomicCAS(status, 0, code) == 0) atomicExch(status + 1, where);
+}
+
+// Device pointers used by the factorization kernels.
+struct FactorArgs {
+  double *panel, *U, *tinv, *d, *dinv;
+  const int32_t *first, *nb, *rmap;
+  const int64_t *panel_off, *tinv_off, *u_off, *rows_off;
+  int *status;
+};
+
+struct FactorDevice {
+  FactorArgs args;
+  const int64_t *a_dest;
+  const double *a_val;
+  const int32_t *level_sn;
+  const int32_t *ea_pairs;
+  const int64_t *trail_prefix;
+};
+
+// Device pointers used by the sweep kernel.
+struct SweepArgs {
+  const double *panel, *tinv, *dinv;
+  const int32_t *first, *nb, *rmap;
+  const int64_t *panel_off, *tinv_off, *rows_off;
+  const int32_t *qa, *qb;
+  const int64_t *qorig;
+  double *carry;   // carry_slots x nbmax: the B-part of each query's front, slot-major
+  double *racc;    // carry_slots: running sum_k y_k^2 / d_k of each query
+  double *R;       // nq results in the caller's query order
+  int64_t nbmax;
+  int64_t wave_base;
+};
+
+int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, std::string &err);
+
+// Launches the sweep of one wave, level by level.  If `events` is non-null it must hold
+// 2 * nlevels events; launch l is bracketed by events[2l], events[2l+1].
+int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_items,
+                   const SweepArgs &args, cudaStream_t stream, cudaEvent_t *events,
+                   std::string &err);
+
+}  // namespace peers

@@ -1,0 +1,145 @@
+// Internal data structures shared by the host analysis, the device factorization and the
+// device sweep of the PEERS library.  Not part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "peers.h"
+
+#ifdef __CUDACC__
+#define PEERS_HD __host__ __device__
+#else
+#define PEERS_HD
+#endif
+
+namespace peers {
+
+// Width of a column block: the factorization's panel blocks, the sweep's diagonal-block
+// inverses and the sweep's update steps all use it, so every query's arithmetic is blocked
+// identically whatever tile it lands in.
+constexpr int kBlock = 32;
+// Rows x columns of one trailing-update tile of the factorization.
+constexpr int kTile = 64;
+// Largest number of queries one sweep tile (one CTA) carries.
+constexpr int kQMax = 32;
+// Shared-memory budget of one sweep CTA for its query fronts (bytes).
+constexpr int64_t kSweepSmemBudget = 200 * 1024;
+
+// Largest dynamic shared memory of one CTA on sm_103a (bytes).
+constexpr int64_t kMaxSmem = 232448;
+
+// Row stride (in queries) of a sweep CTA's shared front: a multiple of 4, at least 4.
+PEERS_HD inline int64_t sweep_qstride(int64_t Q) { return Q < 4 ? 4 : (Q + 3) / 4 * 4; }
+// Dynamic shared memory of a sweep CTA for a front of N rows and Q queries: the front
+// itself plus the block's y values and y^2/d terms.
+PEERS_HD inline int64_t sweep_smem_bytes(int64_t N, int64_t Q) {
+  return (N + 2 * kBlock) * sweep_qstride(Q) * 8;
+}
+
+// One unit of sweep work: queries [q0, q0+nq) of the sorted query order at supernode s.
+// src >= 0: the queries arrive from child supernode src (their carries are scattered through
+// src's relative map); src == -1: the queries start at s (seeded with +1/-1).
+struct SweepItem {
+  int32_t s;
+  int32_t src;
+  int32_t q0;
+  int32_t nq;
+  int32_t j0;   // first column block (block-aligned) with a non-zero right-hand side
+  int32_t pad;
+};
+
+// One wave of the sweep: the queries [q_begin, q_end) of the sorted order, walked to the
+// root level by level.  items[level_ptr[l] .. level_ptr[l+1]) are the level's items.
+struct SweepWave {
+  int64_t q_begin, q_end;
+  std::vector<int64_t> level_ptr;
+  std::vector<int64_t> level_smem;   // dynamic shared memory of the level's launch
+  std::vector<SweepItem> items;
+};
+
+struct Symbolic {
+  // ---- graph ----
+  int64_t n = 0;        // graph nodes
+  int64_t nr = 0;       // reduced nodes (n - 1)
+  int32_t ground = 0;
+  int64_t nnz_csr = 0;  // stored CSR entries of the input graph
+  // reduced node r <-> graph node: graph = r + (r >= ground)
+  std::vector<int32_t> perm;   // elimination position k -> reduced node
+  std::vector<int32_t> iperm;  // reduced node -> elimination position
+
+  // ---- supernodes (postorder; columns of supernode s are [first[s], first[s+1])) ----
+  int32_t nsuper = 0;
+  std::vector<int32_t> first;       // nsuper + 1
+  std::vector<int32_t> parent;      // nsuper
+  std::vector<int32_t> nb;          // below-diagonal row count
+  std::vector<int32_t> level;       // height above the leaves
+  std::vector<int32_t> fdesc;       // first (lowest-numbered) supernode of the subtree
+  std::vector<int32_t> child_ptr, child_list;   // children in increasing order
+  std::vector<int64_t> rows_off;    // nsuper + 1: B_s = rows[rows_off[s] .. rows_off[s+1])
+  std::vector<int32_t> rows;        // global row indices (elimination positions), ascending
+  std::vector<int32_t> rmap;        // parallel to rows: local row of B_s[t] in the parent front
+  std::vector<int32_t> col2sn;      // column -> supernode
+  int32_t nlevels = 0;
+  std::vector<int32_t> level_ptr;   // nlevels + 1
+  std::vector<int32_t> level_sn;    // supernodes by level, each level sorted by n_c descending
+
+  // ---- device layout of the factor ----
+  std::vector<int64_t> panel_off;   // panel of s: (n_c+n_b) x n_c column-major, ld = n_c+n_b
+  int64_t panel_total = 0;
+  std::vector<int64_t> tinv_off;    // diagonal-block inverses of s: block J at +kBlock^2 * J
+  int64_t tinv_total = 0;
+  std::vector<int64_t> u_off;       // update matrix of s: n_b x n_b column-major
+  int64_t u_total = 0;
+  // assembly of L_r into the panels: entry e goes to panel[a_dest[e]].  Entries are the
+  // strictly-lower entries followed by the nr diagonal entries.  a_src[e] is the CSR index
+  // of the conductance of an off-diagonal entry.
+  std::vector<int64_t> a_dest;
+  std::vector<int64_t> a_src;
+  int64_t nnz_lower = 0;
+  // diagonal of the reduced node r = sum of the conductances of CSR row g(r)
+  std::vector<int64_t> csr_indptr;  // copy of the input indptr (to rebuild degrees)
+  std::vector<double> w0;           // conductances given to analyze
+  // factorization schedule per level: number of column blocks of the widest supernode
+  std::vector<int32_t> level_nblocks;
+  // trailing-update tiles: for (level l, block J) the active supernodes are the first
+  // na = trail_na[tp] of level l's list; trail_prefix[trail_off[tp] + i] is the tile prefix
+  // of the i-th active supernode (na + 1 entries).  tp = trail_base[l] + J.
+  std::vector<int64_t> trail_base, trail_off, trail_na;
+  std::vector<int64_t> trail_prefix;
+  // extend-add schedule: for level l and child rank r, pairs (parent, child) in
+  // ea_pairs[ea_off[ea_base[l] + r] .. ea_off[ea_base[l] + r + 1])
+  std::vector<int64_t> ea_base;     // nlevels + 1 (index into ea_off)
+  std::vector<int64_t> ea_off;
+  std::vector<int32_t> ea_pairs;    // (parent, child) interleaved
+  int64_t factor_fma = 0;
+
+  // ---- queries ----
+  int64_t nq = 0;                   // as given
+  int64_t nq_trivial = 0;
+  int64_t nq_two = 0;
+  int64_t nsorted = 0;              // non-trivial queries, sorted by (start supernode, lo)
+  std::vector<int64_t> qorig;       // sorted slot -> user query index
+  std::vector<int32_t> qa, qb;      // local seed rows (+1 at qa, -1 at qb; qb = -1: none)
+  std::vector<int64_t> qbeg;        // nsuper + 1: first slot whose start supernode is >= s
+  std::vector<int32_t> qtile;       // tile size (queries per CTA) per supernode
+  int32_t nbmax = 0;
+  std::vector<SweepWave> waves;
+  int64_t carry_slots = 0;          // slots of the carry buffer (largest wave)
+  int64_t walk_entries = 0, walk_fma = 0;
+  double t_order = 0, t_symbolic = 0, t_queries = 0;
+};
+
+// Host analysis (analyze.cpp).  Returns a PEERS_* status and fills `err`.
+int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indices,
+            const double *w, int32_t ground, int64_t nq, const int32_t *qu, const int32_t *qv,
+            const double *coords, int dim, const peers_options &opt, std::string &err);
+
+// Conductance-dependent assembly values (off-diagonals -w, then diagonals = degrees) in the
+// order of a_dest, for conductances w (CSR layout of the analysed graph).
+void assembly_values(const Symbolic &S, const double *w, std::vector<double> &vals);
+
+inline int32_t sn_nc(const Symbolic &S, int32_t s) { return S.first[s + 1] - S.first[s]; }
+
+}  // namespace peers

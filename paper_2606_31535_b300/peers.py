@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libpeers.so (include/peers.h).
+
+Argument marshalling only: every step of the computation runs in the library (host analysis
+in C++, factorization and sweep in CUDA kernels).  PyTorch is used for device buffers and
+the CUDA stream; the library is loaded from this package directory and a missing library is
+an error, never a fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpeers.so")
+
+OK = 0
+EINVAL, ENOTCONNECTED, ENOTSPD, ENOMEM, ECUDA, ETIMEOUT, ENOTREADY = -1, -2, -3, -4, -5, -6, -7
+OUT_DEVICE = 1
+
+_lib = None
+
+
+class PeersError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("ordering", ctypes.c_int32), ("nd_leaf", ctypes.c_int32),
+                ("relax_small", ctypes.c_int32), ("relax_max", ctypes.c_int32),
+                ("relax_frac", ctypes.c_double), ("reserved", ctypes.c_int64 * 8)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "n", "n_reduced", "nnz_a", "nnz_l", "nsuper", "levels", "max_nc", "max_nb", "nq",
+        "nq_trivial", "nq_two_branch", "walk_entries", "walk_fma", "factor_fma",
+        "device_bytes")] + [("t_order", ctypes.c_double), ("t_symbolic", ctypes.c_double),
+                            ("t_queries", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def load(path: str | None = None):
+    """Loads libpeers.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2606_31535_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "peers_create": (ctypes.c_int, [P(vp), ctypes.c_int, vp]),
+        "peers_destroy": (None, [vp]),
+        "peers_analyze": (ctypes.c_int, [vp, i64, vp, vp, vp, i32, i64, vp, vp, vp, ctypes.c_int,
+                                         vp, P(vp)]),
+        "peers_symbolic_info": (ctypes.c_int, [vp, P(Info)]),
+        "peers_num_queries": (i64, [vp]),
+        "peers_footprint_bytes": (i64, [vp]),
+        "peers_free_symbolic": (None, [vp]),
+        "peers_symbolic_export": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+        "peers_factor": (ctypes.c_int, [vp, vp, vp, P(vp)]),
+        "peers_numeric_diag": (ctypes.c_int, [vp, vp, vp]),
+        "peers_free_numeric": (None, [vp]),
+        "peers_query": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+        "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "peers_last_timing": (ctypes.c_int, [vp, P(dbl)]),
+        "peers_last_level_times": (ctypes.c_int, [vp, P(dbl), i64]),
+        "peers_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "peers_last_error": (ctypes.c_char_p, []),
+        "peers_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        lib = load()
+        msg = lib.peers_last_error().decode() or lib.peers_strerror(status).decode()
+        raise PeersError(status, where, msg)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(int(a.data_ptr()))   # torch tensor
+
+
+class Context:
+    """A device and the CUDA stream the library issues its work on."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        self.device = device
+        self._stream = stream
+        handle = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        _check(lib.peers_create(ctypes.byref(handle), int(device), s), "peers_create")
+        self._h = handle
+
+    @classmethod
+    def for_torch(cls, device: int = 0):
+        """Context on torch's current stream of `device`."""
+        import torch
+        return cls(device, torch.cuda.current_stream(device))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().peers_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_timing(self, on: bool = True):
+        _check(load().peers_set_timing(self._h, int(on)), "peers_set_timing")
+
+    def last_timing(self) -> dict:
+        out = (ctypes.c_double * 3)()
+        _check(load().peers_last_timing(self._h, out), "peers_last_timing")
+        return {"sweep_s": out[0], "max_launch_s": out[1], "factor_s": out[2]}
+
+    def last_level_times(self) -> np.ndarray:
+        buf = (ctypes.c_double * 4096)()
+        n = load().peers_last_level_times(self._h, buf, 4096)
+        if n < 0:
+            _check(n, "peers_last_level_times")
+        return np.array(buf[:min(n, 4096)])
+
+
+class Symbolic:
+    """Host plan: ordering, elimination tree, supernodes and query grouping."""
+
+    def __init__(self, n, indptr, indices, w, ground=0, qu=None, qv=None, coords=None,
+                 options: Options | None = None):
+        lib = load()
+        self._keep = [np.ascontiguousarray(indptr, dtype=np.int64),
+                      np.ascontiguousarray(indices, dtype=np.int32),
+                      np.ascontiguousarray(w, dtype=np.float64)]
+        if qu is not None:
+            qu = np.ascontiguousarray(qu, dtype=np.int32)
+            qv = np.ascontiguousarray(qv, dtype=np.int32)
+            nq = qu.size
+        else:
+            nq = -1
+        c = None if coords is None else np.ascontiguousarray(coords, dtype=np.float64)
+        dim = 0 if c is None else (c.shape[1] if c.ndim == 2 else 1)
+        h = ctypes.c_void_p()
+        opt = ctypes.byref(options) if options is not None else None
+        _check(lib.peers_analyze(None, int(n), _ptr(self._keep[0]), _ptr(self._keep[1]),
+                                 _ptr(self._keep[2]), int(ground), int(nq), _ptr(qu), _ptr(qv),
+                                 _ptr(c), int(dim), opt, ctypes.byref(h)), "peers_analyze")
+        self._h = h
+        self.n = int(n)
+        self.nq = int(lib.peers_num_queries(h))
+
+    @classmethod
+    def of(cls, g, ground=0, qu=None, qv=None, use_coords=True, options=None):
+        return cls(g.n, g.indptr, g.indices, g.w, ground, qu, qv,
+                   g.coords if use_coords else None, options)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().peers_free_symbolic(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().peers_symbolic_info(self._h, ctypes.byref(inf)), "peers_symbolic_info")
+        return inf.as_dict()
+
+    def footprint_bytes(self) -> int:
+        return int(load().peers_footprint_bytes(self._h))
+
+    def export(self) -> dict:
+        inf = self.info()
+        nr, ns = inf["n_reduced"], inf["nsuper"]
+        perm = np.empty(nr, np.int32)
+        first = np.empty(ns + 1, np.int32)
+        parent = np.empty(ns, np.int32)
+        nb = np.empty(ns, np.int32)
+        level = np.empty(ns, np.int32)
+        _check(load().peers_symbolic_export(self._h, _ptr(perm), _ptr(first), _ptr(parent),
+                                            _ptr(nb), _ptr(level)), "peers_symbolic_export")
+        return {"perm": perm, "first": first, "parent": parent, "nb": nb, "level": level}
+
+
+class Numeric:
+    """Device-resident L D L^T factor of a plan's grounded Laplacian."""
+
+    def __init__(self, ctx: Context, sym: Symbolic, w=None):
+        lib = load()
+        self._ctx, self._sym = ctx, sym
+        self._w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib.peers_factor(ctx._h, sym._h, _ptr(self._w), ctypes.byref(h)), "peers_factor")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().peers_free_numeric(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def diag(self) -> np.ndarray:
+        d = np.empty(self._sym.info()["n_reduced"], np.float64)
+        _check(load().peers_numeric_diag(self._ctx._h, self._h, _ptr(d)), "peers_numeric_diag")
+        return d
+
+
+def query(ctx: Context, sym: Symbolic, num: Numeric, out=None):
+    """Resistances of the plan's queries.  `out` may be a float64 torch CUDA tensor (written on
+    the device) or a numpy array (host); None allocates a numpy array."""
+    lib = load()
+    if out is None:
+        out = np.empty(sym.nq, dtype=np.float64)
+    flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
+    _check(lib.peers_query(ctx._h, sym._h, num._h, _ptr(out), flags), "peers_query")
+    return out
+
+
+def effective_resistance(g, qu=None, qv=None, ground=0, device=0, use_coords=True):
+    """One-shot convenience: analyse, factor on `device` and sweep; returns a numpy array."""
+    ctx = Context(device)
+    sym = Symbolic.of(g, ground, qu, qv, use_coords)
+    num = Numeric(ctx, sym)
+    return query(ctx, sym, num)

@@ -1,0 +1,161 @@
+"""Host-side tests of the C-ABI library (no GPU): the exported symbols, input validation and
+the structure produced by peers_analyze."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2606_31535_b300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2606_31535_b300 import build, peers
+    build.build()
+    peers.load()
+    return peers
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "peers.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(peers_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(P):
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(P.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_strerror_and_version(P):
+    lib = P.load()
+    assert lib.peers_strerror(0) == b"ok"
+    assert lib.peers_strerror(P.ENOTSPD)
+    assert b"sm_103a" in lib.peers_version()
+
+
+def _bad(P, g, **kw):
+    with pytest.raises(P.PeersError) as e:
+        P.Symbolic(g.n, g.indptr, g.indices, g.w, **kw)
+    return e.value.status
+
+
+def test_rejects_malformed_graphs(P):
+    g = I.grid2d(6, 7, seed=1)
+    w = g.w.copy()
+    w[3] = -1.0
+    assert _bad(P, I.Graph(g.n, g.indptr, g.indices, w)) == P.EINVAL
+    w = g.w.copy()
+    w[5] = np.nan
+    assert _bad(P, I.Graph(g.n, g.indptr, g.indices, w)) == P.EINVAL
+    w = g.w.copy()
+    w[0] *= 2.0   # (u,v) and (v,u) differ
+    assert _bad(P, I.Graph(g.n, g.indptr, g.indices, w)) == P.EINVAL
+    idx = g.indices.copy()
+    idx[0] = 0    # self-loop at node 0
+    assert _bad(P, I.Graph(g.n, g.indptr, idx, g.w)) == P.EINVAL
+    assert _bad(P, g, ground=g.n) == P.EINVAL
+    # two disjoint grids
+    a = I.grid2d(4, 4, seed=2)
+    u, v = a.all_edges()
+    ww = a.edge_weights()
+    two = I.from_edges(32, np.concatenate([u, u + 16]), np.concatenate([v, v + 16]),
+                       np.concatenate([ww, ww]))
+    assert _bad(P, two) == P.ENOTCONNECTED
+    with pytest.raises(P.PeersError):
+        P.Symbolic(g.n, g.indptr, g.indices, g.w, qu=np.array([0]), qv=np.array([g.n]))
+
+
+def test_duplicate_edge_rejected(P):
+    g = I.from_edges(3, np.array([0, 0, 1]), np.array([1, 1, 2]), np.array([1.0, 1.0, 1.0]))
+    assert _bad(P, g) == P.EINVAL
+
+
+@pytest.mark.parametrize("maker,use_coords", [
+    (I.grid32, True), (I.grid32, False),
+    (lambda: I.pdn3(side=33, seed=3), True),
+    (lambda: I.rgg(4000, seed=4), True), (lambda: I.rgg(4000, seed=4), False),
+    (lambda: I.grid_deleted(40, 45, seed=5), False),
+])
+def test_supernodal_structure(P, maker, use_coords):
+    """Supernodes partition the columns, parents come later, levels are heights, and the
+    elimination order is a permutation of the reduced nodes."""
+    g = maker()
+    sym = P.Symbolic.of(g, use_coords=use_coords)
+    inf = sym.info()
+    ex = sym.export()
+    nr, ns = inf["n_reduced"], inf["nsuper"]
+    assert nr == g.n - 1
+    assert np.array_equal(np.sort(ex["perm"]), np.arange(nr))
+    first = ex["first"]
+    assert first[0] == 0 and first[-1] == nr and np.all(np.diff(first) > 0)
+    par = ex["parent"]
+    assert np.all((par == -1) | (par > np.arange(ns)))
+    lev = ex["level"]
+    for s in range(ns):
+        if par[s] != -1:
+            assert lev[par[s]] > lev[s]
+    assert inf["levels"] == lev.max() + 1
+    # roots have no rows below the diagonal; others do
+    assert np.all((par == -1) == (ex["nb"] == 0))
+    # the analysis counts at least as much executed work as walk work
+    assert inf["walk_fma"] >= inf["walk_entries"] > 0
+    assert inf["nnz_l"] >= inf["nnz_a"] + nr
+
+
+def test_walk_work_matches_a_direct_count(P):
+    """W from the analysis equals a count done here from the exported structure."""
+    g = I.grid2d(12, 12, seed=6)
+    sym = P.Symbolic.of(g)
+    inf, ex = sym.info(), sym.export()
+    first, par, nb = ex["first"], ex["parent"], ex["nb"]
+    pos = np.empty(g.n - 1, np.int64)
+    pos[ex["perm"]] = np.arange(g.n - 1)
+    col2sn = np.repeat(np.arange(first.size - 1), np.diff(first))
+
+    # rows of each supernode, rebuilt by brute force from the elimination of L_r's pattern
+    n1 = g.n - 1
+    A = np.zeros((n1, n1), bool)
+    rows = np.repeat(np.arange(g.n), np.diff(g.indptr))
+    for a, b in zip(rows, g.indices):
+        if a and b:
+            A[pos[a - 1], pos[b - 1]] = True
+    Lp = A.copy()
+    for k in range(n1):   # symbolic elimination
+        nzr = np.flatnonzero(Lp[k + 1:, k]) + k + 1
+        Lp[np.ix_(nzr, nzr)] = True
+    # supernode's rows below its columns: union of its columns' patterns
+    W = 0
+    u, v = g.all_edges()
+    for a, b in zip(u, v):
+        pa, pb = (pos[x - 1] if x else -1 for x in (a, b))
+        lo = max(pa, pb) if min(pa, pb) < 0 else min(pa, pb)
+        s = col2sn[lo]
+        fc = lo - first[s]
+        while s != -1:
+            nc = first[s + 1] - first[s]
+            np_ = nc - fc
+            W += np_ * (np_ - 1) // 2 + nb[s] * np_ + np_
+            if par[s] == -1:
+                break
+            # first non-zero column in the parent: the parent-local row of the smallest row
+            # below s
+            below = np.flatnonzero(Lp[first[s + 1]:, first[s + 1] - 1]) + first[s + 1]
+            fc = below[0] - first[par[s]]
+            s = par[s]
+    assert W == inf["walk_entries"]
+
+
+def test_all_edge_order_and_footprint(P):
+    g = I.grid32()
+    sym = P.Symbolic.of(g)
+    assert sym.nq == g.m
+    assert sym.footprint_bytes() > 8 * sym.info()["nnz_l"]

@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the all-edge effective-resistance sweep (PEERS implicit-inverse walk).
+
+One step = peers_query over every edge of the 1M-node 3-layer PDN mesh (3 x 577 x 577 5-point
+grids, vias every 4th node, conductances log-uniform 1e-2..1e2, seed 2, node 0 grounded):
+2 036 162 queries, each walked from its starting supernode to the root (§8 rows A1-A4).  The
+factor is resident before the timed region; `value` is edge queries per second of the device
+sweep, `e2e` the same metric through the public API with host buffers (conductances uploaded
+and factored, results copied back) inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank runs an independent replica on its own GPU (weak scaling);
+the sweep itself needs no collective.  `--impl reference` times the CPU oracle (tests'
+oracle/) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge queries/s, all-edge sweep (1M-node PDN grid, FP64)"
+UNIT = "queries/s"
+WORKLOAD = "pdn3x577x577_vias4_loguniform_1e-2_1e2_seed2_all_edges"
+HBM_FALLBACK_GBS = 6400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pdn1m", choices=["pdn1m", "grid32", "grid512"])
+    ap.add_argument("--cpu-sample", type=int, default=16000,
+                    help="edges in the oracle's CPU-baseline sample (0 = skip)")
+    ap.add_argument("--ref-sample", type=int, default=8000,
+                    help="edges per step of --impl reference")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def make_graph(name):
+    from paper_2606_31535_b300 import inputs as I
+    if name == "pdn1m":
+        return I.pdn1m()
+    if name == "grid512":
+        return I.grid2d(512, 512, seed=3, law="loguniform", lo=1e-2, hi=1e2)
+    return I.grid32()
+
+
+def workload_name(name):
+    return {"pdn1m": WORKLOAD, "grid32": "grid32x32_uniform_0.5_2_seed1_all_edges",
+            "grid512": "grid512x512_loguniform_seed3_all_edges"}[name]
+
+
+# ------------------------------------------------------------------ CPU oracle (host cores)
+
+def _oracle_sample(workload, sample, steps, warmup, seed, out_q):
+    """Runs in a spawned process: factors with the oracle (untimed), then times the per-query
+    path solves on `sample` seeded edges per step, on all host cores."""
+    import oracle
+    g = make_graph(workload)
+    t0 = time.time()
+    F = oracle.Factor.of(g)
+    t_fact = time.time() - t0
+    u, v = g.all_edges()
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(u.size, min(sample, u.size), replace=False)
+    cores = os.cpu_count() or 1
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        F.resistance(u[idx], v[idx], threads=cores)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+    out_q.put({"t_factor_s": t_fact, "times": times, "sample": int(idx.size), "cores": cores})
+
+
+def start_oracle(workload, sample, steps, warmup, seed):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_sample, args=(workload, sample, steps, warmup, seed, q))
+    p.start()
+    return p, q
+
+
+# ------------------------------------------------------------------ clocks
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def start_clocks(dev):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}",
+                              "--format=csv,noheader,nounits", "-i", str(dev), "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, f
+
+
+def stop_clocks(p, f):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    f.flush()
+    f.seek(0)
+    rows = [r.split(",") for r in f.read().strip().splitlines() if r.count(",") >= 8]
+    f.close()
+    os.unlink(f.name)
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                      and "Not" not in r[5 + i]})
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p, q = start_oracle(args.workload, args.ref_sample, args.steps, args.warmup, seed=7)
+    res = q.get()
+    p.join()
+    t = sum(res["times"])
+    value = res["sample"] * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.workload), "queries_per_step": res["sample"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "sample": f"{res['sample']} seeded edges per step (oracle factor "
+                                   f"{res['t_factor_s']:.1f} s, untimed)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    oracle_proc = None
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        # spawned before the first GPU call; runs on the host cores while the GPU works
+        oracle_proc = start_oracle(args.workload, args.cpu_sample, 1, 0, seed=11)
+
+    import torch
+    from paper_2606_31535_b300 import peers as P
+
+    g = make_graph(args.workload)
+    t0 = time.time()
+    sym = P.Symbolic.of(g)
+    t_analyze = time.time() - t0
+    info = sym.info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    ctx = P.Context(local, stream)
+    peaks64 = ctx.fp64_peaks()
+    fp64_peak = peaks64["dfma"]
+    num = P.Numeric(ctx, sym)
+    nq = sym.nq
+    R = torch.empty(nq, dtype=torch.float64, device=f"cuda:{local}")
+
+    for _ in range(args.warmup):
+        P.query(ctx, sym, num, R)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    barrier()
+    torch.cuda.synchronize()
+    clk = start_clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        P.query(ctx, sym, num, R)
+        launches += ctx.last_stats()["sweep_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = stop_clocks(*clk)
+    t = e0.elapsed_time(e1) * 1e-3
+    if dist is not None:
+        tt = torch.tensor([t], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    step_s = t / args.steps
+    value = nq * args.steps * world / t
+
+    sweep_stats = ctx.last_stats()
+    num.close()
+    # end to end through the public API: pinned conductances -> factor -> sweep -> host R
+    w_pin = torch.from_numpy(g.w).pin_memory()
+    r_pin = torch.empty(nq, dtype=torch.float64).pin_memory()
+    e2e_times, h2d, d2h = [], 0, 0
+    for _ in range(args.e2e_steps):
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        num2 = P.Numeric(ctx, sym, w_pin.numpy())
+        h2d = ctx.last_stats()["h2d_bytes"]
+        P.query(ctx, sym, num2, r_pin.numpy())
+        st = ctx.last_stats()
+        d2h = st["d2h_bytes"]
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        num2.close()
+        del num2
+    t_e2e = max(e2e_times)
+    if dist is not None:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    # the e2e result must equal the device-resident result
+    same = bool(np.array_equal(r_pin.numpy(), R.cpu().numpy()))
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    algo_flops = 2.0 * info["walk_entries"]          # per step
+    achieved_tf = algo_flops / step_s / 1e12
+    walk_gbs = 8.0 * info["walk_entries"] / step_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.workload), "n": g.n, "edges": nq,
+                   "queries_per_step": nq, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2: %.2f GB factor panels + %.1f GB query fronts"
+                         % (8e-9 * info["nnz_l"], 1e-9 * info["device_bytes"])},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak if fp64_peak else None,
+                     "traffic": None,
+                     "kernel": "k_sweep (FP64 DFMA; peak = DFMA throughput measured live; "
+                               "mma.sync f64 measured %.3f TFLOP/s)" % peaks64["dmma"],
+                     "algorithmic": "2 flops x W walk entries per step, W = %d" % info["walk_entries"]},
+        "hbm_walk": {"achieved_gbs": walk_gbs, "peak_gbs": hbm or HBM_FALLBACK_GBS,
+                     "frac": walk_gbs / (hbm or HBM_FALLBACK_GBS),
+                     "peak_source": "measured" if hbm else "fallback",
+                     "bytes_per_step": 8 * info["walk_entries"]},
+        "e2e": {"value": nq * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "includes": "factor + sweep",
+                "matches_device_result": same},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "analysis": {"t_analyze_s": t_analyze, "nsuper": info["nsuper"],
+                     "levels": info["levels"], "nnz_l": info["nnz_l"],
+                     "walk_fma": info["walk_fma"]},
+    }
+    if oracle_proc is not None:
+        p, q = oracle_proc
+        res = q.get()
+        p.join()
+        tq = res["times"][0]
+        line["cpu_baseline"] = {"value": res["sample"] / tq, "unit": UNIT, "cores": res["cores"],
+                                "kind": "oracle",
+                                "sample": f"{res['sample']} seeded edges of the same workload, "
+                                          f"per-query path solves timed (oracle factor "
+                                          f"{res['t_factor_s']:.1f} s untimed)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -144,21 +144,38 @@ void peers_free_numeric(peers_numeric *num);
 /* Effective resistance of every query of the plan into R[0 .. peers_num_queries(sym)), in the
  * plan's query order.  R is a device pointer when flags has PEERS_OUT_DEVICE, else a host
  * pointer.  One launch per level of the supernodal etree walks every query from its starting
- * supernode to the root (eq. 16-18 over the etree path of Lemma 1).
+ * supernode to the root (eq. 16-18 over the etree path of Lemma 1).  A pair whose endpoints'
+ * etree paths only meet above the lower endpoint's supernode (a listed non-edge pair) is
+ * walked as two branches that merge at their lowest common supernode, with one more small
+ * launch per wave to combine the branches' sums.
  * Errors: PEERS_EINVAL, PEERS_ENOMEM, PEERS_ECUDA. */
 int peers_query(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num, double *R,
                 int flags);
 
-/* Device seconds of the last peers_query / peers_factor on this context, split per kernel
- * class: out[0] = sweep total, out[1] = largest single sweep launch, out[2] = factor total.
- * Filled only when timing was enabled with peers_set_timing(ctx, 1). */
+/* Counters of the last peers_factor / peers_query on a context.  Device times are filled only
+ * while timing is enabled (peers_set_timing(ctx, 1)); counts and bytes always. */
+typedef struct peers_stats {
+  double sweep_s;          /* device seconds of the sweep launches of the last peers_query */
+  double max_launch_s;     /* longest single sweep launch */
+  double factor_s;         /* device seconds of the last peers_factor */
+  int64_t sweep_launches;  /* kernels launched by the last peers_query */
+  int64_t factor_launches; /* kernels launched by the last peers_factor */
+  int64_t h2d_bytes;       /* host-to-device bytes of the last peers_factor + peers_query */
+  int64_t d2h_bytes;       /* device-to-host bytes of the last peers_query (+ factor status) */
+} peers_stats;
 int peers_set_timing(peers_ctx *ctx, int enable);
-int peers_last_timing(const peers_ctx *ctx, double out[3]);
+int peers_last_stats(const peers_ctx *ctx, peers_stats *out);
 
 /* Device milliseconds of each sweep launch (one per etree level) of the last timed
  * peers_query, summed over waves, into ms[0 .. min(levels, cap)).  Returns the level count or
  * a negative status. */
 int peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap);
+
+/* Measures the FP64 throughput of the context's device with short register-only kernels
+ * (about 50 ms): tflops[0] = DFMA on the CUDA cores, tflops[1] = mma.sync m8n8k4 f64 (the
+ * FP64 tensor path), both in TFLOP/s with 2 flops per multiply-add.  tflops[0] is the sweep's
+ * roofline denominator: the sweep is bound by FP64 FMA throughput. */
+int peers_fp64_peak(peers_ctx *ctx, double tflops[2]);
 
 /* ---- misc ------------------------------------------------------------------------------- */
 const char *peers_strerror(int status);

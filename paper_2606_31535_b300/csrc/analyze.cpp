@@ -696,7 +696,9 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   }
   S.nq = nq;
   struct Rec { int32_t s0, a, b; int64_t idx; };
+  struct Two { int32_t lo, hi; int64_t idx; };
   std::vector<Rec> recs;
+  std::vector<Two> twos;
   recs.reserve(static_cast<size_t>(nq));
   S.nq_trivial = 0;
   S.nq_two = 0;
@@ -719,8 +721,8 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
       } else {
         auto rb = S.rows.begin() + S.rows_off[s0], re = S.rows.begin() + S.rows_off[s0 + 1];
         auto it = std::lower_bound(rb, re, hi);
-        if (it == re || *it != hi) {
-          S.nq_two++;
+        if (it == re || *it != hi) {   // paths meet above s0: two-branch walk
+          twos.push_back({lo, hi, i});
           continue;
         }
         b = nc + static_cast<int32_t>(it - rb);
@@ -728,13 +730,7 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     }
     recs.push_back({s0, lo - f, b, i});
   }
-  if (S.nq_two > 0) {
-    err = std::to_string(S.nq_two) +
-          " queries are pairs whose etree paths only meet above their starting supernode; "
-          "this build walks single paths (every graph edge and every pair touching the "
-          "ground qualifies)";
-    return PEERS_EINVAL;
-  }
+  S.nq_two = static_cast<int64_t>(twos.size());
   std::sort(recs.begin(), recs.end(), [](const Rec &x, const Rec &y) {
     if (x.s0 != y.s0) return x.s0 < y.s0;
     if (x.a != y.a) return x.a < y.a;
@@ -742,9 +738,10 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     return x.idx < y.idx;
   });
   S.nsorted = static_cast<int64_t>(recs.size());
-  S.qorig.resize(recs.size());
-  S.qa.resize(recs.size());
-  S.qb.resize(recs.size());
+  const int64_t nslots = S.nsorted + 2 * S.nq_two;
+  S.qorig.resize(static_cast<size_t>(nslots));
+  S.qa.resize(static_cast<size_t>(nslots));
+  S.qb.resize(static_cast<size_t>(nslots));
   S.qbeg.assign(static_cast<size_t>(ns) + 1, 0);
   for (size_t k = 0; k < recs.size(); ++k) {
     S.qorig[k] = recs[k].idx;
@@ -844,6 +841,118 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     }
     S.waves.push_back(std::move(W));
     if (S.nsorted == 0) break;
+  }
+  if (S.nsorted == 0 && S.nq_two > 0) S.waves.clear();
+
+  // ---- two-branch walk (listed pairs whose etree paths merge above the start) ----
+  // Slots nsorted + 2k (branch of the lower endpoint, continues after the merge) and
+  // nsorted + 2k + 1 (branch of the upper endpoint, ends at the merge supernode).
+  S.ldesc.clear();
+  S.two_user.clear();
+  S.two_a.clear();
+  S.two_b.clear();
+  if (S.nq_two > 0) {
+    std::vector<int32_t> depth(static_cast<size_t>(ns), 0);
+    for (int32_t s = ns - 1; s >= 0; --s)
+      depth[s] = S.parent[s] == -1 ? 0 : depth[S.parent[s]] + 1;
+    const int64_t per_two = std::max<int64_t>(1, per_wave / 2);
+    const int32_t kInf = INT32_MAX;
+    for (int64_t k0 = 0; k0 < S.nq_two; k0 += per_two) {
+      const int64_t k1 = std::min<int64_t>(S.nq_two, k0 + per_two);
+      std::vector<std::pair<int32_t, SweepDesc>> steps;   // (supernode, step)
+      for (int64_t k = k0; k < k1; ++k) {
+        const Two &t = twos[k];
+        const int32_t sa = S.col2sn[t.lo], sb = S.col2sn[t.hi];
+        const int32_t A = static_cast<int32_t>(S.nsorted + 2 * k), B = A + 1;
+        S.qorig[A] = S.qorig[B] = t.idx;
+        S.qa[A] = t.lo - S.first[sa];
+        S.qb[A] = -1;
+        S.qa[B] = -1;
+        S.qb[B] = t.hi - S.first[sb];
+        // merge supernode = lowest common ancestor of sa and sb (-1: different trees)
+        int32_t x = sa, y = sb;
+        while (x != y && x != -1 && y != -1) {
+          if (depth[x] >= depth[y]) x = S.parent[x]; else y = S.parent[y];
+        }
+        const int32_t m = (x == y) ? x : -1;
+        int32_t prev = -1;
+        for (int32_t p = sa; p != m; prev = p, p = S.parent[p])
+          steps.push_back({p, SweepDesc{A, prev, -1, -1, -1}});
+        const int32_t child_a = prev;
+        prev = -1;
+        if (sb != m)
+          for (int32_t p = sb; p != m; prev = p, p = S.parent[p])
+            steps.push_back({p, SweepDesc{B, prev, -1, -1, -1}});
+        const int32_t child_b = prev;
+        if (m != -1) {
+          if (sb == m)
+            steps.push_back({m, SweepDesc{A, child_a, -1, -1, t.hi - S.first[m]}});
+          else
+            steps.push_back({m, SweepDesc{A, child_a, B, child_b, -1}});
+          prev = m;
+          for (int32_t p = S.parent[m]; p != -1; prev = p, p = S.parent[p])
+            steps.push_back({p, SweepDesc{A, prev, -1, -1, -1}});
+        }
+        S.two_user.push_back(t.idx);
+        S.two_a.push_back(A);
+        S.two_b.push_back(m == -1 ? B : -1);
+      }
+      std::stable_sort(steps.begin(), steps.end(), [&](const auto &u, const auto &v) {
+        if (S.level[u.first] != S.level[v.first]) return S.level[u.first] < S.level[v.first];
+        return u.first < v.first;
+      });
+      SweepWave W;
+      W.q_begin = S.nsorted + 2 * k0;
+      W.q_end = S.nsorted + 2 * k1;
+      W.two_begin = k0;
+      W.two_end = k1;
+      S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
+      W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+      W.level_smem.assign(static_cast<size_t>(S.nlevels), 0);
+      auto first_row = [&](const SweepDesc &d) -> int32_t {
+        int32_t r = kInf;
+        if (d.src_a >= 0) r = S.rmap[S.rows_off[d.src_a]];
+        else {
+          if (S.qa[d.a] >= 0) r = std::min(r, S.qa[d.a]);
+          if (S.qb[d.a] >= 0) r = std::min(r, S.qb[d.a]);
+        }
+        if (d.b >= 0) r = std::min(r, S.rmap[S.rows_off[d.src_b]]);
+        else if (d.seed_b >= 0) r = std::min(r, d.seed_b);
+        return r;
+      };
+      size_t i = 0;
+      for (int32_t l = 0; l < S.nlevels; ++l) {
+        while (i < steps.size() && S.level[steps[i].first] == l) {
+          const int32_t p = steps[i].first;
+          size_t e = i;
+          while (e < steps.size() && steps[e].first == p) ++e;
+          for (size_t c = i; c < e; c += S.qtile[p]) {
+            const size_t ce = std::min(e, c + static_cast<size_t>(S.qtile[p]));
+            SweepItem it{};
+            it.s = p;
+            it.src = -1;
+            it.kind = 1;
+            it.q0 = static_cast<int32_t>(S.ldesc.size());
+            it.nq = static_cast<int32_t>(ce - c);
+            int32_t j0 = kInf;
+            for (size_t q = c; q < ce; ++q) {
+              const int32_t fr = first_row(steps[q].second);
+              j0 = std::min(j0, fr);
+              S.walk_entries += entries(p, fr);
+              S.ldesc.push_back(steps[q].second);
+            }
+            it.j0 = (j0 / kBlock) * kBlock;
+            S.walk_fma += it.nq * item_fma(p, it.j0);
+            W.items.push_back(it);
+            W.level_smem[l] = std::max(W.level_smem[l],
+                                       sweep_smem_bytes(sn_nc(S, p) + S.nb[p], it.nq));
+          }
+          i = e;
+        }
+        W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
+      }
+      S.waves.push_back(std::move(W));
+    }
   }
   S.t_queries = since(t2);
   return PEERS_OK;

@@ -20,7 +20,7 @@ struct peers_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   bool timing = false;
-  double times[3] = {0, 0, 0};
+  peers_stats stats{};
   std::vector<double> level_ms;
 };
 
@@ -32,6 +32,7 @@ struct peers_numeric {
   int device = 0;
   const peers_symbolic *sym = nullptr;   // not owned; must outlive this handle
   std::vector<void *> allocs;
+  int64_t h2d_bytes = 0;   // bytes uploaded while building this handle
   // factor
   double *panel = nullptr, *tinv = nullptr, *d = nullptr, *dinv = nullptr;
   int32_t *first = nullptr, *nb = nullptr, *rmap = nullptr;
@@ -40,6 +41,9 @@ struct peers_numeric {
   int32_t *qa = nullptr, *qb = nullptr;
   int64_t *qorig = nullptr;
   SweepItem *items = nullptr;
+  peers::SweepDesc *ldesc = nullptr;
+  int64_t *two_user = nullptr;
+  int32_t *two_a = nullptr, *two_b = nullptr;
   std::vector<int64_t> wave_item_off;
   double *carry = nullptr, *racc = nullptr, *Rdev = nullptr;
 };
@@ -74,6 +78,7 @@ int upload(peers_numeric *num, T **p, const std::vector<T> &v, cudaStream_t st, 
   int rc = dalloc(num, p, static_cast<int64_t>(v.size()), err);
   if (rc != PEERS_OK || v.empty()) return rc;
   CUDA_TRY(cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  num->h2d_bytes += static_cast<int64_t>(sizeof(T) * v.size());
   return PEERS_OK;
 }
 
@@ -139,13 +144,15 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
-  int rc = peers::run_factor(S, D, st, err);
+  int64_t launches = 0;
+  int rc = peers::run_factor(S, D, st, &launches, err);
+  ctx->stats.factor_launches = launches;
   if (ctx->timing) {
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    ctx->times[2] = ms * 1e-3;
+    ctx->stats.factor_s = ms * 1e-3;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
@@ -167,7 +174,13 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
     all.insert(all.end(), W.items.begin(), W.items.end());
   }
   TRY(upload(num, &num->items, all, st, err));
+  TRY(upload(num, &num->ldesc, S.ldesc, st, err));
+  TRY(upload(num, &num->two_user, S.two_user, st, err));
+  TRY(upload(num, &num->two_a, S.two_a, st, err));
+  TRY(upload(num, &num->two_b, S.two_b, st, err));
   CUDA_TRY(cudaStreamSynchronize(st));
+  ctx->stats.h2d_bytes = num->h2d_bytes;
+  ctx->stats.d2h_bytes = 2 * sizeof(int);
   return PEERS_OK;
 }
 
@@ -200,6 +213,7 @@ int query_impl(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, do
   a.qa = num->qa;
   a.qb = num->qb;
   a.qorig = num->qorig;
+  a.ldesc = num->ldesc;
   a.carry = num->carry;
   a.racc = num->racc;
   a.R = Rout;
@@ -209,25 +223,38 @@ int query_impl(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, do
     ev.resize(2 * static_cast<size_t>(S.nlevels));
     for (auto &e : ev) cudaEventCreate(&e);
     ctx->level_ms.assign(static_cast<size_t>(S.nlevels), 0.0);
-    ctx->times[0] = ctx->times[1] = 0;
+    ctx->stats.sweep_s = ctx->stats.max_launch_s = 0;
   }
-  for (size_t w = 0; w < S.waves.size() && S.nsorted > 0; ++w) {
-    TRY(peers::run_sweep_wave(S, S.waves[w], num->items + num->wave_item_off[w], a, st,
-                              ctx->timing ? ev.data() : nullptr, err));
+  int64_t launches = 0;
+  for (size_t w = 0; w < S.waves.size() && S.nsorted + S.nq_two > 0; ++w) {
+    const peers::SweepWave &W = S.waves[w];
+    TRY(peers::run_sweep_wave(S, W, num->items + num->wave_item_off[w], a, st,
+                              ctx->timing ? ev.data() : nullptr, &launches, err));
+    if (W.two_end > W.two_begin) {
+      peers::SweepArgs c = a;
+      c.wave_base = W.q_begin;
+      TRY(peers::run_two_branch_combine(c, num->two_user, num->two_a, num->two_b, W.two_begin,
+                                        W.two_end, st, &launches, err));
+    }
     if (ctx->timing) {
       CUDA_TRY(cudaStreamSynchronize(st));
       for (int32_t l = 0; l < S.nlevels; ++l) {
         float ms = 0;
         cudaEventElapsedTime(&ms, ev[2 * l], ev[2 * l + 1]);
         ctx->level_ms[l] += ms;
-        ctx->times[0] += ms * 1e-3;
-        ctx->times[1] = std::max(ctx->times[1], ms * 1e-3);
+        ctx->stats.sweep_s += ms * 1e-3;
+        ctx->stats.max_launch_s = std::max(ctx->stats.max_launch_s, ms * 1e-3);
       }
     }
   }
   for (auto &e : ev) cudaEventDestroy(e);
-  if (host_out && S.nq > 0)
+  ctx->stats.sweep_launches = launches;
+  ctx->stats.d2h_bytes = 0;
+  ctx->stats.h2d_bytes = 0;
+  if (host_out && S.nq > 0) {
     CUDA_TRY(cudaMemcpyAsync(R, Rout, sizeof(double) * S.nq, cudaMemcpyDeviceToHost, st));
+    ctx->stats.d2h_bytes = static_cast<int64_t>(sizeof(double)) * S.nq;
+  }
   CUDA_TRY(cudaStreamSynchronize(st));
   CUDA_TRY(cudaGetLastError());
   return PEERS_OK;
@@ -432,10 +459,21 @@ int peers_set_timing(peers_ctx *ctx, int enable) {
   return PEERS_OK;
 }
 
-int peers_last_timing(const peers_ctx *ctx, double out[3]) {
+int peers_last_stats(const peers_ctx *ctx, peers_stats *out) {
   if (!ctx || !out) return fail(PEERS_EINVAL, "null argument");
-  for (int i = 0; i < 3; ++i) out[i] = ctx->times[i];
+  *out = ctx->stats;
   return PEERS_OK;
+}
+
+int peers_fp64_peak(peers_ctx *ctx, double tflops[2]) {
+  if (!ctx || !tflops) return fail(PEERS_EINVAL, "null argument");
+  std::string err;
+  auto run = [&]() -> int {
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    return peers::fp64_peak(ctx->stream, tflops, err);
+  };
+  int rc = run();
+  return rc == PEERS_OK ? rc : fail(rc, err);
 }
 
 int peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap) {

@@ -49,6 +49,7 @@ struct SweepArgs {
   const int64_t *panel_off, *tinv_off, *rows_off;
   const int32_t *qa, *qb;
   const int64_t *qorig;
+  const SweepDesc *ldesc;   // two-branch walk steps (kind-1 items)
   double *carry;   // carry_slots x nbmax: the B-part of each query's front, slot-major
   double *racc;    // carry_slots: running sum_k y_k^2 / d_k of each query
   double *R;       // nq results in the caller's query order
@@ -56,12 +57,24 @@ struct SweepArgs {
   int64_t wave_base;
 };
 
-int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, std::string &err);
+// Runs the whole factorization on `stream`; adds the number of kernels launched to *launches.
+int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, int64_t *launches,
+               std::string &err);
 
 // Launches the sweep of one wave, level by level.  If `events` is non-null it must hold
 // 2 * nlevels events; launch l is bracketed by events[2l], events[2l+1].
 int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_items,
                    const SweepArgs &args, cudaStream_t stream, cudaEvent_t *events,
-                   std::string &err);
+                   int64_t *launches, std::string &err);
+
+// Finishes the two-branch queries [k0, k1) of a wave: R[user] = r of slot a (+ r of slot b
+// when the two branches end in different etree roots).
+int run_two_branch_combine(const SweepArgs &args, const int64_t *two_user, const int32_t *two_a,
+                           const int32_t *two_b, int64_t k0, int64_t k1, cudaStream_t stream,
+                           int64_t *launches, std::string &err);
+
+// FP64 throughput probes (TFLOP/s) on the current device: out[0] DFMA (CUDA cores),
+// out[1] mma.sync m8n8k4 f64 (the FP64 tensor path).
+int fp64_peak(cudaStream_t stream, double out[2], std::string &err);
 
 }  // namespace peers

@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
 }
 
 // Host driver: the full factorization on `stream`.  Returns a PEERS_* status.
-int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, std::string &err) {
+int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, int64_t *launches,
+               std::string &err) {
   FactorArgs a = D.args;
   CUDA_TRY(cudaMemsetAsync(a.panel, 0, sizeof(double) * S.panel_total, stream));
   if (S.u_total > 0) CUDA_TRY(cudaMemsetAsync(a.U, 0, sizeof(double) * S.u_total, stream));
@@ -207,7 +208,10 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, st
   {
     const int64_t cnt = static_cast<int64_t>(S.a_dest.size());
     const int blocks = static_cast<int>(std::min<int64_t>((cnt + 255) / 256, 148 * 16));
-    if (cnt > 0) k_assemble<<<blocks, 256, 0, stream>>>(D.a_dest, D.a_val, cnt, a.panel);
+    if (cnt > 0) {
+      k_assemble<<<blocks, 256, 0, stream>>>(D.a_dest, D.a_val, cnt, a.panel);
+      ++*launches;
+    }
     CUDA_TRY(cudaGetLastError());
   }
   for (int32_t l = 0; l < S.nlevels; ++l) {
@@ -221,6 +225,7 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, st
       if (maxnb == 0) continue;
       dim3 grid(static_cast<unsigned>(p1 - p0), static_cast<unsigned>((maxnb + 7) / 8));
       k_extend_add<<<grid, 256, 0, stream>>>(D.ea_pairs + 2 * p0, a);
+      ++*launches;
       CUDA_TRY(cudaGetLastError());
     }
     // 2. right-looking column blocks
@@ -229,6 +234,7 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, st
       const int32_t na = static_cast<int32_t>(S.trail_na[tp]);
       if (na == 0) continue;
       k_diag_block<<<na, 32, 0, stream>>>(sns, J, a);
+      ++*launches;
       CUDA_TRY(cudaGetLastError());
       int32_t maxrows = 0;
       for (int32_t i = 0; i < na; ++i) {
@@ -239,12 +245,14 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, st
       if (maxrows > 0) {
         dim3 grid(static_cast<unsigned>(na), static_cast<unsigned>((maxrows + 127) / 128));
         k_panel_rows<<<grid, 128, 0, stream>>>(sns, J, a);
+        ++*launches;
         CUDA_TRY(cudaGetLastError());
       }
       const int64_t ntiles = S.trail_prefix[S.trail_off[tp] + na];
       if (ntiles > 0) {
         k_trailing<<<static_cast<unsigned>(ntiles), 256, 0, stream>>>(
             sns, J, D.trail_prefix + S.trail_off[tp], na, a);
+        ++*launches;
         CUDA_TRY(cudaGetLastError());
       }
     }

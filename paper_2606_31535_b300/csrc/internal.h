@@ -38,22 +38,34 @@ PEERS_HD inline int64_t sweep_smem_bytes(int64_t N, int64_t Q) {
   return (N + 2 * kBlock) * sweep_qstride(Q) * 8;
 }
 
-// One unit of sweep work: queries [q0, q0+nq) of the sorted query order at supernode s.
-// src >= 0: the queries arrive from child supernode src (their carries are scattered through
-// src's relative map); src == -1: the queries start at s (seeded with +1/-1).
+// One unit of sweep work at supernode s.
+//   kind 0 (range): the query slots [q0, q0+nq) of the sorted order.  src >= 0: they arrive
+//     from child supernode src (their carries are scattered through src's relative map);
+//     src == -1: they start at s (seeded with +1 at qa, -1 at qb).
+//   kind 1 (list): nq entries ldesc[q0 .. q0+nq) of the two-branch walk (see SweepDesc).
 struct SweepItem {
   int32_t s;
   int32_t src;
   int32_t q0;
   int32_t nq;
   int32_t j0;   // first column block (block-aligned) with a non-zero right-hand side
-  int32_t pad;
+  int32_t kind;
+};
+
+// One query step of the two-branch walk (a listed pair whose endpoints' etree paths meet
+// only above the lower endpoint's supernode).  The front of slot `a` comes from child `src_a`
+// (or its seed when src_a == -1); when `b` >= 0 the carry of slot b from child src_b is added
+// (the two branches merge here); when b == -1 and seed_b >= 0, -1 is added at local row
+// seed_b (the upper endpoint's column lies in this supernode).  The result goes to slot a.
+struct SweepDesc {
+  int32_t a, src_a, b, src_b, seed_b;
 };
 
 // One wave of the sweep: the queries [q_begin, q_end) of the sorted order, walked to the
 // root level by level.  items[level_ptr[l] .. level_ptr[l+1]) are the level's items.
 struct SweepWave {
   int64_t q_begin, q_end;
+  int64_t two_begin = 0, two_end = 0;   // two-branch queries finished by this wave (combine)
   std::vector<int64_t> level_ptr;
   std::vector<int64_t> level_smem;   // dynamic shared memory of the level's launch
   std::vector<SweepItem> items;
@@ -126,6 +138,11 @@ struct Symbolic {
   std::vector<int32_t> qtile;       // tile size (queries per CTA) per supernode
   int32_t nbmax = 0;
   std::vector<SweepWave> waves;
+  // two-branch walk: step descriptors, and per such query (user index, slot a, slot b of a
+  // branch that ends in another etree root or -1) for the final combine
+  std::vector<SweepDesc> ldesc;
+  std::vector<int64_t> two_user;
+  std::vector<int32_t> two_a, two_b;
   int64_t carry_slots = 0;          // slots of the carry buffer (largest wave)
   int64_t walk_entries = 0, walk_fma = 0;
   double t_order = 0, t_symbolic = 0, t_queries = 0;

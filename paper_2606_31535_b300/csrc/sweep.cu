@@ -45,7 +45,35 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepItem *__rest
   for (int64_t idx = int64_t(j0) * QP + tid; idx < int64_t(N) * QP; idx += kSweepThreads)
     X[idx] = 0.0;
   __syncthreads();
-  if (it.src >= 0) {
+  if (it.kind == 1) {
+    // two-branch walk steps: per entry its own source (child carry or seed) ...
+    const int warp = tid / 32, lane = tid % 32;
+    for (int q = warp; q < Q; q += kSweepThreads / 32) {
+      const SweepDesc d = a.ldesc[it.q0 + q];
+      const int64_t sa = int64_t(d.a) - a.wave_base;
+      if (d.src_a >= 0) {
+        const int32_t nbc = a.nb[d.src_a];
+        const int32_t *rm = a.rmap + a.rows_off[d.src_a];
+        for (int32_t t = lane; t < nbc; t += 32) X[rm[t] * QP + q] = a.carry[sa * a.nbmax + t];
+      } else if (lane == 0) {
+        if (a.qa[d.a] >= 0) X[a.qa[d.a] * QP + q] = 1.0;
+        if (a.qb[d.a] >= 0) X[a.qb[d.a] * QP + q] = -1.0;
+      }
+    }
+    __syncthreads();
+    // ... plus, where the two branches merge, the other branch's carry or the -1 seed
+    for (int q = warp; q < Q; q += kSweepThreads / 32) {
+      const SweepDesc d = a.ldesc[it.q0 + q];
+      if (d.b >= 0) {
+        const int64_t sb = int64_t(d.b) - a.wave_base;
+        const int32_t nbc = a.nb[d.src_b];
+        const int32_t *rm = a.rmap + a.rows_off[d.src_b];
+        for (int32_t t = lane; t < nbc; t += 32) X[rm[t] * QP + q] += a.carry[sb * a.nbmax + t];
+      } else if (d.seed_b >= 0 && lane == 0) {
+        X[d.seed_b * QP + q] -= 1.0;
+      }
+    }
+  } else if (it.src >= 0) {
     // queries arriving from child src: scatter its carried B-part into this front
     const int32_t nbc = a.nb[it.src];
     const int32_t *rm = a.rmap + a.rows_off[it.src];
@@ -57,9 +85,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepItem *__rest
   } else {
     // queries starting here: e_lo - e_hi in local rows (eq. 4: no -1 when hi is the ground)
     for (int32_t q = tid; q < Q; q += kSweepThreads) {
-      X[a.qa[it.q0 + q] * QP + q] = 1.0;
-      const int32_t b = a.qb[it.q0 + q];
-      if (b >= 0) X[b * QP + q] = -1.0;
+      const int32_t qa = a.qa[it.q0 + q], qb = a.qb[it.q0 + q];
+      if (qa >= 0) X[qa * QP + q] = 1.0;
+      if (qb >= 0) X[qb * QP + q] = -1.0;
     }
   }
 
@@ -121,6 +149,22 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepItem *__rest
     }
   }
   __syncthreads();
+  if (it.kind == 1) {
+    // two-branch steps keep their running sum in slot a; the combine kernel writes R
+    const int warp = tid / 32, lane = tid % 32;
+    for (int q = warp; q < Q; q += kSweepThreads / 32) {
+      const int64_t sa = int64_t(a.ldesc[it.q0 + q].a) - a.wave_base;
+      for (int32_t t = lane; t < nbv; t += 32) a.carry[sa * a.nbmax + t] = X[(nc + t) * QP + q];
+    }
+    if (tid < Q) {
+      const SweepDesc d = a.ldesc[it.q0 + tid];
+      double tot = r;
+      if (d.src_a >= 0) tot += a.racc[int64_t(d.a) - a.wave_base];
+      if (d.b >= 0) tot += a.racc[int64_t(d.b) - a.wave_base];
+      a.racc[int64_t(d.a) - a.wave_base] = tot;
+    }
+    return;
+  }
   if (nbv > 0) {
     double *cout = a.carry + (int64_t(it.q0) - a.wave_base) * a.nbmax;
     for (int32_t idx = tid; idx < Q * nbv; idx += kSweepThreads) {
@@ -141,7 +185,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepItem *__rest
 
 int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_items,
                    const SweepArgs &args, cudaStream_t stream, cudaEvent_t *events,
-                   std::string &err) {
+                   int64_t *launches, std::string &err) {
   static int configured_smem = 0;   // per process; the kernel's limit only grows
   int64_t need = 0;
   for (int64_t b : W.level_smem) need = std::max(need, b);
@@ -158,10 +202,103 @@ int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_ite
     if (i1 > i0) {
       k_sweep<<<static_cast<unsigned>(i1 - i0), kSweepThreads, W.level_smem[l], stream>>>(
           d_items + i0, a);
+      ++*launches;
       CUDA_TRY(cudaGetLastError());
     }
     if (events) CUDA_TRY(cudaEventRecord(events[2 * l + 1], stream));
   }
+  return PEERS_OK;
+}
+
+__global__ void k_two_branch_combine(const int64_t *__restrict__ user, const int32_t *__restrict__ sa,
+                                     const int32_t *__restrict__ sb, int64_t k0, int64_t k1,
+                                     SweepArgs a) {
+  const int64_t k = k0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (k >= k1) return;
+  double r = a.racc[int64_t(sa[k]) - a.wave_base];
+  if (sb[k] >= 0) r += a.racc[int64_t(sb[k]) - a.wave_base];
+  a.R[user[k]] = r;
+}
+
+int run_two_branch_combine(const SweepArgs &args, const int64_t *two_user, const int32_t *two_a,
+                           const int32_t *two_b, int64_t k0, int64_t k1, cudaStream_t stream,
+                           int64_t *launches, std::string &err) {
+  if (k1 <= k0) return PEERS_OK;
+  const unsigned blocks = static_cast<unsigned>((k1 - k0 + 255) / 256);
+  k_two_branch_combine<<<blocks, 256, 0, stream>>>(two_user, two_a, two_b, k0, k1, args);
+  ++*launches;
+  CUDA_TRY(cudaGetLastError());
+  return PEERS_OK;
+}
+
+// Register-only DFMA chains: 8 independent accumulators per thread.
+__global__ void k_fp64_peak(double *out, int iters, double b, double c) {
+  double a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+  double a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+    a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+__device__ __forceinline__ void dmma_m8n8k4(double &d0, double &d1, double x, double y) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d0), "+d"(d1)
+               : "d"(x), "d"(y));
+}
+
+// Four independent m8n8k4 FP64 MMA chains per warp.
+__global__ void k_dmma_peak(double *out, int iters, double x, double y) {
+  double c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, c6 = 0, c7 = 0;
+  for (int i = 0; i < iters; ++i) {
+    dmma_m8n8k4(c0, c1, x, y);
+    dmma_m8n8k4(c2, c3, x, y);
+    dmma_m8n8k4(c4, c5, x, y);
+    dmma_m8n8k4(c6, c7, x, y);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = c0 + c1 + c2 + c3 + c4 + c5 + c6 + c7;
+}
+
+int fp64_peak(cudaStream_t stream, double out2[2], std::string &err) {
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 4, threads = 256, iters = 4096;
+  double *out = nullptr;
+  CUDA_TRY(cudaMalloc(&out, sizeof(double) * blocks * threads));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 0.0, best_mma = 0.0;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, stream);
+    k_fp64_peak<<<blocks, threads, 0, stream>>>(out, iters, 1.0000001, 1e-9);
+    cudaEventRecord(e1, stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms > 0) best = std::max(best, 2.0 * 8 * iters * double(blocks) * threads / (ms * 1e9));
+  }
+  for (int rep = 0; rep < 4; ++rep) {
+    const int mthreads = 128, miters = 1024;
+    cudaEventRecord(e0, stream);
+    k_dmma_peak<<<blocks, mthreads, 0, stream>>>(out, miters, 1.0, 1.0);
+    cudaEventRecord(e1, stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    // 4 MMAs of 8x8x4 per iteration per warp, 2 flops per multiply-add
+    const double flops = 2.0 * 8 * 8 * 4 * 4 * double(miters) * blocks * (mthreads / 32);
+    if (rep > 0 && ms > 0) best_mma = std::max(best_mma, flops / (ms * 1e9));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaGetLastError();
+  cudaFree(out);
+  if (e != cudaSuccess) { err = cudaGetErrorString(e); return PEERS_ECUDA; }
+  out2[0] = best;
+  out2[1] = best_mma;
   return PEERS_OK;
 }
 

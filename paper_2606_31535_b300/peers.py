@@ -34,6 +34,16 @@ class Options(ctypes.Structure):
                 ("relax_frac", ctypes.c_double), ("reserved", ctypes.c_int64 * 8)]
 
 
+class Stats(ctypes.Structure):
+    _fields_ = [("sweep_s", ctypes.c_double), ("max_launch_s", ctypes.c_double),
+                ("factor_s", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
+                ("factor_launches", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Info(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n", "n_reduced", "nnz_a", "nnz_l", "nsuper", "levels", "max_nc", "max_nb", "nq",
@@ -71,7 +81,8 @@ def load(path: str | None = None):
         "peers_free_numeric": (None, [vp]),
         "peers_query": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
-        "peers_last_timing": (ctypes.c_int, [vp, P(dbl)]),
+        "peers_last_stats": (ctypes.c_int, [vp, P(Stats)]),
+        "peers_fp64_peak": (ctypes.c_int, [vp, P(dbl)]),
         "peers_last_level_times": (ctypes.c_int, [vp, P(dbl), i64]),
         "peers_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "peers_last_error": (ctypes.c_char_p, []),
@@ -128,10 +139,16 @@ class Context:
     def set_timing(self, on: bool = True):
         _check(load().peers_set_timing(self._h, int(on)), "peers_set_timing")
 
-    def last_timing(self) -> dict:
-        out = (ctypes.c_double * 3)()
-        _check(load().peers_last_timing(self._h, out), "peers_last_timing")
-        return {"sweep_s": out[0], "max_launch_s": out[1], "factor_s": out[2]}
+    def last_stats(self) -> dict:
+        st = Stats()
+        _check(load().peers_last_stats(self._h, ctypes.byref(st)), "peers_last_stats")
+        return st.as_dict()
+
+    def fp64_peaks(self) -> dict:
+        """Measured FP64 throughput (TFLOP/s): DFMA and mma.sync m8n8k4 f64."""
+        out = (ctypes.c_double * 2)()
+        _check(load().peers_fp64_peak(self._h, out), "peers_fp64_peak")
+        return {"dfma": out[0], "dmma": out[1]}
 
     def last_level_times(self) -> np.ndarray:
         buf = (ctypes.c_double * 4096)()

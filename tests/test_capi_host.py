@@ -159,3 +159,22 @@ def test_all_edge_order_and_footprint(P):
     sym = P.Symbolic.of(g)
     assert sym.nq == g.m
     assert sym.footprint_bytes() > 8 * sym.info()["nnz_l"]
+
+
+def test_two_branch_pairs_are_planned(P):
+    g = I.grid2d(30, 30, seed=1)
+    u, v = I.random_pairs(g.n, 500, seed=3)
+    inf = P.Symbolic.of(g, qu=u, qv=v).info()
+    assert inf["nq"] == 500
+    assert 0 < inf["nq_two_branch"] <= 500
+    assert inf["walk_fma"] >= inf["walk_entries"] > 0
+
+
+def test_wave_budget_option(P):
+    g = I.grid2d(20, 20, seed=2)
+    opt = P.Options()
+    opt.reserved[0] = 64 * 1024
+    small = P.Symbolic.of(g, options=opt)
+    big = P.Symbolic.of(g)
+    assert small.footprint_bytes() < big.footprint_bytes()
+    assert small.info()["walk_entries"] == big.info()["walk_entries"]

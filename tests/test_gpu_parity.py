@@ -148,3 +148,58 @@ def test_pdn_1m_sampled_parity_and_foster(P, ctx, oracle_mod):
     F = oracle_mod.Factor.of(g)
     Ro = F.resistance(u[idx], v[idx])
     assert maxrel(R[idx], Ro) <= TOL
+
+
+def test_listed_pairs_two_branch_walk(P, ctx, oracle_mod):
+    """Non-edge pairs whose etree paths merge above the lower endpoint's supernode (row A5)."""
+    g = I.grid2d(40, 41, seed=20, law="loguniform", lo=1e-2, hi=1e2)
+    pu, pv = I.random_pairs(g.n, 3000, seed=21)
+    u, v = g.all_edges()
+    qu = np.concatenate([pu, u[:500]])
+    qv = np.concatenate([pv, v[:500]])
+    R, sym = run(P, ctx, g, qu, qv)
+    assert sym.info()["nq_two_branch"] > 1000
+    Ro = oracle_mod.resistance(g, qu, qv)
+    assert maxrel(R, Ro) <= TOL
+    # the same pairs with the endpoints swapped
+    Rs, _ = run(P, ctx, g, qv, qu)
+    assert maxrel(Rs, Ro) <= TOL
+
+
+def test_pairs_split_by_the_ground(P, ctx, oracle_mod):
+    """Two grids joined only through the ground node: the reduced Laplacian has two blocks, so
+    a pair across them walks two branches that end in different etree roots."""
+    a = I.grid2d(12, 13, seed=22)
+    ua, va = a.all_edges()
+    wa = a.edge_weights()
+    n = 2 * a.n + 1
+    g0 = 2 * a.n   # the joint
+    eu = np.concatenate([ua, ua + a.n, [5, a.n + 77]])
+    ev = np.concatenate([va, va + a.n, [g0, g0]])
+    ew = np.concatenate([wa, wa[::-1], [2.0, 0.5]])
+    g = I.from_edges(n, eu, ev, ew)
+    rng = np.random.default_rng(23)
+    qu = rng.integers(0, a.n, 400).astype(np.int32)
+    qv = (rng.integers(0, a.n, 400) + a.n).astype(np.int32)
+    qu = np.concatenate([qu, rng.integers(0, n, 200).astype(np.int32)])
+    qv = np.concatenate([qv, rng.integers(0, n, 200).astype(np.int32)])
+    R, _ = run(P, ctx, g, qu, qv, ground=g0, use_coords=False)
+    Ro = oracle_mod.resistance(g, qu, qv, ground=g0, use_coords=False)
+    triv = qu == qv
+    assert np.all(R[triv] == 0)
+    assert maxrel(R[~triv], Ro[~triv]) <= TOL
+
+
+def test_many_waves(P, ctx, oracle_mod):
+    """A tiny carry budget forces many waves of single-path and two-branch queries."""
+    g = I.pdn3(side=25, seed=24)
+    u, v = g.all_edges()
+    pu, pv = I.random_pairs(g.n, 700, seed=25)
+    qu = np.concatenate([u, pu])
+    qv = np.concatenate([v, pv])
+    opt = P.Options()
+    opt.reserved[0] = 256 * 1024   # bytes of carry per wave
+    R, sym = run(P, ctx, g, qu, qv, options=opt)
+    Rfull, _ = run(P, ctx, g, qu, qv)
+    assert np.array_equal(R, Rfull)
+    assert maxrel(R, oracle_mod.resistance(g, qu, qv)) <= TOL

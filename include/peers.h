@@ -152,6 +152,29 @@ void peers_free_numeric(peers_numeric *num);
 int peers_query(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num, double *R,
                 int flags);
 
+/* The sweep of peers_query for callers that cannot let the library allocate device memory:
+ * a framework that owns all device memory through its own pool, or a latency-bound loop that
+ * cannot afford the device-wide synchronisation a cudaMalloc or cudaFree may cause.  The
+ * paper has no counterpart; this is a deployment variant of the same kernels.
+ *   - Inputs are the plan and its resident factor (peers_factor allocated those earlier);
+ *     the output R_device is a device array of peers_num_queries(sym) doubles, written in
+ *     the plan's query order.  The call allocates and frees nothing.
+ *   - Scratch: the fronts carried between levels and the running sums live in one static
+ *     device array of 2 Mi doubles (16 MiB) compiled into the library; every GPU that loads
+ *     the library holds it until the process exits.  A plan fits when
+ *     carry_slots * (max n_b + 1) <= 2 Mi doubles: analyse with peers_options.reserved[0]
+ *     (the carry budget in bytes) at most 16 MiB to bound its waves.  A plan that does not
+ *     fit is rejected with PEERS_EINVAL and a message naming both sizes.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     and caches it; make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents.  Nothing in it
+ *     needs to start at zero (each carry is written before it is read); R is cleared by the
+ *     call.  Calls that overlap on the GPU (other streams, other contexts, other threads)
+ *     race on the array: serialise them.
+ * Errors: PEERS_EINVAL, PEERS_ECUDA. */
+int peers_query_noalloc(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
+                        double *R_device);
+
 /* Counters of the last peers_factor / peers_query on a context.  Device times are filled only
  * while timing is enabled (peers_set_timing(ctx, 1)); counts and bytes always. */
 typedef struct peers_stats {

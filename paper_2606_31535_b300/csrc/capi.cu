@@ -453,6 +453,40 @@ int peers_query(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *
   return rc == PEERS_OK ? rc : fail(rc, err);
 }
 
+int peers_query_noalloc(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
+                        double *R_device) {
+  if (!ctx || !sym || !num || (!R_device && sym->S.nq > 0))
+    return fail(PEERS_EINVAL, "null argument");
+  if (num->sym != sym) return fail(PEERS_EINVAL, "numeric handle belongs to another plan");
+  if (num->device != ctx->device) return fail(PEERS_EINVAL, "context on another device");
+  const Symbolic &S = sym->S;
+  peers::SweepArgs a{};
+  a.panel = num->panel;
+  a.tinv = num->tinv;
+  a.dinv = num->dinv;
+  a.first = num->first;
+  a.nb = num->nb;
+  a.rmap = num->rmap;
+  a.panel_off = num->panel_off;
+  a.tinv_off = num->tinv_off;
+  a.rows_off = num->rows_off;
+  a.qa = num->qa;
+  a.qb = num->qb;
+  a.qorig = num->qorig;
+  a.ldesc = num->ldesc;
+  a.nbmax = S.nbmax;
+  std::string err;
+  int64_t launches = 0;
+  int rc = peers::query_noalloc(ctx->stream, ctx->device, S, a, num->items,
+                                num->wave_item_off.data(), num->two_user, num->two_a,
+                                num->two_b, R_device, &launches, err);
+  if (rc != PEERS_OK) return fail(rc, err);
+  ctx->stats.sweep_launches = launches;
+  ctx->stats.h2d_bytes = 0;
+  ctx->stats.d2h_bytes = 0;
+  return PEERS_OK;
+}
+
 int peers_set_timing(peers_ctx *ctx, int enable) {
   if (!ctx) return fail(PEERS_EINVAL, "null context");
   ctx->timing = enable != 0;

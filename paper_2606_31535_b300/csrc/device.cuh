@@ -73,6 +73,13 @@ int run_two_branch_combine(const SweepArgs &args, const int64_t *two_user, const
                            const int32_t *two_b, int64_t k0, int64_t k1, cudaStream_t stream,
                            int64_t *launches, std::string &err);
 
+// The sweep with its scratch in the library's static device array (sweep_static.cu); no
+// device memory is allocated or freed.  R is a device array of S.nq doubles.
+int query_noalloc(cudaStream_t stream, int device, const Symbolic &S, const SweepArgs &base,
+                  const SweepItem *items, const int64_t *wave_item_off,
+                  const int64_t *two_user, const int32_t *two_a, const int32_t *two_b,
+                  double *R, int64_t *launches, std::string &err);
+
 // FP64 throughput probes (TFLOP/s) on the current device: out[0] DFMA (CUDA cores),
 // out[1] mma.sync m8n8k4 f64 (the FP64 tensor path).
 int fp64_peak(cudaStream_t stream, double out[2], std::string &err);

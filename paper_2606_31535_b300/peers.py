@@ -80,6 +80,7 @@ def load(path: str | None = None):
         "peers_numeric_diag": (ctypes.c_int, [vp, vp, vp]),
         "peers_free_numeric": (None, [vp]),
         "peers_query": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+        "peers_query_noalloc": (ctypes.c_int, [vp, vp, vp, vp]),
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "peers_last_stats": (ctypes.c_int, [vp, P(Stats)]),
         "peers_fp64_peak": (ctypes.c_int, [vp, P(dbl)]),
@@ -249,6 +250,13 @@ def query(ctx: Context, sym: Symbolic, num: Numeric, out=None):
         out = np.empty(sym.nq, dtype=np.float64)
     flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
     _check(lib.peers_query(ctx._h, sym._h, num._h, _ptr(out), flags), "peers_query")
+    return out
+
+
+def query_noalloc(ctx: Context, sym: Symbolic, num: Numeric, out):
+    """Resistances into the device tensor `out` (float64, sym.nq entries) with the library's
+    static scratch array: the library allocates no device memory during the call."""
+    _check(load().peers_query_noalloc(ctx._h, sym._h, num._h, _ptr(out)), "peers_query_noalloc")
     return out
 
 

@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pdn1m", choices=["pdn1m", "grid32", "grid512"])
+    ap.add_argument("--workload", default="pdn1m",
+                    choices=["pdn1m", "grid32", "grid512", "batch256"])
     ap.add_argument("--cpu-sample", type=int, default=16000,
                     help="edges in the oracle's CPU-baseline sample (0 = skip)")
     ap.add_argument("--ref-sample", type=int, default=8000,
@@ -63,7 +64,8 @@ def make_graph(name):
 
 def workload_name(name):
     return {"pdn1m": WORKLOAD, "grid32": "grid32x32_uniform_0.5_2_seed1_all_edges",
-            "grid512": "grid512x512_loguniform_seed3_all_edges"}[name]
+            "grid512": "grid512x512_loguniform_seed3_all_edges",
+            "batch256": "batch256_grids_5pct_deleted_and_rgg6_1k_64k_loguniform_seeds3000+i_all_edges"}[name]
 
 
 # ------------------------------------------------------------------ CPU oracle (host cores)
@@ -313,12 +315,119 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched graphs
+
+def run_batch(args):
+    """256 independent graphs swept together (one persistent launch per aligned level, CUDA
+    graph replay), against the same graphs swept one at a time on the same GPU."""
+    import torch
+    from paper_2606_31535_b300 import inputs as I
+    from paper_2606_31535_b300 import peers as P
+
+    t0 = time.time()
+    graphs = I.batch_graphs()
+    t_gen = time.time() - t0
+    t0 = time.time()
+    syms = [P.Symbolic.of(g) for g in graphs]
+    t_analyze = time.time() - t0
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = P.Context(0, stream)
+    peaks64 = ctx.fp64_peaks()
+    t0 = time.time()
+    nums = [P.Numeric(ctx, s) for s in syms]
+    torch.cuda.synchronize()
+    t_factor = time.time() - t0
+    batch = P.Batch(ctx, syms, nums, cuda_graph=True)
+    binfo = batch.info()
+    nq = sum(s.nq for s in syms)
+    W = sum(s.info()["walk_entries"] for s in syms)
+    levels = sum(s.info()["levels"] for s in syms)
+    outs = [torch.empty(s.nq, dtype=torch.float64, device="cuda:0") for s in syms]
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3 / k
+
+    def batched():
+        batch.query(outs)
+
+    def one_at_a_time():
+        for s, m, o in zip(syms, nums, outs):
+            P.query(ctx, s, m, o)
+
+    for _ in range(args.warmup):
+        batched()
+    clk = start_clocks(0)
+    t_batch = timed(batched, args.steps)
+    clocks = stop_clocks(*clk)
+    ref = [o.clone() for o in outs]
+    for _ in range(max(1, args.warmup // 2)):
+        one_at_a_time()
+    t_single = timed(one_at_a_time, args.steps)
+    same = all(bool(torch.equal(a, b)) for a, b in zip(ref, outs))
+
+    # end to end: pinned conductances -> factor every graph -> batched sweep -> host results
+    pins = [torch.from_numpy(g.w).pin_memory() for g in graphs]
+    hosts = [torch.empty(s.nq, dtype=torch.float64).pin_memory().numpy() for s in syms]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nums2, h2d = [], 0
+    for s, w in zip(syms, pins):
+        nums2.append(P.Numeric(ctx, s, w.numpy()))
+        h2d += ctx.last_stats()["h2d_bytes"]
+    b2 = P.Batch(ctx, syms, nums2, cuda_graph=False)
+    b2.query(hosts)
+    d2h = ctx.last_stats()["d2h_bytes"]
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    b2.close()
+    for m in nums2:
+        m.close()
+
+    achieved_tf = 2.0 * W / t_batch / 1e12
+    line = {
+        "metric": "edge queries/s, batched all-edge sweep of 256 graphs (FP64)",
+        "value": nq / t_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name("batch256"), "graphs": len(graphs),
+                   "nodes": int(sum(g.n for g in graphs)), "edges": nq,
+                   "l2": "inputs larger than L2: %.2f GB of factors and fronts"
+                         % (1e-9 * binfo["device_bytes"])},
+        "one_at_a_time": {"value": nq / t_single, "ms_per_step": 1e3 * t_single,
+                          "launches": levels, "same_results": same},
+        "batched": {"launches": binfo["launches"], "items": binfo["items"],
+                    "cuda_graph": True},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peaks64["dfma"],
+                     "unit": "TFLOP/s", "frac": achieved_tf / peaks64["dfma"], "traffic": None,
+                     "kernel": "k_sweep_multi"},
+        "e2e": {"value": nq / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "includes": "factor all 256 + batched sweep"},
+        "gpu_launches": int(binfo["launches"] * args.steps),
+        "clocks": clocks,
+        "analysis": {"t_generate_s": t_gen, "t_analyze_s": t_analyze, "t_factor_s": t_factor,
+                     "walk_entries": W},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch256":
+        return run_batch(args)
     return run_ours(args)
 
 

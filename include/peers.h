@@ -175,6 +175,31 @@ int peers_query(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *
 int peers_query_noalloc(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
                         double *R_device);
 
+/* ---- batched sweep of many graphs -------------------------------------------------------- */
+
+/* Many independent graphs, each with its own plan and factor, swept together: the graphs'
+ * level sequences are aligned and the t-th level of every graph becomes one persistent
+ * kernel launch (CTAs pull work items of all graphs until the level is done), so G graphs of
+ * heights H_g take max_g H_g launches.  With PEERS_BATCH_CUDA_GRAPH the launch sequence is
+ * captured into a CUDA graph on the first peers_batch_query and replayed afterwards.  Each
+ * graph's results are bit-identical to its own peers_query (an item's arithmetic depends
+ * only on its supernode and queries).  The handles must outlive the batch.  This is the
+ * batching pattern of the sweep; the paper's own parallel driver is Alg. 8. */
+typedef struct peers_batch peers_batch;
+#define PEERS_BATCH_CUDA_GRAPH 1
+int peers_batch_create(peers_ctx *ctx, int32_t count, const peers_symbolic *const *syms,
+                       const peers_numeric *const *nums, int flags, peers_batch **out);
+/* R[i] receives graph i's peers_num_queries(syms[i]) results (host pointers, or device
+ * pointers with PEERS_OUT_DEVICE); R may be NULL to leave them in the batch. */
+int peers_batch_query(peers_ctx *ctx, peers_batch *b, double *const *R, int flags);
+/* out[0] steps (aligned levels), out[1] work items, out[2] launches per query,
+ * out[3] device bytes held by the batch. */
+int peers_batch_info(const peers_batch *b, int64_t out[4]);
+void peers_batch_free(peers_batch *b);
+/* One-shot: create, query once (no graph capture), free. */
+int peers_query_batch(peers_ctx *ctx, int32_t count, const peers_symbolic *const *syms,
+                      const peers_numeric *const *nums, double *const *R, int flags);
+
 /* Counters of the last peers_factor / peers_query on a context.  Device times are filled only
  * while timing is enabled (peers_set_timing(ctx, 1)); counts and bytes always. */
 typedef struct peers_stats {

@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpeers.so")
-SOURCES = ["analyze.cpp", "factor.cu", "sweep.cu", "sweep_static.cu", "capi.cu"]
-HEADERS = ["internal.h", "device.cuh"]
+SOURCES = ["analyze.cpp", "factor.cu", "sweep.cu", "sweep_static.cu", "batch.cu", "capi.cu"]
+HEADERS = ["internal.h", "device.cuh", "handles.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3,-Wall",

@@ -9,44 +9,9 @@
 #include <vector>
 
 #include "device.cuh"
+#include "handles.h"
 #include "internal.h"
 #include "peers.h"
-
-using peers::SweepItem;
-using peers::Symbolic;
-
-struct peers_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  bool timing = false;
-  peers_stats stats{};
-  std::vector<double> level_ms;
-};
-
-struct peers_symbolic {
-  Symbolic S;
-};
-
-struct peers_numeric {
-  int device = 0;
-  const peers_symbolic *sym = nullptr;   // not owned; must outlive this handle
-  std::vector<void *> allocs;
-  int64_t h2d_bytes = 0;   // bytes uploaded while building this handle
-  // factor
-  double *panel = nullptr, *tinv = nullptr, *d = nullptr, *dinv = nullptr;
-  int32_t *first = nullptr, *nb = nullptr, *rmap = nullptr;
-  int64_t *panel_off = nullptr, *tinv_off = nullptr, *rows_off = nullptr;
-  // sweep plan
-  int32_t *qa = nullptr, *qb = nullptr;
-  int64_t *qorig = nullptr;
-  SweepItem *items = nullptr;
-  peers::SweepDesc *ldesc = nullptr;
-  int64_t *two_user = nullptr;
-  int32_t *two_a = nullptr, *two_b = nullptr;
-  std::vector<int64_t> wave_item_off;
-  double *carry = nullptr, *racc = nullptr, *Rdev = nullptr;
-};
 
 namespace {
 
@@ -56,6 +21,12 @@ int fail(int status, const std::string &msg) {
   g_error = msg;
   return status;
 }
+
+}  // namespace
+
+int peers_fail(int status, const std::string &msg) { return fail(status, msg); }
+
+namespace {
 
 template <class T>
 int dalloc(peers_numeric *num, T **p, int64_t count, std::string &err) {

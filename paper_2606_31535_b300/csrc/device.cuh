@@ -53,6 +53,8 @@ struct SweepArgs {
   double *carry;   // carry_slots x nbmax: the B-part of each query's front, slot-major
   double *racc;    // carry_slots: running sum_k y_k^2 / d_k of each query
   double *R;       // nq results in the caller's query order
+  const int64_t *two_user;   // two-branch combine: user index, slot a, slot b per query
+  const int32_t *two_a, *two_b;
   int64_t nbmax;
   int64_t wave_base;
 };
@@ -72,6 +74,14 @@ int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_ite
 int run_two_branch_combine(const SweepArgs &args, const int64_t *two_user, const int32_t *two_a,
                            const int32_t *two_b, int64_t k0, int64_t k1, cudaStream_t stream,
                            int64_t *launches, std::string &err);
+
+// One launch of the multi-graph (persistent) sweep kernel: nitems items, each with its
+// argument block table[item.g]; CTAs pull items through *counter (zero before the launch).
+int run_multi_step(const SweepItem *items, int64_t nitems, const SweepArgs *table, int *counter,
+                   int64_t smem, int64_t grid, cudaStream_t stream, std::string &err);
+// Grid of a persistent multi-graph launch (CTAs that fit the GPU at once, at most nitems);
+// also raises the kernel's dynamic shared-memory limit to smem.  Call outside stream capture.
+int multi_step_grid(int64_t smem, int64_t nitems, int64_t *grid, std::string &err);
 
 // The sweep with its scratch in the library's static device array (sweep_static.cu); no
 // device memory is allocated or freed.  R is a device array of S.nq doubles.

@@ -1,0 +1,73 @@
+// Definitions of the C-ABI handles (library-internal; shared by capi.cu and batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+#include "peers.h"
+
+using peers::SweepItem;
+using peers::Symbolic;
+
+struct peers_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool timing = false;
+  peers_stats stats{};
+  std::vector<double> level_ms;
+};
+
+struct peers_symbolic {
+  Symbolic S;
+};
+
+struct peers_numeric {
+  int device = 0;
+  const peers_symbolic *sym = nullptr;   // not owned; must outlive this handle
+  std::vector<void *> allocs;
+  int64_t h2d_bytes = 0;   // bytes uploaded while building this handle
+  // factor
+  double *panel = nullptr, *tinv = nullptr, *d = nullptr, *dinv = nullptr;
+  int32_t *first = nullptr, *nb = nullptr, *rmap = nullptr;
+  int64_t *panel_off = nullptr, *tinv_off = nullptr, *rows_off = nullptr;
+  // sweep plan
+  int32_t *qa = nullptr, *qb = nullptr;
+  int64_t *qorig = nullptr;
+  SweepItem *items = nullptr;
+  peers::SweepDesc *ldesc = nullptr;
+  int64_t *two_user = nullptr;
+  int32_t *two_a = nullptr, *two_b = nullptr;
+  std::vector<int64_t> wave_item_off;
+  double *carry = nullptr, *racc = nullptr, *Rdev = nullptr;
+};
+
+
+// Argument block of the sweep kernels for one factored plan (scratch and R left unset).
+inline peers::SweepArgs sweep_args_of(const peers_numeric *num, const Symbolic &S) {
+  peers::SweepArgs a{};
+  a.panel = num->panel;
+  a.tinv = num->tinv;
+  a.dinv = num->dinv;
+  a.first = num->first;
+  a.nb = num->nb;
+  a.rmap = num->rmap;
+  a.panel_off = num->panel_off;
+  a.tinv_off = num->tinv_off;
+  a.rows_off = num->rows_off;
+  a.qa = num->qa;
+  a.qb = num->qb;
+  a.qorig = num->qorig;
+  a.ldesc = num->ldesc;
+  a.two_user = num->two_user;
+  a.two_a = num->two_a;
+  a.two_b = num->two_b;
+  a.nbmax = S.nbmax;
+  return a;
+}
+
+// Records a failure message for peers_last_error and returns the status.
+int peers_fail(int status, const std::string &msg);

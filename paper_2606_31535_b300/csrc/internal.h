@@ -43,6 +43,9 @@ PEERS_HD inline int64_t sweep_smem_bytes(int64_t N, int64_t Q) {
 //     from child supernode src (their carries are scattered through src's relative map);
 //     src == -1: they start at s (seeded with +1 at qa, -1 at qb).
 //   kind 1 (list): nq entries ldesc[q0 .. q0+nq) of the two-branch walk (see SweepDesc).
+//   kind 2 (combine): finish the two-branch queries [q0, q0+nq) of a wave (multi-graph
+//     launches only; single-graph sweeps use a separate combine launch).
+// g selects the graph/wave argument block in multi-graph launches (0 otherwise).
 struct SweepItem {
   int32_t s;
   int32_t src;
@@ -50,6 +53,8 @@ struct SweepItem {
   int32_t nq;
   int32_t j0;   // first column block (block-aligned) with a non-zero right-hand side
   int32_t kind;
+  int32_t g;
+  int32_t pad;
 };
 
 // One query step of the two-branch walk (a listed pair whose endpoints' etree paths meet

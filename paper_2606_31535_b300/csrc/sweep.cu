@@ -28,10 +28,17 @@ namespace peers {
 
 constexpr int kSweepThreads = 256;
 
-__global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepItem *__restrict__ items,
-                                                         SweepArgs a) {
-  extern __shared__ double smem[];
-  const SweepItem it = items[blockIdx.x];
+// One work item (see SweepItem) by one CTA of kSweepThreads threads.
+__device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs &a,
+                                           double *smem) {
+  if (it.kind == 2) {   // combine two-branch sums (multi-graph launches)
+    for (int64_t k = it.q0 + threadIdx.x; k < int64_t(it.q0) + it.nq; k += kSweepThreads) {
+      double r = a.racc[int64_t(a.two_a[k]) - a.wave_base];
+      if (a.two_b[k] >= 0) r += a.racc[int64_t(a.two_b[k]) - a.wave_base];
+      a.R[a.two_user[k]] = r;
+    }
+    return;
+  }
   const int32_t s = it.s, Q = it.nq;
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
   const int QP = static_cast<int>(sweep_qstride(Q));
@@ -181,6 +188,58 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepItem *__rest
     else
       a.R[a.qorig[slot]] = tot;
   }
+}
+
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepItem *__restrict__ items,
+                                                         SweepArgs a) {
+  extern __shared__ double smem[];
+  sweep_item(items[blockIdx.x], a, smem);
+}
+
+// Persistent multi-graph launch: as many CTAs as fit on the GPU, each pulling items (sorted
+// largest first) until the level's list is exhausted.  Items of different graphs, and of
+// different requests of a server, share one launch.
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_multi(const SweepItem *__restrict__ items,
+                                                               int64_t nitems,
+                                                               const SweepArgs *__restrict__ table,
+                                                               int *counter) {
+  extern __shared__ double smem[];
+  __shared__ int next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int64_t i = next;
+    __syncthreads();
+    if (i >= nitems) break;
+    const SweepItem it = items[i];
+    sweep_item(it, table[it.g], smem);
+    __syncthreads();
+  }
+}
+
+int multi_step_grid(int64_t smem, int64_t nitems, int64_t *grid, std::string &err) {
+  static int configured_smem = 0;
+  if (smem > configured_smem) {
+    CUDA_TRY(cudaFuncSetAttribute(k_sweep_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+    configured_smem = static_cast<int>(smem);
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_multi, kSweepThreads,
+                                                         static_cast<size_t>(smem)));
+  *grid = std::min<int64_t>(nitems, int64_t(std::max(per_sm, 1)) * sms);
+  return PEERS_OK;
+}
+
+int run_multi_step(const SweepItem *items, int64_t nitems, const SweepArgs *table, int *counter,
+                   int64_t smem, int64_t grid, cudaStream_t stream, std::string &err) {
+  if (grid <= 0 || nitems <= 0) return PEERS_OK;
+  k_sweep_multi<<<static_cast<unsigned>(grid), kSweepThreads, smem, stream>>>(items, nitems,
+                                                                             table, counter);
+  CUDA_TRY(cudaGetLastError());
+  return PEERS_OK;
 }
 
 int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_items,

@@ -81,6 +81,11 @@ def load(path: str | None = None):
         "peers_free_numeric": (None, [vp]),
         "peers_query": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
         "peers_query_noalloc": (ctypes.c_int, [vp, vp, vp, vp]),
+        "peers_batch_create": (ctypes.c_int, [vp, ctypes.c_int32, vp, vp, ctypes.c_int, P(vp)]),
+        "peers_batch_query": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "peers_batch_info": (ctypes.c_int, [vp, P(i64)]),
+        "peers_batch_free": (None, [vp]),
+        "peers_query_batch": (ctypes.c_int, [vp, ctypes.c_int32, vp, vp, vp, ctypes.c_int]),
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "peers_last_stats": (ctypes.c_int, [vp, P(Stats)]),
         "peers_fp64_peak": (ctypes.c_int, [vp, P(dbl)]),
@@ -251,6 +256,48 @@ def query(ctx: Context, sym: Symbolic, num: Numeric, out=None):
     flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
     _check(lib.peers_query(ctx._h, sym._h, num._h, _ptr(out), flags), "peers_query")
     return out
+
+
+BATCH_CUDA_GRAPH = 1
+
+
+class Batch:
+    """Many factored graphs swept together: one persistent launch per aligned etree level,
+    optionally captured in a CUDA graph (replayed on every query after the first)."""
+
+    def __init__(self, ctx: Context, syms, nums, cuda_graph: bool = True):
+        lib = load()
+        self._ctx, self._syms, self._nums = ctx, list(syms), list(nums)
+        n = len(self._syms)
+        hs = (ctypes.c_void_p * n)(*[s._h.value for s in self._syms])
+        hn = (ctypes.c_void_p * n)(*[m._h.value for m in self._nums])
+        h = ctypes.c_void_p()
+        _check(lib.peers_batch_create(ctx._h, n, hs, hn, BATCH_CUDA_GRAPH if cuda_graph else 0,
+                                      ctypes.byref(h)), "peers_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().peers_batch_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 4)()
+        _check(load().peers_batch_info(self._h, out), "peers_batch_info")
+        return {"steps": out[0], "items": out[1], "launches": out[2], "device_bytes": out[3]}
+
+    def query(self, outs=None):
+        """Returns (or fills) one result array per graph: numpy arrays (host) or float64 torch
+        CUDA tensors (device)."""
+        if outs is None:
+            outs = [np.empty(s.nq, dtype=np.float64) for s in self._syms]
+        n = len(outs)
+        flags = 0 if isinstance(outs[0], np.ndarray) else OUT_DEVICE
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(o).value for o in outs])
+        _check(load().peers_batch_query(self._ctx._h, self._h, ptrs, flags), "peers_batch_query")
+        return outs
 
 
 def query_noalloc(ctx: Context, sym: Symbolic, num: Numeric, out):

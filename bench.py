@@ -44,7 +44,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pdn1m",
-                    choices=["pdn1m", "grid32", "grid512", "batch256"])
+                    choices=["pdn1m", "grid32", "grid512", "batch256", "serve"])
+    ap.add_argument("--requests", type=int, default=80,
+                    help="serve workload: requests in the stream (the full stream is 500)")
+    ap.add_argument("--rho", default="0.9",
+                    help="serve workload: offered loads, comma separated (e.g. 0.5,0.9,1.5)")
     ap.add_argument("--cpu-sample", type=int, default=16000,
                     help="edges in the oracle's CPU-baseline sample (0 = skip)")
     ap.add_argument("--ref-sample", type=int, default=8000,
@@ -65,7 +69,8 @@ def make_graph(name):
 def workload_name(name):
     return {"pdn1m": WORKLOAD, "grid32": "grid32x32_uniform_0.5_2_seed1_all_edges",
             "grid512": "grid512x512_loguniform_seed3_all_edges",
-            "batch256": "batch256_grids_5pct_deleted_and_rgg6_1k_64k_loguniform_seeds3000+i_all_edges"}[name]
+            "batch256": "batch256_grids_5pct_deleted_and_rgg6_1k_64k_loguniform_seeds3000+i_all_edges",
+            "serve": "serve_stream_n10k_500k_grid_or_rgg_all_or_10pct_edges_poisson_seed4"}[name]
 
 
 # ------------------------------------------------------------------ CPU oracle (host cores)
@@ -420,6 +425,113 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------ serving stream
+
+def _replay(P, reqs, arrivals, server_kw):
+    """Submits each request at its arrival time (relative to now) to a fresh server and
+    waits for all; returns (latencies, server stats)."""
+    import threading
+    sv = P.Server(0, **server_kw)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, (g, qu, qv) in enumerate(reqs):
+            delay = arrivals[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = sv.submit(g, qu, qv)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.001)
+        _, l = sv.wait(tickets[i])
+        lat.append(l)
+    th.join()
+    st = sv.stats()
+    sv.close()
+    return np.array(lat), st
+
+
+def _replay_plain(P, ctx, reqs, arrivals):
+    """The same stream served one request at a time through the plain API (analyse, factor,
+    sweep), in arrival order; latency = completion - arrival."""
+    t0 = time.perf_counter()
+    lat, nq = [], 0
+    for i, (g, qu, qv) in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        sym = P.Symbolic.of(g, 0, qu, qv)
+        num = P.Numeric(ctx, sym)
+        R = P.query(ctx, sym, num)
+        nq += R.size
+        lat.append(time.perf_counter() - t0 - arrivals[i])
+        num.close()
+        sym.close()
+    wall = time.perf_counter() - t0 - arrivals[0]
+    return np.array(lat), nq / wall
+
+
+def run_serve(args):
+    import torch
+    from paper_2606_31535_b300 import inputs as I
+    from paper_2606_31535_b300 import peers as P
+
+    t0 = time.time()
+    reqs = [I.serve_request(i) for i in range(args.requests)]
+    t_gen = time.time() - t0
+    torch.cuda.set_device(0)
+    ctx = P.Context(0)
+    # t_single: the plain API on a few requests, one at a time
+    sample = reqs[:min(8, len(reqs))]
+    t0 = time.perf_counter()
+    for g, qu, qv in sample:
+        sym = P.Symbolic.of(g, 0, qu, qv)
+        P.query(ctx, sym, P.Numeric(ctx, sym))
+    t_single = (time.perf_counter() - t0) / len(sample)
+    workers = max(2, min(8, (os.cpu_count() or 4) // 2))
+    nq_total = sum((g.m if qu is None else qu.size) for g, qu, qv in reqs)
+    loads = []
+    for rho in [float(x) for x in args.rho.split(",")]:
+        arrivals = I.poisson_arrivals(len(reqs), rho / t_single, seed=4)
+        arrivals -= arrivals[0]
+        lat_b, st_b = _replay(P, reqs, arrivals, {"max_active": 64, "workers": workers})
+        lat_1, st_1 = _replay(P, reqs, arrivals, {"max_active": 1, "workers": workers})
+        lat_p, qps_p = _replay_plain(P, ctx, reqs, arrivals)
+        loads.append({
+            "rho": rho, "arrival_rate_per_s": rho / t_single,
+            "continuous_batching": {"qps": st_b["qps"], "p50_s": float(np.percentile(lat_b, 50)),
+                                    "p99_s": float(np.percentile(lat_b, 99)),
+                                    "mean_s": float(lat_b.mean()), "steps": st_b["steps"],
+                                    "peak_bytes": st_b["peak_bytes"]},
+            "one_at_a_time_on_gpu": {"qps": st_1["qps"], "p50_s": float(np.percentile(lat_1, 50)),
+                                     "p99_s": float(np.percentile(lat_1, 99)),
+                                     "note": "same server, one admitted request at a time"},
+            "plain_api_fifo": {"qps": qps_p, "p50_s": float(np.percentile(lat_p, 50)),
+                               "p99_s": float(np.percentile(lat_p, 99)),
+                               "note": "analyse + factor + sweep per request, in order"},
+        })
+    main_load = loads[0]
+    line = {
+        "metric": "edge queries/s and p50/p99 request latency, served request stream (FP64)",
+        "value": main_load["continuous_batching"]["qps"], "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name("serve"), "requests": len(reqs),
+                   "queries": int(nq_total), "t_single_s": t_single, "workers": workers,
+                   "generation_s": t_gen},
+        "latency": {"p50_s": main_load["continuous_batching"]["p50_s"],
+                    "p99_s": main_load["continuous_batching"]["p99_s"]},
+        "loads": loads,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.warmup < 0 or args.steps < 1:
@@ -428,6 +540,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch256":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -200,6 +200,42 @@ void peers_batch_free(peers_batch *b);
 int peers_query_batch(peers_ctx *ctx, int32_t count, const peers_symbolic *const *syms,
                       const peers_numeric *const *nums, double *const *R, int flags);
 
+/* ---- serving: continuous batching of requests ------------------------------------------- */
+
+/* A request loop on one device.  Each submitted request (a graph and its queries, copied at
+ * submit) is analysed and factored by one of `workers` host threads on its own CUDA stream,
+ * admitted when its device footprint (peers_footprint_bytes) fits in `mem_budget_bytes`
+ * next to the admitted requests and at most `max_active` are admitted, and then swept by
+ * continuous batching: one persistent launch per step carries the next etree level of every
+ * active request; requests join at the next step after their factor is ready and leave after
+ * their last level.  Results equal peers_query's bit for bit, alone or in the mix.
+ * mem_budget_bytes <= 0 selects 64 GiB; max_active <= 0 selects 64; workers <= 0 selects 4. */
+typedef struct peers_server peers_server;
+typedef struct peers_server_stats {
+  int64_t submitted, completed, failed, queries;
+  int64_t steps, launches;      /* sweep steps run, kernel launches */
+  int64_t peak_bytes;           /* largest admitted footprint sum */
+  double wall_s;                /* first submit to last completion */
+  double qps;                   /* completed queries / wall_s */
+  double p50_s, p99_s, mean_s;  /* request latency, submit to results ready */
+} peers_server_stats;
+int peers_server_create(int device, int64_t mem_budget_bytes, int32_t max_active,
+                        int32_t workers, peers_server **out);
+/* Same graph/query arguments as peers_analyze; returns a ticket. */
+int peers_server_submit(peers_server *sv, int64_t n, const int64_t *indptr,
+                        const int32_t *indices, const double *w, int32_t ground, int64_t nq,
+                        const int32_t *qu, const int32_t *qv, const double *coords, int dim,
+                        int64_t *ticket);
+/* 1 = results ready, 0 = not yet, < 0 = the request failed with that status. */
+int peers_server_poll(peers_server *sv, int64_t ticket);
+/* Blocks until the request is done, copies up to `cap` results into host R (may be NULL),
+ * stores the request's latency, and releases the ticket. */
+int peers_server_wait(peers_server *sv, int64_t ticket, double *R, int64_t cap,
+                      double *latency_s);
+int peers_server_get_stats(peers_server *sv, peers_server_stats *out);
+/* Finishes the admitted and queued requests, then stops the threads and frees everything. */
+void peers_server_destroy(peers_server *sv);
+
 /* Counters of the last peers_factor / peers_query on a context.  Device times are filled only
  * while timing is enabled (peers_set_timing(ctx, 1)); counts and bytes always. */
 typedef struct peers_stats {

@@ -351,7 +351,10 @@ int64_t peers_footprint_bytes(const peers_symbolic *sym) {
   const Symbolic &S = sym->S;
   int64_t items = 0;
   for (const auto &W : S.waves) items += static_cast<int64_t>(W.items.size());
+  // resident factor + sweep scratch + results, plus the factorization's transient update
+  // matrices and assembly arrays (freed when peers_factor returns)
   return 8 * (S.panel_total + S.tinv_total + 2 * S.nr + S.carry_slots * (S.nbmax + 1) + S.nq) +
+         8 * (S.u_total + 2 * static_cast<int64_t>(S.a_dest.size())) +
          4 * (3 * int64_t(S.nsuper) + static_cast<int64_t>(S.rmap.size()) + 2 * S.nsorted) +
          8 * (3 * int64_t(S.nsuper) + S.nsorted) + static_cast<int64_t>(sizeof(SweepItem)) * items;
 }

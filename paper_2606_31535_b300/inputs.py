@@ -130,30 +130,24 @@ def pdn3(side: int = 577, layers: int = 3, via_stride: int = 4, seed: int = 2,
     return from_edges(layers * per, eu, ev, ew, coords, f"pdn{layers}x{side}x{side}")
 
 
-def _find(parent: np.ndarray, x: int) -> int:
-    while parent[x] != x:
-        parent[x] = parent[parent[x]]
-        x = parent[x]
-    return x
-
-
 def grid_deleted(rows: int, cols: int, seed: int, frac: float = 0.05,
                  lo: float = 1e-2, hi: float = 1e2) -> Graph:
     """Grid with ``frac`` of its edges deleted while keeping it connected: a random spanning
     tree (Kruskal on seeded random keys) is kept and round(frac*m) edges are deleted
     uniformly among the non-tree edges.  Conductances log-uniform, drawn for the surviving
     edges in grid draw order."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import minimum_spanning_tree
+
     rng = _rng(seed)
     eu, ev = _grid_edges(rows, cols)
     m = eu.size
     keys = rng.random(m)
-    parent = np.arange(rows * cols)
-    tree = np.zeros(m, dtype=bool)
-    for e in np.argsort(keys, kind="stable"):
-        a, b = _find(parent, int(eu[e])), _find(parent, int(ev[e]))
-        if a != b:
-            parent[a] = b
-            tree[e] = True
+    # Kruskal on the seeded keys = the minimum spanning tree for those (distinct) keys
+    n = rows * cols
+    mst = minimum_spanning_tree(coo_matrix((keys + 1.0, (eu, ev)), shape=(n, n))).tocoo()
+    in_tree = set(zip(np.minimum(mst.row, mst.col).tolist(), np.maximum(mst.row, mst.col).tolist()))
+    tree = np.fromiter(((int(a), int(b)) in in_tree for a, b in zip(eu, ev)), dtype=bool, count=m)
     non_tree = np.flatnonzero(~tree)
     k = int(round(frac * m))
     drop = rng.choice(non_tree, size=min(k, non_tree.size), replace=False)
@@ -257,3 +251,28 @@ def random_pairs(n: int, k: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
     v = rng.integers(0, n - 1, size=k)
     v = v + (v >= u)
     return u.astype(np.int32), v.astype(np.int32)
+
+
+def serve_request(i: int, base_seed: int = 4, n_lo: int = 10_000, n_hi: int = 500_000):
+    """Request i of the serving stream: n log-uniform in [n_lo, n_hi]; a near-square grid with
+    5% of its edges deleted or a random geometric graph (mean degree 6), 50/50; all edges or a
+    seeded uniform 10% subset of them, 50/50.  Returns (graph, qu, qv) with qu = qv = None for
+    all edges."""
+    rng = np.random.Generator(np.random.PCG64([base_seed, i]))
+    n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+    sub = int(rng.integers(0, 2 ** 31))
+    if rng.random() < 0.5:
+        r = int(round(math.sqrt(n)))
+        g = grid_deleted(r, max(2, int(round(n / r))), seed=sub)
+    else:
+        g = rgg(n, seed=sub)
+    if rng.random() < 0.5:
+        return g, None, None
+    qu, qv = query_subset(g, 0.1, seed=sub + 1)
+    return g, qu, qv
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson process of the given rate."""
+    rng = _rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))

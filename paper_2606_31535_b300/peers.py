@@ -44,6 +44,15 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "queries",
+                                               "steps", "launches", "peak_bytes")] + \
+               [(k, ctypes.c_double) for k in ("wall_s", "qps", "p50_s", "p99_s", "mean_s")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Info(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n", "n_reduced", "nnz_a", "nnz_l", "nsuper", "levels", "max_nc", "max_nb", "nq",
@@ -86,6 +95,14 @@ def load(path: str | None = None):
         "peers_batch_info": (ctypes.c_int, [vp, P(i64)]),
         "peers_batch_free": (None, [vp]),
         "peers_query_batch": (ctypes.c_int, [vp, ctypes.c_int32, vp, vp, vp, ctypes.c_int]),
+        "peers_server_create": (ctypes.c_int, [ctypes.c_int, i64, ctypes.c_int32, ctypes.c_int32,
+                                               P(vp)]),
+        "peers_server_submit": (ctypes.c_int, [vp, i64, vp, vp, vp, i32, i64, vp, vp, vp,
+                                               ctypes.c_int, P(i64)]),
+        "peers_server_poll": (ctypes.c_int, [vp, i64]),
+        "peers_server_wait": (ctypes.c_int, [vp, i64, vp, i64, P(dbl)]),
+        "peers_server_get_stats": (ctypes.c_int, [vp, P(ServerStats)]),
+        "peers_server_destroy": (None, [vp]),
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "peers_last_stats": (ctypes.c_int, [vp, P(Stats)]),
         "peers_fp64_peak": (ctypes.c_int, [vp, P(dbl)]),
@@ -298,6 +315,67 @@ class Batch:
         ptrs = (ctypes.c_void_p * n)(*[_ptr(o).value for o in outs])
         _check(load().peers_batch_query(self._ctx._h, self._h, ptrs, flags), "peers_batch_query")
         return outs
+
+
+class Server:
+    """Continuous-batching request loop on one device (see peers_server_* in peers.h)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0,
+                 workers: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.peers_server_create(int(device), int(mem_budget_bytes), int(max_active),
+                                       int(workers), ctypes.byref(h)), "peers_server_create")
+        self._h = h
+        self._nq = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().peers_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def submit(self, g, qu=None, qv=None, ground: int = 0, use_coords: bool = True) -> int:
+        """Queues a request (graph + queries; all edges when qu is None); returns its ticket.
+        The library copies the arrays before returning."""
+        ip = np.ascontiguousarray(g.indptr, dtype=np.int64)
+        ix = np.ascontiguousarray(g.indices, dtype=np.int32)
+        w = np.ascontiguousarray(g.w, dtype=np.float64)
+        if qu is not None:
+            qu = np.ascontiguousarray(qu, dtype=np.int32)
+            qv = np.ascontiguousarray(qv, dtype=np.int32)
+            nq = qu.size
+        else:
+            nq = -1
+        c = None
+        dim = 0
+        if use_coords and g.coords is not None:
+            c = np.ascontiguousarray(g.coords, dtype=np.float64)
+            dim = c.shape[1]
+        t = ctypes.c_int64()
+        _check(load().peers_server_submit(self._h, int(g.n), _ptr(ip), _ptr(ix), _ptr(w),
+                                          int(ground), int(nq), _ptr(qu), _ptr(qv), _ptr(c), dim,
+                                          ctypes.byref(t)), "peers_server_submit")
+        self._nq[t.value] = g.m if nq < 0 else nq
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return int(load().peers_server_poll(self._h, int(ticket)))
+
+    def wait(self, ticket: int):
+        """(results, latency seconds) of a request; raises PeersError if it failed."""
+        nq = self._nq.pop(ticket)
+        R = np.empty(nq, dtype=np.float64)
+        lat = ctypes.c_double()
+        _check(load().peers_server_wait(self._h, int(ticket), _ptr(R), nq, ctypes.byref(lat)),
+               "peers_server_wait")
+        return R, lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().peers_server_get_stats(self._h, ctypes.byref(st)), "peers_server_get_stats")
+        return st.as_dict()
 
 
 def query_noalloc(ctx: Context, sym: Symbolic, num: Numeric, out):

@@ -147,6 +147,21 @@ def stop_clocks(p, f):
             "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def profiled_traffic(workload):
+    """DRAM bytes per k_sweep launch from the committed ncu capture of this workload, or None
+    when there is none or the kernel source has changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_sweep_dram_%s.json" % workload)
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        with open(os.path.join(ROOT, "paper_2606_31535_b300", "csrc", "sweep.cu"), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
+    return rec["dram_bytes_per_launch"] if rec.get("sweep_cu_sha256_16") == sha else None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -286,7 +301,8 @@ def run_ours(args):
                          % (8e-9 * info["nnz_l"], 1e-9 * info["device_bytes"])},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak if fp64_peak else None,
-                     "traffic": None,
+                     "traffic": profiled_traffic(args.workload),
+                     "traffic_note": "DRAM bytes per k_sweep launch (ncu, profiles/)",
                      "kernel": "k_sweep (FP64 DFMA; peak = DFMA throughput measured live; "
                                "mma.sync f64 measured %.3f TFLOP/s)" % peaks64["dmma"],
                      "algorithmic": "2 flops x W walk entries per step, W = %d" % info["walk_entries"]},

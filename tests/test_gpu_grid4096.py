@@ -1,0 +1,45 @@
+"""The 4096 x 4096 grid (16.7M nodes, 33.5M edges, conductances log-uniform 1e-3..1e3): the
+full-size factorization on the device, then 2000 seeded edges swept and compared with the
+oracle's values stored by tests/golden/make_grid4096_sample.py (the oracle needs about 20
+minutes of one CPU core to factor this graph, so its values are computed once)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2606_31535_b300 import inputs as I
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+TOL = 1e-9
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "grid4096_sample.json")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_31535_b300 import build, peers
+    build.build()
+    peers.load()
+    return peers
+
+
+def test_grid4096_sampled_parity(P):
+    d = json.load(open(GOLDEN))
+    g = I.grid4096()
+    u, v = g.all_edges()
+    idx = np.array(d["edge_index"])
+    # the stored sample still names the same edges of the same generator
+    assert np.array_equal(u[idx], d["u"]) and np.array_equal(v[idx], d["v"])
+    ctx = P.Context(0)
+    ctx.set_timing(True)
+    sym = P.Symbolic.of(g, 0, np.array(d["u"]), np.array(d["v"]))
+    num = P.Numeric(ctx, sym)
+    factor_s = ctx.last_stats()["factor_s"]
+    R = P.query(ctx, sym, num)
+    Ro = np.array(d["R"])
+    err = float(np.max(np.abs(R - Ro) / Ro))
+    print(f"grid4096: factor {factor_s:.2f} s on the device, max rel err {err:.3e}")
+    assert err <= TOL

@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=8000,
                     help="edges per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the largest tiles instead of running the tile autotuner")
     return ap.parse_args()
 
 
@@ -162,6 +164,12 @@ def profiled_traffic(workload):
     return rec["dram_bytes_per_launch"] if rec.get("sweep_cu_sha256_16") == sha else None
 
 
+def tuning_cache():
+    """Tile-autotuner cache file: $PEERS_TUNING_CACHE, else one in the system temp dir."""
+    return os.environ.get("PEERS_TUNING_CACHE",
+                          os.path.join(tempfile.gettempdir(), "peers_tiles.txt"))
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -227,6 +235,11 @@ def run_ours(args):
     num = P.Numeric(ctx, sym)
     nq = sym.nq
     R = torch.empty(nq, dtype=torch.float64, device=f"cuda:{local}")
+    tiles = None
+    if not args.no_autotune:
+        t0 = time.time()
+        tiles = P.autotune(ctx, sym, num, tuning_cache())
+        tiles["seconds"] = time.time() - t0
 
     for _ in range(args.warmup):
         P.query(ctx, sym, num, R)
@@ -315,6 +328,7 @@ def run_ours(args):
                 "matches_device_result": same},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "tiles": tiles,
         "analysis": {"t_analyze_s": t_analyze, "nsuper": info["nsuper"],
                      "levels": info["levels"], "nnz_l": info["nnz_l"],
                      "walk_fma": info["walk_fma"]},

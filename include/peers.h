@@ -64,7 +64,13 @@ typedef struct peers_options {
                            (0 = default 32) */
   double relax_frac;    /* tolerated fraction of explicit zeros in an amalgamated supernode
                            (0 = default 0.15) */
-  int64_t reserved[8];
+  int64_t carry_budget; /* device bytes of query fronts carried between levels per wave
+                           (0 = default 48 GiB); a smaller budget splits the queries into more
+                           waves walked one after another */
+  int32_t qcap[4];      /* sweep tile caps: at most qcap[c] queries per CTA for supernodes
+                           whose front has N rows in class c = [0,128), [128,512), [512,2048),
+                           [2048,inf); 0 = the largest tile that fits (up to 32) */
+  int64_t reserved[6];
 } peers_options;
 
 /* Statistics of an analysis (all counts exact). */
@@ -139,6 +145,24 @@ int peers_factor(peers_ctx *ctx, const peers_symbolic *sym, const double *w, pee
 int peers_numeric_diag(peers_ctx *ctx, const peers_numeric *num, double *d_host);
 void peers_free_numeric(peers_numeric *num);
 
+/* ---- tile shapes --------------------------------------------------------------------------- */
+
+/* Re-tiles a factored plan's sweep with new per-size-class caps (see peers_options.qcap) and
+ * re-uploads its work lists.  Results are unchanged bit for bit: column blocks stay aligned,
+ * so a query's arithmetic never depends on its tile.  Only the speed changes. */
+int peers_retile(peers_ctx *ctx, peers_symbolic *sym, peers_numeric *num, const int32_t qcap[4]);
+
+/* Autotuner for the sweep's tile shapes: for each front-size class it times every candidate
+ * cap (1, 2, 4, 8, 16, 32 queries per CTA) on the heaviest supernodes of that class of this
+ * plan, keeps the fastest and re-tiles the plan (as peers_retile).  `cache_path` (may be NULL)
+ * names a text file of "<GPU name>|class<c>|<cap>" lines: classes found there are not measured
+ * again, and the measured ones are added.  qcap_out receives the caps, gain_out the speed-up of
+ * each class's chosen cap over the largest tile on the timed supernodes (1 when not measured).
+ * The timing runs overwrite the plan's carried fronts; results of later peers_query calls are
+ * unaffected.  This is the batching tuner of the sweep; the paper has no counterpart. */
+int peers_autotune(peers_ctx *ctx, peers_symbolic *sym, peers_numeric *num,
+                   const char *cache_path, int32_t qcap_out[4], double gain_out[4]);
+
 /* ---- the sweep (device) ------------------------------------------------------------------ */
 
 /* Effective resistance of every query of the plan into R[0 .. peers_num_queries(sym)), in the
@@ -162,8 +186,8 @@ int peers_query(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *
  *   - Scratch: the fronts carried between levels and the running sums live in one static
  *     device array of 2 Mi doubles (16 MiB) compiled into the library; every GPU that loads
  *     the library holds it until the process exits.  A plan fits when
- *     carry_slots * (max n_b + 1) <= 2 Mi doubles: analyse with peers_options.reserved[0]
- *     (the carry budget in bytes) at most 16 MiB to bound its waves.  A plan that does not
+ *     carry_slots * (max n_b + 1) <= 2 Mi doubles: analyse with peers_options.carry_budget
+ *     at most 16 MiB to bound its waves.  A plan that does not
  *     fit is rejected with PEERS_EINVAL and a message naming both sizes.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *     and caches it; make that first call before any stream capture.

@@ -320,6 +320,223 @@ void assembly_values(const Symbolic &S, const double *w, std::vector<double> &va
   }
 }
 
+// Tiles, waves and the two-branch walk of an analysed plan for the given per-size-class
+// tile caps (queries per CTA; 0 = the largest that fits).  Rebuilding it does not change the
+// arithmetic of any query: blocks stay aligned to kBlock whatever the tile.
+int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
+  struct Two { int32_t lo, hi; int64_t idx; };
+  const int32_t kInfCol = INT32_MAX;
+  (void)kInfCol;
+  // tile sizes: as many queries as fit the shared-memory budget, up to the size class's cap
+  const int32_t ns = S.nsuper;
+  for (int c = 0; c < kSizeClasses; ++c)
+    S.qcap[c] = qcap && qcap[c] > 0 ? std::min<int32_t>(qcap[c], kQMax) : kQMax;
+  S.qtile.assign(static_cast<size_t>(ns), 1);
+  for (int32_t s = 0; s < ns; ++s) {
+    const int64_t N = sn_nc(S, s) + S.nb[s];
+    int64_t q = kSweepSmemBudget / (8 * (N + 2 * kBlock));
+    q = std::min<int64_t>(q, S.qcap[size_class(N)]);
+    if (q >= 4) q -= q % 4;
+    S.qtile[s] = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(kQMax, q)));
+    if (sweep_smem_bytes(N, S.qtile[s]) > kMaxSmem) {
+      err = "supernode front of " + std::to_string(N) + " rows exceeds one CTA's shared memory";
+      return PEERS_ENOMEM;
+    }
+  }
+
+  // waves: bound the carry buffer (one slot of nbmax doubles per query in flight)
+  const int64_t budget = S.carry_budget;
+  const int64_t slot_bytes = std::max<int64_t>(8, int64_t(8) * S.nbmax);
+  int64_t per_wave = std::max<int64_t>(1, budget / slot_bytes);
+  if (per_wave > INT32_MAX) per_wave = INT32_MAX;
+  S.waves.clear();
+  S.carry_slots = 0;
+  S.walk_entries = 0;
+  S.walk_fma = 0;
+  auto item_fma = [&](int32_t s, int32_t j0) -> int64_t {
+    const int64_t nc = sn_nc(S, s), N = nc + S.nb[s];
+    int64_t f = 0;
+    for (int64_t J = j0; J < nc; J += kBlock) {
+      const int64_t bw = std::min<int64_t>(kBlock, nc - J);
+      f += bw * (bw - 1) / 2 + (N - J - bw) * bw + bw;
+    }
+    return f;
+  };
+  auto entries = [&](int32_t s, int64_t first_col) -> int64_t {
+    const int64_t np = sn_nc(S, s) - first_col;
+    return np * (np - 1) / 2 + int64_t(S.nb[s]) * np + np;
+  };
+  for (int64_t w0 = 0; w0 < std::max<int64_t>(S.nsorted, 1); w0 += per_wave) {
+    SweepWave W;
+    W.q_begin = w0;
+    W.q_end = std::min<int64_t>(S.nsorted, w0 + per_wave);
+    if (W.q_end <= W.q_begin && S.nsorted > 0) break;
+    S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
+    W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+    std::vector<std::pair<int64_t, SweepItem>> lv;
+    for (int32_t l = 0; l < S.nlevels; ++l) {
+      lv.clear();
+      for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
+        const int32_t p = S.level_sn[i];
+        const int32_t tile = S.qtile[p];
+        auto emit = [&](int32_t src, int64_t b, int64_t e) {
+          b = std::max(b, W.q_begin);
+          e = std::min(e, W.q_end);
+          for (int64_t q = b; q < e; q += tile) {
+            SweepItem it{};
+            it.s = p;
+            it.src = src;
+            it.q0 = static_cast<int32_t>(q);
+            it.nq = static_cast<int32_t>(std::min<int64_t>(tile, e - q));
+            int32_t j0;
+            if (src >= 0) {
+              j0 = S.rmap[S.rows_off[src]];
+              S.walk_entries += it.nq * entries(p, j0);
+            } else {
+              j0 = S.qa[q];
+              for (int64_t k = q; k < q + it.nq; ++k) S.walk_entries += entries(p, S.qa[k]);
+            }
+            it.j0 = (j0 / kBlock) * kBlock;
+            const int64_t f = it.nq * item_fma(p, it.j0);
+            S.walk_fma += f;
+            lv.push_back({f, it});
+          }
+        };
+        for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
+          const int32_t ch = S.child_list[c];
+          emit(ch, S.qbeg[S.fdesc[ch]], S.qbeg[ch + 1]);
+        }
+        emit(-1, S.qbeg[p], S.qbeg[p + 1]);
+      }
+      std::stable_sort(lv.begin(), lv.end(),
+                       [](const auto &x, const auto &y) { return x.first > y.first; });
+      int64_t smem = 0;
+      for (auto &x : lv) {
+        W.items.push_back(x.second);
+        const int32_t s = x.second.s;
+        smem = std::max(smem, sweep_smem_bytes(sn_nc(S, s) + S.nb[s], x.second.nq));
+      }
+      W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
+      W.level_smem.push_back(smem);
+    }
+    S.waves.push_back(std::move(W));
+    if (S.nsorted == 0) break;
+  }
+  if (S.nsorted == 0 && S.nq_two > 0) S.waves.clear();
+
+  // ---- two-branch walk (listed pairs whose etree paths merge above the start) ----
+  // Slots nsorted + 2k (branch of the lower endpoint, continues after the merge) and
+  // nsorted + 2k + 1 (branch of the upper endpoint, ends at the merge supernode).
+  S.ldesc.clear();
+  S.two_user.clear();
+  S.two_a.clear();
+  S.two_b.clear();
+  if (S.nq_two > 0) {
+    std::vector<int32_t> depth(static_cast<size_t>(ns), 0);
+    for (int32_t s = ns - 1; s >= 0; --s)
+      depth[s] = S.parent[s] == -1 ? 0 : depth[S.parent[s]] + 1;
+    const int64_t per_two = std::max<int64_t>(1, per_wave / 2);
+    const int32_t kInf = INT32_MAX;
+    for (int64_t k0 = 0; k0 < S.nq_two; k0 += per_two) {
+      const int64_t k1 = std::min<int64_t>(S.nq_two, k0 + per_two);
+      std::vector<std::pair<int32_t, SweepDesc>> steps;   // (supernode, step)
+      for (int64_t k = k0; k < k1; ++k) {
+        const Two t{S.two_lo[k], S.two_hi[k], S.two_idx[k]};
+        const int32_t sa = S.col2sn[t.lo], sb = S.col2sn[t.hi];
+        const int32_t A = static_cast<int32_t>(S.nsorted + 2 * k), B = A + 1;
+        S.qorig[A] = S.qorig[B] = t.idx;
+        S.qa[A] = t.lo - S.first[sa];
+        S.qb[A] = -1;
+        S.qa[B] = -1;
+        S.qb[B] = t.hi - S.first[sb];
+        // merge supernode = lowest common ancestor of sa and sb (-1: different trees)
+        int32_t x = sa, y = sb;
+        while (x != y && x != -1 && y != -1) {
+          if (depth[x] >= depth[y]) x = S.parent[x]; else y = S.parent[y];
+        }
+        const int32_t m = (x == y) ? x : -1;
+        int32_t prev = -1;
+        for (int32_t p = sa; p != m; prev = p, p = S.parent[p])
+          steps.push_back({p, SweepDesc{A, prev, -1, -1, -1}});
+        const int32_t child_a = prev;
+        prev = -1;
+        if (sb != m)
+          for (int32_t p = sb; p != m; prev = p, p = S.parent[p])
+            steps.push_back({p, SweepDesc{B, prev, -1, -1, -1}});
+        const int32_t child_b = prev;
+        if (m != -1) {
+          if (sb == m)
+            steps.push_back({m, SweepDesc{A, child_a, -1, -1, t.hi - S.first[m]}});
+          else
+            steps.push_back({m, SweepDesc{A, child_a, B, child_b, -1}});
+          prev = m;
+          for (int32_t p = S.parent[m]; p != -1; prev = p, p = S.parent[p])
+            steps.push_back({p, SweepDesc{A, prev, -1, -1, -1}});
+        }
+        S.two_user.push_back(t.idx);
+        S.two_a.push_back(A);
+        S.two_b.push_back(m == -1 ? B : -1);
+      }
+      std::stable_sort(steps.begin(), steps.end(), [&](const auto &u, const auto &v) {
+        if (S.level[u.first] != S.level[v.first]) return S.level[u.first] < S.level[v.first];
+        return u.first < v.first;
+      });
+      SweepWave W;
+      W.q_begin = S.nsorted + 2 * k0;
+      W.q_end = S.nsorted + 2 * k1;
+      W.two_begin = k0;
+      W.two_end = k1;
+      S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
+      W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+      W.level_smem.assign(static_cast<size_t>(S.nlevels), 0);
+      auto first_row = [&](const SweepDesc &d) -> int32_t {
+        int32_t r = kInf;
+        if (d.src_a >= 0) r = S.rmap[S.rows_off[d.src_a]];
+        else {
+          if (S.qa[d.a] >= 0) r = std::min(r, S.qa[d.a]);
+          if (S.qb[d.a] >= 0) r = std::min(r, S.qb[d.a]);
+        }
+        if (d.b >= 0) r = std::min(r, S.rmap[S.rows_off[d.src_b]]);
+        else if (d.seed_b >= 0) r = std::min(r, d.seed_b);
+        return r;
+      };
+      size_t i = 0;
+      for (int32_t l = 0; l < S.nlevels; ++l) {
+        while (i < steps.size() && S.level[steps[i].first] == l) {
+          const int32_t p = steps[i].first;
+          size_t e = i;
+          while (e < steps.size() && steps[e].first == p) ++e;
+          for (size_t c = i; c < e; c += S.qtile[p]) {
+            const size_t ce = std::min(e, c + static_cast<size_t>(S.qtile[p]));
+            SweepItem it{};
+            it.s = p;
+            it.src = -1;
+            it.kind = 1;
+            it.q0 = static_cast<int32_t>(S.ldesc.size());
+            it.nq = static_cast<int32_t>(ce - c);
+            int32_t j0 = kInf;
+            for (size_t q = c; q < ce; ++q) {
+              const int32_t fr = first_row(steps[q].second);
+              j0 = std::min(j0, fr);
+              S.walk_entries += entries(p, fr);
+              S.ldesc.push_back(steps[q].second);
+            }
+            it.j0 = (j0 / kBlock) * kBlock;
+            S.walk_fma += it.nq * item_fma(p, it.j0);
+            W.items.push_back(it);
+            W.level_smem[l] = std::max(W.level_smem[l],
+                                       sweep_smem_bytes(sn_nc(S, p) + S.nb[p], it.nq));
+          }
+          i = e;
+        }
+        W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
+      }
+      S.waves.push_back(std::move(W));
+    }
+  }
+  return PEERS_OK;
+}
+
 // ------------------------------------------------------------------------- analyze
 
 int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indices,
@@ -751,209 +968,19 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   }
   for (int32_t s = 0; s < ns; ++s) S.qbeg[s + 1] += S.qbeg[s];
 
-  // tile sizes: as many queries as fit the shared-memory budget, up to kQMax
-  S.qtile.assign(static_cast<size_t>(ns), 1);
-  for (int32_t s = 0; s < ns; ++s) {
-    const int64_t N = sn_nc(S, s) + S.nb[s];
-    int64_t q = kSweepSmemBudget / (8 * (N + 2 * kBlock));
-    if (q >= 4) q -= q % 4;
-    S.qtile[s] = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(kQMax, q)));
-    if (sweep_smem_bytes(N, S.qtile[s]) > kMaxSmem) {
-      err = "supernode front of " + std::to_string(N) + " rows exceeds one CTA's shared memory";
-      return PEERS_ENOMEM;
-    }
+  S.two_lo.resize(twos.size());
+  S.two_hi.resize(twos.size());
+  S.two_idx.resize(twos.size());
+  for (size_t k = 0; k < twos.size(); ++k) {
+    S.two_lo[k] = twos[k].lo;
+    S.two_hi[k] = twos[k].hi;
+    S.two_idx[k] = twos[k].idx;
   }
-
-  // waves: bound the carry buffer (one slot of nbmax doubles per query in flight)
-  int64_t budget = opt.reserved[0] > 0 ? opt.reserved[0] : (int64_t(48) << 30);
-  const int64_t slot_bytes = std::max<int64_t>(8, int64_t(8) * S.nbmax);
-  int64_t per_wave = std::max<int64_t>(1, budget / slot_bytes);
-  if (per_wave > INT32_MAX) per_wave = INT32_MAX;
-  S.waves.clear();
-  S.carry_slots = 0;
-  S.walk_entries = 0;
-  S.walk_fma = 0;
-  auto item_fma = [&](int32_t s, int32_t j0) -> int64_t {
-    const int64_t nc = sn_nc(S, s), N = nc + S.nb[s];
-    int64_t f = 0;
-    for (int64_t J = j0; J < nc; J += kBlock) {
-      const int64_t bw = std::min<int64_t>(kBlock, nc - J);
-      f += bw * (bw - 1) / 2 + (N - J - bw) * bw + bw;
-    }
-    return f;
-  };
-  auto entries = [&](int32_t s, int64_t first_col) -> int64_t {
-    const int64_t np = sn_nc(S, s) - first_col;
-    return np * (np - 1) / 2 + int64_t(S.nb[s]) * np + np;
-  };
-  for (int64_t w0 = 0; w0 < std::max<int64_t>(S.nsorted, 1); w0 += per_wave) {
-    SweepWave W;
-    W.q_begin = w0;
-    W.q_end = std::min<int64_t>(S.nsorted, w0 + per_wave);
-    if (W.q_end <= W.q_begin && S.nsorted > 0) break;
-    S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
-    W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
-    std::vector<std::pair<int64_t, SweepItem>> lv;
-    for (int32_t l = 0; l < S.nlevels; ++l) {
-      lv.clear();
-      for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
-        const int32_t p = S.level_sn[i];
-        const int32_t tile = S.qtile[p];
-        auto emit = [&](int32_t src, int64_t b, int64_t e) {
-          b = std::max(b, W.q_begin);
-          e = std::min(e, W.q_end);
-          for (int64_t q = b; q < e; q += tile) {
-            SweepItem it{};
-            it.s = p;
-            it.src = src;
-            it.q0 = static_cast<int32_t>(q);
-            it.nq = static_cast<int32_t>(std::min<int64_t>(tile, e - q));
-            int32_t j0;
-            if (src >= 0) {
-              j0 = S.rmap[S.rows_off[src]];
-              S.walk_entries += it.nq * entries(p, j0);
-            } else {
-              j0 = S.qa[q];
-              for (int64_t k = q; k < q + it.nq; ++k) S.walk_entries += entries(p, S.qa[k]);
-            }
-            it.j0 = (j0 / kBlock) * kBlock;
-            const int64_t f = it.nq * item_fma(p, it.j0);
-            S.walk_fma += f;
-            lv.push_back({f, it});
-          }
-        };
-        for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
-          const int32_t ch = S.child_list[c];
-          emit(ch, S.qbeg[S.fdesc[ch]], S.qbeg[ch + 1]);
-        }
-        emit(-1, S.qbeg[p], S.qbeg[p + 1]);
-      }
-      std::stable_sort(lv.begin(), lv.end(),
-                       [](const auto &x, const auto &y) { return x.first > y.first; });
-      int64_t smem = 0;
-      for (auto &x : lv) {
-        W.items.push_back(x.second);
-        const int32_t s = x.second.s;
-        smem = std::max(smem, sweep_smem_bytes(sn_nc(S, s) + S.nb[s], x.second.nq));
-      }
-      W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
-      W.level_smem.push_back(smem);
-    }
-    S.waves.push_back(std::move(W));
-    if (S.nsorted == 0) break;
-  }
-  if (S.nsorted == 0 && S.nq_two > 0) S.waves.clear();
-
-  // ---- two-branch walk (listed pairs whose etree paths merge above the start) ----
-  // Slots nsorted + 2k (branch of the lower endpoint, continues after the merge) and
-  // nsorted + 2k + 1 (branch of the upper endpoint, ends at the merge supernode).
-  S.ldesc.clear();
-  S.two_user.clear();
-  S.two_a.clear();
-  S.two_b.clear();
-  if (S.nq_two > 0) {
-    std::vector<int32_t> depth(static_cast<size_t>(ns), 0);
-    for (int32_t s = ns - 1; s >= 0; --s)
-      depth[s] = S.parent[s] == -1 ? 0 : depth[S.parent[s]] + 1;
-    const int64_t per_two = std::max<int64_t>(1, per_wave / 2);
-    const int32_t kInf = INT32_MAX;
-    for (int64_t k0 = 0; k0 < S.nq_two; k0 += per_two) {
-      const int64_t k1 = std::min<int64_t>(S.nq_two, k0 + per_two);
-      std::vector<std::pair<int32_t, SweepDesc>> steps;   // (supernode, step)
-      for (int64_t k = k0; k < k1; ++k) {
-        const Two &t = twos[k];
-        const int32_t sa = S.col2sn[t.lo], sb = S.col2sn[t.hi];
-        const int32_t A = static_cast<int32_t>(S.nsorted + 2 * k), B = A + 1;
-        S.qorig[A] = S.qorig[B] = t.idx;
-        S.qa[A] = t.lo - S.first[sa];
-        S.qb[A] = -1;
-        S.qa[B] = -1;
-        S.qb[B] = t.hi - S.first[sb];
-        // merge supernode = lowest common ancestor of sa and sb (-1: different trees)
-        int32_t x = sa, y = sb;
-        while (x != y && x != -1 && y != -1) {
-          if (depth[x] >= depth[y]) x = S.parent[x]; else y = S.parent[y];
-        }
-        const int32_t m = (x == y) ? x : -1;
-        int32_t prev = -1;
-        for (int32_t p = sa; p != m; prev = p, p = S.parent[p])
-          steps.push_back({p, SweepDesc{A, prev, -1, -1, -1}});
-        const int32_t child_a = prev;
-        prev = -1;
-        if (sb != m)
-          for (int32_t p = sb; p != m; prev = p, p = S.parent[p])
-            steps.push_back({p, SweepDesc{B, prev, -1, -1, -1}});
-        const int32_t child_b = prev;
-        if (m != -1) {
-          if (sb == m)
-            steps.push_back({m, SweepDesc{A, child_a, -1, -1, t.hi - S.first[m]}});
-          else
-            steps.push_back({m, SweepDesc{A, child_a, B, child_b, -1}});
-          prev = m;
-          for (int32_t p = S.parent[m]; p != -1; prev = p, p = S.parent[p])
-            steps.push_back({p, SweepDesc{A, prev, -1, -1, -1}});
-        }
-        S.two_user.push_back(t.idx);
-        S.two_a.push_back(A);
-        S.two_b.push_back(m == -1 ? B : -1);
-      }
-      std::stable_sort(steps.begin(), steps.end(), [&](const auto &u, const auto &v) {
-        if (S.level[u.first] != S.level[v.first]) return S.level[u.first] < S.level[v.first];
-        return u.first < v.first;
-      });
-      SweepWave W;
-      W.q_begin = S.nsorted + 2 * k0;
-      W.q_end = S.nsorted + 2 * k1;
-      W.two_begin = k0;
-      W.two_end = k1;
-      S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
-      W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
-      W.level_smem.assign(static_cast<size_t>(S.nlevels), 0);
-      auto first_row = [&](const SweepDesc &d) -> int32_t {
-        int32_t r = kInf;
-        if (d.src_a >= 0) r = S.rmap[S.rows_off[d.src_a]];
-        else {
-          if (S.qa[d.a] >= 0) r = std::min(r, S.qa[d.a]);
-          if (S.qb[d.a] >= 0) r = std::min(r, S.qb[d.a]);
-        }
-        if (d.b >= 0) r = std::min(r, S.rmap[S.rows_off[d.src_b]]);
-        else if (d.seed_b >= 0) r = std::min(r, d.seed_b);
-        return r;
-      };
-      size_t i = 0;
-      for (int32_t l = 0; l < S.nlevels; ++l) {
-        while (i < steps.size() && S.level[steps[i].first] == l) {
-          const int32_t p = steps[i].first;
-          size_t e = i;
-          while (e < steps.size() && steps[e].first == p) ++e;
-          for (size_t c = i; c < e; c += S.qtile[p]) {
-            const size_t ce = std::min(e, c + static_cast<size_t>(S.qtile[p]));
-            SweepItem it{};
-            it.s = p;
-            it.src = -1;
-            it.kind = 1;
-            it.q0 = static_cast<int32_t>(S.ldesc.size());
-            it.nq = static_cast<int32_t>(ce - c);
-            int32_t j0 = kInf;
-            for (size_t q = c; q < ce; ++q) {
-              const int32_t fr = first_row(steps[q].second);
-              j0 = std::min(j0, fr);
-              S.walk_entries += entries(p, fr);
-              S.ldesc.push_back(steps[q].second);
-            }
-            it.j0 = (j0 / kBlock) * kBlock;
-            S.walk_fma += it.nq * item_fma(p, it.j0);
-            W.items.push_back(it);
-            W.level_smem[l] = std::max(W.level_smem[l],
-                                       sweep_smem_bytes(sn_nc(S, p) + S.nb[p], it.nq));
-          }
-          i = e;
-        }
-        W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
-      }
-      S.waves.push_back(std::move(W));
-    }
-  }
+  S.carry_budget = opt.carry_budget > 0 ? opt.carry_budget : (int64_t(48) << 30);
+  int32_t caps[kSizeClasses];
+  for (int c = 0; c < kSizeClasses; ++c) caps[c] = opt.qcap[c];
+  st = build_sweep_plan(S, caps, err);
+  if (st != PEERS_OK) return st;
   S.t_queries = since(t2);
   return PEERS_OK;
 }

@@ -67,6 +67,35 @@ void dfree(peers_numeric *num, void *p) {
     if (rc_ != PEERS_OK) return rc_; \
   } while (0)
 
+// The tile-dependent part of the sweep plan: work items of every wave and the two-branch
+// walk's steps (replaced after a re-tiling).
+int upload_tiles(peers_numeric *num, const Symbolic &S, cudaStream_t st, std::string &err) {
+  for (void *p : {static_cast<void *>(num->items), static_cast<void *>(num->ldesc),
+                  static_cast<void *>(num->two_user), static_cast<void *>(num->two_a),
+                  static_cast<void *>(num->two_b)})
+    if (p) dfree(num, p);
+  num->items = nullptr;
+  num->ldesc = nullptr;
+  num->two_user = nullptr;
+  num->two_a = num->two_b = nullptr;
+  std::vector<SweepItem> all;
+  num->wave_item_off.clear();
+  for (const auto &W : S.waves) {
+    num->wave_item_off.push_back(static_cast<int64_t>(all.size()));
+    all.insert(all.end(), W.items.begin(), W.items.end());
+  }
+  TRY(upload(num, &num->items, all, st, err));
+  TRY(upload(num, &num->ldesc, S.ldesc, st, err));
+  TRY(upload(num, &num->two_user, S.two_user, st, err));
+  TRY(upload(num, &num->two_a, S.two_a, st, err));
+  TRY(upload(num, &num->two_b, S.two_b, st, err));
+  // the carry buffer is sized by the plan's waves: drop it, the next query re-allocates
+  if (num->carry) dfree(num, num->carry);
+  if (num->racc) dfree(num, num->racc);
+  num->carry = num->racc = nullptr;
+  return PEERS_OK;
+}
+
 int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peers_numeric *num,
                 std::string &err) {
   const Symbolic &S = sym->S;
@@ -138,32 +167,38 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
   TRY(upload(num, &num->qa, S.qa, st, err));
   TRY(upload(num, &num->qb, S.qb, st, err));
   TRY(upload(num, &num->qorig, S.qorig, st, err));
-  std::vector<SweepItem> all;
-  num->wave_item_off.clear();
-  for (const auto &W : S.waves) {
-    num->wave_item_off.push_back(static_cast<int64_t>(all.size()));
-    all.insert(all.end(), W.items.begin(), W.items.end());
-  }
-  TRY(upload(num, &num->items, all, st, err));
-  TRY(upload(num, &num->ldesc, S.ldesc, st, err));
-  TRY(upload(num, &num->two_user, S.two_user, st, err));
-  TRY(upload(num, &num->two_a, S.two_a, st, err));
-  TRY(upload(num, &num->two_b, S.two_b, st, err));
+  TRY(upload_tiles(num, S, st, err));
   CUDA_TRY(cudaStreamSynchronize(st));
   ctx->stats.h2d_bytes = num->h2d_bytes;
   ctx->stats.d2h_bytes = 2 * sizeof(int);
   return PEERS_OK;
 }
 
+}  // namespace
+
+int ensure_carry(peers_numeric *num, const Symbolic &S, std::string &err) {
+  if (!num->carry && S.carry_slots > 0) {
+    TRY(dalloc(num, &num->carry, std::max<int64_t>(1, S.carry_slots * S.nbmax), err));
+    TRY(dalloc(num, &num->racc, S.carry_slots, err));
+  }
+  return PEERS_OK;
+}
+
+int refresh_tiles(peers_ctx *ctx, const Symbolic &S, peers_numeric *num, std::string &err) {
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  TRY(upload_tiles(num, S, ctx->stream, err));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return PEERS_OK;
+}
+
+namespace {
+
 int query_impl(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, double *R,
                int flags, std::string &err) {
   const Symbolic &S = sym->S;
   cudaStream_t st = ctx->stream;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  if (!num->carry && S.carry_slots > 0) {
-    TRY(dalloc(num, &num->carry, std::max<int64_t>(1, S.carry_slots * S.nbmax), err));
-    TRY(dalloc(num, &num->racc, S.carry_slots, err));
-  }
+  TRY(ensure_carry(num, S, err));
   double *Rout = R;
   const bool host_out = !(flags & PEERS_OUT_DEVICE);
   if (host_out) {

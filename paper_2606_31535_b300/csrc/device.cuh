@@ -75,6 +75,10 @@ int run_two_branch_combine(const SweepArgs &args, const int64_t *two_user, const
                            const int32_t *two_b, int64_t k0, int64_t k1, cudaStream_t stream,
                            int64_t *launches, std::string &err);
 
+// One k_sweep launch over an arbitrary item list (the autotuner's timing runs).
+int run_items(const SweepItem *d_items, int64_t n, const SweepArgs &args, int64_t smem,
+              cudaStream_t stream, std::string &err);
+
 // One launch of the multi-graph (persistent) sweep kernel: nitems items, each with its
 // argument block table[item.g]; CTAs pull items through *counter (zero before the launch).
 int run_multi_step(const SweepItem *items, int64_t nitems, const SweepArgs *table, int *counter,

@@ -71,3 +71,8 @@ inline peers::SweepArgs sweep_args_of(const peers_numeric *num, const Symbolic &
 
 // Records a failure message for peers_last_error and returns the status.
 int peers_fail(int status, const std::string &msg);
+
+// Allocates the sweep's carry buffer of a factored plan if it has none (capi.cu).
+int ensure_carry(peers_numeric *num, const Symbolic &S, std::string &err);
+// Re-uploads the tile-dependent sweep plan after build_sweep_plan (capi.cu).
+int refresh_tiles(peers_ctx *ctx, const Symbolic &S, peers_numeric *num, std::string &err);

@@ -38,6 +38,11 @@ PEERS_HD inline int64_t sweep_smem_bytes(int64_t N, int64_t Q) {
   return (N + 2 * kBlock) * sweep_qstride(Q) * 8;
 }
 
+// Front-size classes of the sweep's tile policy: rows N of a supernode's front in
+// [0,128), [128,512), [512,2048), [2048,inf).
+constexpr int kSizeClasses = 4;
+inline int size_class(int64_t N) { return N < 128 ? 0 : N < 512 ? 1 : N < 2048 ? 2 : 3; }
+
 // One unit of sweep work at supernode s.
 //   kind 0 (range): the query slots [q0, q0+nq) of the sorted order.  src >= 0: they arrive
 //     from child supernode src (their carries are scattered through src's relative map);
@@ -141,6 +146,10 @@ struct Symbolic {
   std::vector<int32_t> qa, qb;      // local seed rows (+1 at qa, -1 at qb; qb = -1: none)
   std::vector<int64_t> qbeg;        // nsuper + 1: first slot whose start supernode is >= s
   std::vector<int32_t> qtile;       // tile size (queries per CTA) per supernode
+  int32_t qcap[kSizeClasses] = {kQMax, kQMax, kQMax, kQMax};   // tile caps in use
+  int64_t carry_budget = 0;         // bytes of carried fronts per wave
+  std::vector<int32_t> two_lo, two_hi;   // two-branch queries (elimination positions)
+  std::vector<int64_t> two_idx;          // and their user indices
   int32_t nbmax = 0;
   std::vector<SweepWave> waves;
   // two-branch walk: step descriptors, and per such query (user index, slot a, slot b of a
@@ -157,6 +166,9 @@ struct Symbolic {
 int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indices,
             const double *w, int32_t ground, int64_t nq, const int32_t *qu, const int32_t *qv,
             const double *coords, int dim, const peers_options &opt, std::string &err);
+
+// (Re)builds the sweep's tiles and waves of an analysed plan (analyze.cpp).
+int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err);
 
 // Conductance-dependent assembly values (off-diagonals -w, then diagonals = degrees) in the
 // order of a_dest, for conductances w (CSR layout of the analysed graph).

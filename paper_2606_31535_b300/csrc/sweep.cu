@@ -217,13 +217,29 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_multi(const SweepItem *
   }
 }
 
-int multi_step_grid(int64_t smem, int64_t nitems, int64_t *grid, std::string &err) {
-  static int configured_smem = 0;
-  if (smem > configured_smem) {
-    CUDA_TRY(cudaFuncSetAttribute(k_sweep_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem)));
-    configured_smem = static_cast<int>(smem);
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`
+// (the limit only ever grows, so launches configured earlier stay valid).
+template <class K>
+int ensure_smem(K kernel, int *configured, int64_t bytes, std::string &err) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    err = "device index out of range";
+    return PEERS_EINVAL;
   }
+  if (bytes > configured[dev]) {
+    CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(bytes)));
+    configured[dev] = static_cast<int>(bytes);
+  }
+  return PEERS_OK;
+}
+int g_sweep_smem[64] = {};
+int g_multi_smem[64] = {};
+
+int multi_step_grid(int64_t smem, int64_t nitems, int64_t *grid, std::string &err) {
+  int rc = ensure_smem(k_sweep_multi, g_multi_smem, smem, err);
+  if (rc != PEERS_OK) return rc;
   int dev = 0, sms = 0, per_sm = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -242,17 +258,14 @@ int run_multi_step(const SweepItem *items, int64_t nitems, const SweepArgs *tabl
   return PEERS_OK;
 }
 
+
 int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_items,
                    const SweepArgs &args, cudaStream_t stream, cudaEvent_t *events,
                    int64_t *launches, std::string &err) {
-  static int configured_smem = 0;   // per process; the kernel's limit only grows
   int64_t need = 0;
   for (int64_t b : W.level_smem) need = std::max(need, b);
-  if (need > configured_smem) {
-    CUDA_TRY(cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(need)));
-    configured_smem = static_cast<int>(need);
-  }
+  int rc = ensure_smem(k_sweep, g_sweep_smem, need, err);
+  if (rc != PEERS_OK) return rc;
   SweepArgs a = args;
   a.wave_base = W.q_begin;
   for (int32_t l = 0; l < S.nlevels; ++l) {
@@ -266,6 +279,16 @@ int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_ite
     }
     if (events) CUDA_TRY(cudaEventRecord(events[2 * l + 1], stream));
   }
+  return PEERS_OK;
+}
+
+int run_items(const SweepItem *d_items, int64_t n, const SweepArgs &args, int64_t smem,
+              cudaStream_t stream, std::string &err) {
+  int rc = ensure_smem(k_sweep, g_sweep_smem, smem, err);
+  if (rc != PEERS_OK) return rc;
+  if (n <= 0) return PEERS_OK;
+  k_sweep<<<static_cast<unsigned>(n), kSweepThreads, smem, stream>>>(d_items, args);
+  CUDA_TRY(cudaGetLastError());
   return PEERS_OK;
 }
 

@@ -59,7 +59,7 @@ int query_noalloc(cudaStream_t stream, int device, const Symbolic &S, const Swee
   if (need > kNoAllocScratchDoubles) {
     err = "the plan needs " + std::to_string(need) + " doubles of sweep scratch but the "
           "static buffer holds " + std::to_string(kNoAllocScratchDoubles) +
-          "; analyse with a smaller carry budget (peers_options.reserved[0] <= " +
+          "; analyse with a smaller carry budget (peers_options.carry_budget <= " +
           std::to_string(kNoAllocScratchDoubles * 8) + " bytes) or use peers_query";
     return PEERS_EINVAL;
   }

@@ -31,7 +31,8 @@ class PeersError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("ordering", ctypes.c_int32), ("nd_leaf", ctypes.c_int32),
                 ("relax_small", ctypes.c_int32), ("relax_max", ctypes.c_int32),
-                ("relax_frac", ctypes.c_double), ("reserved", ctypes.c_int64 * 8)]
+                ("relax_frac", ctypes.c_double), ("carry_budget", ctypes.c_int64),
+                ("qcap", ctypes.c_int32 * 4), ("reserved", ctypes.c_int64 * 6)]
 
 
 class Stats(ctypes.Structure):
@@ -103,6 +104,8 @@ def load(path: str | None = None):
         "peers_server_wait": (ctypes.c_int, [vp, i64, vp, i64, P(dbl)]),
         "peers_server_get_stats": (ctypes.c_int, [vp, P(ServerStats)]),
         "peers_server_destroy": (None, [vp]),
+        "peers_retile": (ctypes.c_int, [vp, vp, vp, vp]),
+        "peers_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_char_p, vp, vp]),
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "peers_last_stats": (ctypes.c_int, [vp, P(Stats)]),
         "peers_fp64_peak": (ctypes.c_int, [vp, P(dbl)]),
@@ -262,6 +265,23 @@ class Numeric:
         d = np.empty(self._sym.info()["n_reduced"], np.float64)
         _check(load().peers_numeric_diag(self._ctx._h, self._h, _ptr(d)), "peers_numeric_diag")
         return d
+
+
+def retile(ctx: Context, sym: Symbolic, num: Numeric, qcap):
+    """Re-tiles a factored plan with per-size-class caps (4 ints; 0 = largest that fits)."""
+    caps = np.ascontiguousarray(qcap, dtype=np.int32)
+    _check(load().peers_retile(ctx._h, sym._h, num._h, _ptr(caps)), "peers_retile")
+
+
+def autotune(ctx: Context, sym: Symbolic, num: Numeric, cache_path: str | None = None) -> dict:
+    """Times the candidate tile caps per front-size class on this plan, re-tiles it with the
+    fastest, and records them in `cache_path`.  Returns {"qcap": [...], "gain": [...]}."""
+    caps = np.zeros(4, dtype=np.int32)
+    gain = np.zeros(4, dtype=np.float64)
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(load().peers_autotune(ctx._h, sym._h, num._h, path, _ptr(caps), _ptr(gain)),
+           "peers_autotune")
+    return {"qcap": caps.tolist(), "gain": gain.tolist()}
 
 
 def query(ctx: Context, sym: Symbolic, num: Numeric, out=None):

@@ -173,7 +173,7 @@ def test_two_branch_pairs_are_planned(P):
 def test_wave_budget_option(P):
     g = I.grid2d(20, 20, seed=2)
     opt = P.Options()
-    opt.reserved[0] = 64 * 1024
+    opt.carry_budget = 64 * 1024
     small = P.Symbolic.of(g, options=opt)
     big = P.Symbolic.of(g)
     assert small.footprint_bytes() < big.footprint_bytes()

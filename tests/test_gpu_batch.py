@@ -42,7 +42,7 @@ def test_batch_equals_single_sweeps(P, oracle_mod, cuda_graph):
             s = P.Symbolic.of(g, 0, pu, pv)
         elif i == 4:   # and one with many waves
             opt = P.Options()
-            opt.reserved[0] = 128 * 1024
+            opt.carry_budget = 128 * 1024
             s = P.Symbolic.of(g, options=opt)
         else:
             s = P.Symbolic.of(g)

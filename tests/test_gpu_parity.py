@@ -198,8 +198,31 @@ def test_many_waves(P, ctx, oracle_mod):
     qu = np.concatenate([u, pu])
     qv = np.concatenate([v, pv])
     opt = P.Options()
-    opt.reserved[0] = 256 * 1024   # bytes of carry per wave
+    opt.carry_budget = 256 * 1024   # bytes of carry per wave
     R, sym = run(P, ctx, g, qu, qv, options=opt)
     Rfull, _ = run(P, ctx, g, qu, qv)
     assert np.array_equal(R, Rfull)
     assert maxrel(R, oracle_mod.resistance(g, qu, qv)) <= TOL
+
+
+def test_autotune_and_retile_keep_results(P, ctx, tmp_path):
+    """Tile shapes change speed only: results are bit-identical under any caps, the tuner
+    picks caps from its candidate set, and a second run reads them from the cache file."""
+    g = I.grid2d(150, 160, seed=26, law="loguniform", lo=1e-2, hi=1e2)
+    pu, pv = I.random_pairs(g.n, 500, seed=27)
+    u, v = g.all_edges()
+    qu = np.concatenate([u, pu])
+    qv = np.concatenate([v, pv])
+    sym = P.Symbolic.of(g, 0, qu, qv)
+    num = P.Numeric(ctx, sym)
+    R0 = P.query(ctx, sym, num)
+    P.retile(ctx, sym, num, [4, 8, 2, 1])
+    assert np.array_equal(P.query(ctx, sym, num), R0)
+    cache = str(tmp_path / "tiles.txt")
+    res = P.autotune(ctx, sym, num, cache)
+    assert all(c in (1, 2, 4, 8, 16, 32) for c in res["qcap"])
+    assert np.array_equal(P.query(ctx, sym, num), R0)
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) >= 2 and all("|class" in x for x in lines)
+    res2 = P.autotune(ctx, sym, num, cache)
+    assert res2["qcap"] == res["qcap"] and all(x == 1.0 for x in res2["gain"])

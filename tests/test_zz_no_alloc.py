@@ -32,7 +32,7 @@ def test_noalloc_matches_query_on_two_calls_in_a_row(P):
     qu = np.concatenate([u, pu, [7]]).astype(np.int32)
     qv = np.concatenate([v, pv, [7]]).astype(np.int32)   # and one u == v query
     opt = P.Options()
-    opt.reserved[0] = 8 << 20     # carry budget (bytes) inside the 16 MiB static scratch
+    opt.carry_budget = 8 << 20     # carry budget (bytes) inside the 16 MiB static scratch
     ctx = P.Context(0)
     sym = P.Symbolic.of(g, 0, qu, qv, True, opt)
     num = P.Numeric(ctx, sym)

@@ -123,12 +123,17 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
     for (int32_t u = tid; u < units; u += kSweepThreads) {
       const int32_t i = J + bw + u / nch;
       const int c = u - (u / nch) * nch;
-      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+      // x_i -= l_k y_k, one fused multiply-add per term, in k order (the update of x_i
+      // starts from x_i itself, so no separate subtraction is needed)
+      double *xi = X + int64_t(i) * QP + c * 4;
+      const double2 x01 = *reinterpret_cast<const double2 *>(xi);
+      const double2 x23 = *reinterpret_cast<const double2 *>(xi + 2);
+      double acc0 = x01.x, acc1 = x01.y, acc2 = x23.x, acc3 = x23.y;
       const double *yk = Y + c * 4;
       if (bw == kBlock) {
 #pragma unroll 8
         for (int k = 0; k < kBlock; ++k) {
-          const double l = PJ[int64_t(k) * N + i];
+          const double l = -PJ[int64_t(k) * N + i];
           const double2 y01 = *reinterpret_cast<const double2 *>(yk + k * QP);
           const double2 y23 = *reinterpret_cast<const double2 *>(yk + k * QP + 2);
           acc0 = fma(l, y01.x, acc0);
@@ -138,7 +143,7 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
         }
       } else {
         for (int k = 0; k < bw; ++k) {
-          const double l = PJ[int64_t(k) * N + i];
+          const double l = -PJ[int64_t(k) * N + i];
           const double2 y01 = *reinterpret_cast<const double2 *>(yk + k * QP);
           const double2 y23 = *reinterpret_cast<const double2 *>(yk + k * QP + 2);
           acc0 = fma(l, y01.x, acc0);
@@ -147,12 +152,11 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
           acc3 = fma(l, y23.y, acc3);
         }
       }
-      double *xi = X + int64_t(i) * QP + c * 4;
       const int qn = Q - c * 4;
-      xi[0] -= acc0;
-      if (qn > 1) xi[1] -= acc1;
-      if (qn > 2) xi[2] -= acc2;
-      if (qn > 3) xi[3] -= acc3;
+      xi[0] = acc0;
+      if (qn > 1) xi[1] = acc1;
+      if (qn > 2) xi[2] = acc2;
+      if (qn > 3) xi[3] = acc3;
     }
   }
   __syncthreads();

@@ -145,6 +145,24 @@ int peers_factor(peers_ctx *ctx, const peers_symbolic *sym, const double *w, pee
 int peers_numeric_diag(peers_ctx *ctx, const peers_numeric *num, double *d_host);
 void peers_free_numeric(peers_numeric *num);
 
+/* ---- implicit inverse by etree blocks (the paper's order of work) ------------------------- */
+
+/* The same results as peers_query by another route: the entries of Z = L^{-1} that the paper's
+ * row-wise implicit inversion visits (§III-A/C, eq. 11, Lemma 1) are computed block by block,
+ * Z[P_t, C_t] for every supernode t over its ancestor path P_t, top-down (one launch per tree
+ * depth, each block a staircase GEMM from its ancestors' blocks), and each query then reads
+ * its two columns: R_st = sum_i (Z[i,s] - Z[i,t])^2 / d_i (eq. 12, eq. 18).  Work is about the
+ * paper's O(n^alpha nnz(L)) (Thm 4), far below the per-query walk, but device memory holds all
+ * of nnz(Z) at once (peers_blockinv_bytes); the call fails with PEERS_ENOMEM when it does not
+ * fit.  The device memory is allocated and freed inside the call.  Errors: PEERS_EINVAL,
+ * PEERS_ENOMEM, PEERS_ECUDA. */
+int peers_query_blockinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
+                         double *R, int flags);
+/* Device bytes peers_query_blockinv needs for this plan. */
+int64_t peers_blockinv_bytes(const peers_symbolic *sym);
+/* FMAs of its block GEMMs (the dominant kernel), counting the staircase's skipped zeros out. */
+int64_t peers_blockinv_fma(const peers_symbolic *sym);
+
 /* ---- tile shapes --------------------------------------------------------------------------- */
 
 /* Re-tiles a factored plan's sweep with new per-size-class caps (see peers_options.qcap) and

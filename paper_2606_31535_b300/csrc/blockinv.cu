@@ -1,0 +1,721 @@
+// Implicit inverse by elimination-tree blocks: the entries of Z = L^{-1} that the paper's
+// row-wise traversal visits (§III-A/C, eq. 11; Lemma 1: Z[i, j] != 0 only for i an etree
+// ancestor of j), computed block by block on the GPU and then combined per query:
+//     R_st = sum_i (Z[i, s] - Z[i, t])^2 / d_i                  (eq. 12, eq. 18).
+//
+// Layout.  For supernode t with columns C_t, its block Z[P_t, C_t] holds the rows of the
+// ancestor path P_t = C_t ++ C_parent ++ ... ++ C_root, column-major with ld = |P_t|.  Every
+// non-zero of Z lives in exactly one block, and the block of an ancestor a of t occupies the
+// last |P_a| rows of P_t (a suffix), which makes every gather a plain offset.
+//
+// Recurrence (from Z L = I, the column form of eq. 11):
+//     Z[C_t, C_t]   = T_t^{-1}                          (unit-lower diagonal block of L)
+//     Z[P_par, C_t] = -Z[P_par, B_t] * M_t,   M_t = L[B_t, C_t] * T_t^{-1}
+// where column b of Z[P_par, B_t] is the block column of b's own supernode, zero above its
+// suffix (a staircase: a row tile only needs the leading columns of B_t).  Phase 1 forms
+// T_t^{-1} and M_t for every supernode at once; phase 2 walks the tree top-down, one launch
+// per depth, every block of a depth from the (finished) blocks of its ancestors.  The query
+// pass then reads, per query, the two stored columns along their paths.
+//
+// Work is sum_t |P_parent(t)| * n_b(t) * n_c(t) FMAs minus the staircase zeros, about 30x
+// less than walking every query (the paper's Thm 4 order of work), for nnz(Z) of device memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "handles.h"
+#include "internal.h"
+#include "peers.h"
+
+namespace peers {
+namespace {
+
+constexpr int kT = 64;        // GEMM output tile (rows and columns)
+constexpr int kK = 32;        // GEMM inner chunk
+constexpr int kGemmThreads = 256;
+
+struct BiArgs {
+  const double *panel, *tinv, *dinv;
+  const int32_t *first, *nb, *rows;
+  const int64_t *panel_off, *tinv_off, *rows_off;
+  const int64_t *zoff, *moff;      // block offsets of Z and M per supernode
+  const int32_t *plen;             // |P_t|
+  const int32_t *parent;
+  const int32_t *gstart;           // per B_t entry: first row of its column within P_parent
+  const int64_t *gsrc;             // per B_t entry: offset of its column in Z
+  double *Z, *M;
+};
+
+// ---------------------------------------------------------------- phase 1a: T_t^{-1}
+
+// One CTA per (supernode, 32-column block J): columns J of T_t^{-1} by block forward
+// substitution, X_I = inv(T_II) (E_IJ - sum_{J<=K<I} T_IK X_K), written to Z[C_t, J].
+__global__ void __launch_bounds__(256) k_bi_diag(const int32_t *__restrict__ sns,
+                                                 const int32_t *__restrict__ blk, BiArgs a) {
+  __shared__ double Ti[kBlock][kBlock + 1];
+  __shared__ double acc[kBlock][kBlock + 1];
+  const int32_t t = sns[blockIdx.x], J = blk[blockIdx.x];
+  const int32_t nc = a.first[t + 1] - a.first[t], N = nc + a.nb[t];
+  const int32_t ld = a.plen[t];
+  const double *P = a.panel + a.panel_off[t];
+  double *Zt = a.Z + a.zoff[t];
+  const int c0 = J * kBlock, bwJ = min(kBlock, nc - c0);
+  const int nblk = (nc + kBlock - 1) / kBlock;
+  for (int I = J; I < nblk; ++I) {
+    const int r0 = I * kBlock, bwI = min(kBlock, nc - r0);
+    // acc = E_IJ - sum_K T[I rows, K cols] X_K   (X_K = Z[K rows, J cols], already written)
+    for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
+      const int i = e / kBlock, j = e % kBlock;
+      double s = 0.0;
+      if (i < bwI && j < bwJ) {
+        s = (I == J && i == j) ? 1.0 : 0.0;
+        for (int k = c0; k < r0; ++k)
+          s = fma(-P[int64_t(k) * N + r0 + i], Zt[int64_t(c0 + j) * ld + k], s);
+      }
+      acc[i][j] = s;
+    }
+    const double *TI = a.tinv + a.tinv_off[t] + int64_t(I) * kBlock * kBlock;
+    for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
+      const int i = e / kBlock, j = e % kBlock;
+      Ti[i][j] = (i < bwI && j < bwI) ? TI[i * bwI + j] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
+      const int i = e / kBlock, j = e % kBlock;
+      if (i < bwI && j < bwJ) {
+        double s = 0.0;
+        for (int k = 0; k <= i; ++k) s = fma(Ti[i][k], acc[k][j], s);
+        Zt[int64_t(c0 + j) * ld + r0 + i] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- GEMM tiles
+
+// Tile descriptor: supernode, row tile, column tile.
+struct Tile {
+  int32_t t, r, c, pad;
+};
+
+// Phase 1b: M_t = L[B_t, C_t] * Z[C_t, C_t] (lower-triangular right factor: k >= j).
+__global__ void __launch_bounds__(kGemmThreads) k_bi_m(const Tile *__restrict__ tiles, BiArgs a) {
+  __shared__ double As[kK][kT];
+  __shared__ double Bs[kK][kT];
+  const Tile tl = tiles[blockIdx.x];
+  const int32_t t = tl.t;
+  const int32_t nc = a.first[t + 1] - a.first[t], nbv = a.nb[t], N = nc + nbv;
+  const int32_t ld = a.plen[t];
+  const double *P = a.panel + a.panel_off[t];
+  const double *Zt = a.Z + a.zoff[t];
+  const int R0 = tl.r * kT, C0 = tl.c * kT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int k0 = C0; k0 < nc; k0 += kK) {   // Z[k, j] = 0 for k < j
+    for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
+      const int k = e / kT, r = e % kT;
+      const int kk = k0 + k;
+      As[k][r] = (kk < nc && R0 + r < nbv) ? P[int64_t(kk) * N + nc + R0 + r] : 0.0;
+      Bs[k][r] = (kk < nc && C0 + r < nc) ? Zt[int64_t(C0 + r) * ld + kk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kK; ++k) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { av[u] = As[k][tx + 16 * u]; bv[u] = Bs[k][ty + 16 * u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double *Mt = a.M + a.moff[t];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int j = C0 + ty + 16 * v;
+    if (j >= nc) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = R0 + tx + 16 * u;
+      if (i < nbv) Mt[int64_t(i) * nc + j] = acc[u][v];   // row-major n_b x n_c
+    }
+  }
+}
+
+// Phase 2: Z[P_par, C_t] = -Z[P_par, B_t] * M_t for the supernodes of one depth.  Row tile r
+// covers rows [64 r, 64 r + 64) of P_par; only the columns of B_t whose staircase starts
+// above the tile's last row contribute (a prefix of B_t, found by binary search).
+__global__ void __launch_bounds__(kGemmThreads) k_bi_z(const Tile *__restrict__ tiles, BiArgs a) {
+  __shared__ double As[kK][kT];
+  __shared__ double Bs[kK][kT];
+  __shared__ int32_t kend_s;
+  const Tile tl = tiles[blockIdx.x];
+  const int32_t t = tl.t;
+  const int32_t nc = a.first[t + 1] - a.first[t], nbv = a.nb[t];
+  const int32_t ldt = a.plen[t], lp = ldt - nc;   // |P_par|
+  const int R0 = tl.r * kT, C0 = tl.c * kT;
+  const int32_t *gs = a.gstart + a.rows_off[t];
+  const int64_t *gsrc = a.gsrc + a.rows_off[t];
+  if (threadIdx.x == 0) {   // first B_t column whose staircase starts at or below row R0+64
+    int lo = 0, hi = nbv;
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (gs[mid] < R0 + kT) lo = mid + 1; else hi = mid;
+    }
+    kend_s = lo;
+  }
+  __syncthreads();
+  const int32_t kend = kend_s;
+  const double *Mt = a.M + a.moff[t];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < kend; k0 += kK) {
+    for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
+      const int k = e / kT, r = e % kT;
+      const int kk = k0 + k;
+      double g = 0.0, m = 0.0;
+      if (kk < kend) {
+        const int row = R0 + r;
+        const int32_t st = gs[kk];
+        if (row < lp && row >= st) g = a.Z[gsrc[kk] + (row - st)];
+        if (C0 + r < nc) m = Mt[int64_t(kk) * nc + C0 + r];
+      }
+      As[k][r] = g;
+      Bs[k][r] = m;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kK; ++k) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { av[u] = As[k][tx + 16 * u]; bv[u] = Bs[k][ty + 16 * u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double *Zt = a.Z + a.zoff[t];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int j = C0 + ty + 16 * v;
+    if (j >= nc) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = R0 + tx + 16 * u;
+      if (i < lp) Zt[int64_t(j) * ldt + nc + i] = -acc[u][v];
+    }
+  }
+}
+
+// Phase 2 for narrow supernodes (n_c <= NC): one output row of Z[P_par, C_t] per thread, all
+// n_c columns in registers; rows of M_t and the staircase of B_t staged in shared memory.
+constexpr int kNarrowRows = 256;
+constexpr int kNarrowK = 64;
+
+template <int NC>
+__device__ __forceinline__ void bi_z_narrow(const Tile &tl, const BiArgs &a, double *sm) {
+  double *Ms = sm;                                              // kNarrowK x NC
+  int32_t *gss = reinterpret_cast<int32_t *>(Ms + kNarrowK * NC);   // kNarrowK
+  int64_t *gsr = reinterpret_cast<int64_t *>(gss + kNarrowK);       // kNarrowK
+  __shared__ int32_t kend_s;
+  const int32_t t = tl.t;
+  const int32_t nc = a.first[t + 1] - a.first[t], nbv = a.nb[t];
+  const int32_t ldt = a.plen[t], lp = ldt - nc;
+  const int R0 = tl.r * kNarrowRows;
+  const int32_t *gs = a.gstart + a.rows_off[t];
+  const int64_t *gsrc = a.gsrc + a.rows_off[t];
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nbv;
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (gs[mid] < R0 + kNarrowRows) lo = mid + 1; else hi = mid;
+    }
+    kend_s = lo;
+  }
+  __syncthreads();
+  const int32_t kend = kend_s;
+  const double *Mt = a.M + a.moff[t];
+  const int i = R0 + threadIdx.x;
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  for (int k0 = 0; k0 < kend; k0 += kNarrowK) {
+    const int kn = min(kNarrowK, kend - k0);
+    for (int e = threadIdx.x; e < kNarrowK * NC; e += blockDim.x) {
+      const int kk = e / NC, c = e % NC;
+      Ms[e] = (kk < kn && c < nc) ? Mt[int64_t(k0 + kk) * nc + c] : 0.0;
+    }
+    for (int kk = threadIdx.x; kk < kNarrowK; kk += blockDim.x) {
+      gss[kk] = kk < kn ? gs[k0 + kk] : INT32_MAX;
+      gsr[kk] = kk < kn ? gsrc[k0 + kk] : 0;
+    }
+    __syncthreads();
+    if (i < lp) {
+      for (int kk = 0; kk < kn; ++kk) {
+        const int32_t st = gss[kk];
+        if (i < st) break;   // staircase: later columns start further down
+        const double g = a.Z[gsr[kk] + (i - st)];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(g, Ms[kk * NC + c], acc[c]);
+      }
+    }
+    __syncthreads();
+  }
+  if (i < lp) {
+    double *Zt = a.Z + a.zoff[t];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c < nc) Zt[int64_t(c) * ldt + nc + i] = -acc[c];
+  }
+}
+
+// Narrow tiles of one depth; Tile.pad selects the register width (2, 4, 8, 16 or 32 columns).
+__global__ void __launch_bounds__(kNarrowRows) k_bi_z_narrow(const Tile *__restrict__ tiles,
+                                                             BiArgs a) {
+  extern __shared__ double sm[];
+  const Tile tl = tiles[blockIdx.x];
+  switch (tl.pad) {
+    case 2: bi_z_narrow<2>(tl, a, sm); break;
+    case 4: bi_z_narrow<4>(tl, a, sm); break;
+    case 8: bi_z_narrow<8>(tl, a, sm); break;
+    case 16: bi_z_narrow<16>(tl, a, sm); break;
+    default: bi_z_narrow<32>(tl, a, sm); break;
+  }
+}
+
+inline int narrow_width(int32_t nc) {
+  return nc <= 2 ? 2 : nc <= 4 ? 4 : nc <= 8 ? 8 : nc <= 16 ? 16 : 32;
+}
+constexpr size_t kNarrowSmem = size_t(kNarrowK) * 32 * 8 + kNarrowK * 4 + kNarrowK * 8;
+
+// ---------------------------------------------------------------- query pass
+
+struct BiQuery {
+  int32_t s1, j1;   // supernode and local column of the first endpoint's Z column
+  int32_t s2, j2;   // the second (s2 = -1: none, the pair touches the ground)
+  int64_t out;      // index in R
+};
+
+// One warp per query: R = sum over P_s1 \ P_m of z1^2/d + over P_s2 \ P_m of z2^2/d + over
+// P_m of (z1 - z2)^2/d, m = the lowest common supernode of s1 and s2 (s2 itself for an edge).
+__global__ void k_bi_query(const BiQuery *__restrict__ qs, int64_t nq, BiArgs a, double *R) {
+  const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (w >= nq) return;
+  const BiQuery q = qs[w];
+  const double *z1 = a.Z + a.zoff[q.s1] + int64_t(q.j1) * a.plen[q.s1];
+  const double *z2 = q.s2 >= 0 ? a.Z + a.zoff[q.s2] + int64_t(q.j2) * a.plen[q.s2] : nullptr;
+  double acc = 0.0;
+  // ancestors of s2 (to find the merge supernode): walk both paths by plen
+  int32_t x = q.s1, y = q.s2;
+  // branch of s1 below the merge
+  if (y >= 0) {
+    int32_t xs = x, ys = y;
+    while (xs != ys && xs >= 0 && ys >= 0) {
+      if (a.plen[xs] >= a.plen[ys]) xs = a.parent[xs]; else ys = a.parent[ys];
+    }
+    const int32_t m = (xs == ys) ? xs : -1;
+    for (; x != m; x = a.parent[x]) {
+      const int32_t f = a.first[x], nc = a.first[x + 1] - f;
+      const int64_t off = a.plen[q.s1] - a.plen[x];
+      for (int k = lane; k < nc; k += 32) {
+        const double v = z1[off + k];
+        acc = fma(v * v, a.dinv[f + k], acc);
+      }
+    }
+    for (; y != m; y = a.parent[y]) {
+      const int32_t f = a.first[y], nc = a.first[y + 1] - f;
+      const int64_t off = a.plen[q.s2] - a.plen[y];
+      for (int k = lane; k < nc; k += 32) {
+        const double v = z2[off + k];
+        acc = fma(v * v, a.dinv[f + k], acc);
+      }
+    }
+    for (; x != -1; x = a.parent[x]) {   // common part
+      const int32_t f = a.first[x], nc = a.first[x + 1] - f;
+      const int64_t o1 = a.plen[q.s1] - a.plen[x], o2 = a.plen[q.s2] - a.plen[x];
+      for (int k = lane; k < nc; k += 32) {
+        const double v = z1[o1 + k] - z2[o2 + k];
+        acc = fma(v * v, a.dinv[f + k], acc);
+      }
+    }
+  } else {
+    for (; x != -1; x = a.parent[x]) {
+      const int32_t f = a.first[x], nc = a.first[x + 1] - f;
+      const int64_t off = a.plen[q.s1] - a.plen[x];
+      for (int k = lane; k < nc; k += 32) {
+        const double v = z1[off + k];
+        acc = fma(v * v, a.dinv[f + k], acc);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) R[q.out] = acc;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host plan
+
+struct BlockInvPlan {
+  std::vector<int32_t> plen, depth, parent;
+  std::vector<int64_t> zoff, moff;
+  int64_t ztotal = 0, mtotal = 0;
+  std::vector<int32_t> gstart;
+  std::vector<int64_t> gsrc;
+  std::vector<int32_t> diag_sn, diag_blk;          // phase 1a CTAs
+  std::vector<Tile> m_tiles;                       // phase 1b tiles
+  std::vector<Tile> z_tiles;                       // phase 2 tiles, grouped by depth
+  std::vector<int64_t> z_ptr;                      // depth d: z_tiles[z_ptr[d] .. z_ptr[d+1])
+  std::vector<Tile> n_tiles;                       // phase 2 narrow tiles (n_c <= 32)
+  std::vector<int64_t> n_ptr;
+  std::vector<BiQuery> queries;
+  int64_t gemm_fma = 0;                            // phase-2 FMAs with the staircase
+};
+
+int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
+  const int32_t ns = S.nsuper;
+  B.plen.assign(ns, 0);
+  B.depth.assign(ns, 0);
+  B.parent = S.parent;
+  int32_t maxd = 0;
+  for (int32_t t = ns - 1; t >= 0; --t) {
+    const int32_t p = S.parent[t];
+    B.plen[t] = sn_nc(S, t) + (p >= 0 ? B.plen[p] : 0);
+    B.depth[t] = p >= 0 ? B.depth[p] + 1 : 0;
+    maxd = std::max(maxd, B.depth[t]);
+  }
+  B.zoff.assign(ns + 1, 0);
+  B.moff.assign(ns + 1, 0);
+  for (int32_t t = 0; t < ns; ++t) {
+    B.zoff[t + 1] = B.zoff[t] + int64_t(B.plen[t]) * sn_nc(S, t);
+    B.moff[t + 1] = B.moff[t] + int64_t(S.nb[t]) * sn_nc(S, t);
+  }
+  B.ztotal = B.zoff[ns];
+  B.mtotal = B.moff[ns];
+  // staircase of each B_t column inside P_parent, and where its Z column lives
+  B.gstart.assign(S.rows.size(), 0);
+  B.gsrc.assign(S.rows.size(), 0);
+  B.gemm_fma = 0;
+  for (int32_t t = 0; t < ns; ++t) {
+    const int32_t p = S.parent[t];
+    if (p < 0) continue;
+    for (int64_t k = S.rows_off[t]; k < S.rows_off[t + 1]; ++k) {
+      const int32_t b = S.rows[k];
+      const int32_t a = S.col2sn[b];
+      B.gstart[k] = B.plen[p] - B.plen[a];
+      B.gsrc[k] = B.zoff[a] + int64_t(b - S.first[a]) * B.plen[a];
+      B.gemm_fma += int64_t(B.plen[a]) * sn_nc(S, t);
+    }
+  }
+  // phase 1 work
+  B.diag_sn.clear();
+  B.diag_blk.clear();
+  B.m_tiles.clear();
+  for (int32_t t = 0; t < ns; ++t) {
+    const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+    for (int32_t J = 0; J * kBlock < nc; ++J) {
+      B.diag_sn.push_back(t);
+      B.diag_blk.push_back(J);
+    }
+    for (int32_t r = 0; r * kT < nbv; ++r)
+      for (int32_t c = 0; c * kT < nc; ++c) B.m_tiles.push_back({t, r, c, 0});
+  }
+  // phase 2 tiles by depth: 64 x 64 tiles for wide supernodes, one row per thread for
+  // narrow ones (at most 32 columns)
+  std::vector<std::vector<Tile>> per(maxd + 1), pern(maxd + 1);
+  for (int32_t t = 0; t < ns; ++t) {
+    const int32_t nc = sn_nc(S, t), lp = B.plen[t] - nc;
+    if (lp == 0 || S.nb[t] == 0) continue;
+    if (nc <= 32) {
+      for (int32_t r = 0; r * kNarrowRows < lp; ++r)
+        pern[B.depth[t]].push_back({t, r, 0, narrow_width(nc)});
+    } else {
+      for (int32_t r = 0; r * kT < lp; ++r)
+        for (int32_t c = 0; c * kT < nc; ++c) per[B.depth[t]].push_back({t, r, c, 0});
+    }
+  }
+  B.z_tiles.clear();
+  B.z_ptr.assign(1, 0);
+  B.n_tiles.clear();
+  B.n_ptr.assign(1, 0);
+  for (int32_t d = 0; d <= maxd; ++d) {
+    B.z_tiles.insert(B.z_tiles.end(), per[d].begin(), per[d].end());
+    B.z_ptr.push_back(static_cast<int64_t>(B.z_tiles.size()));
+    B.n_tiles.insert(B.n_tiles.end(), pern[d].begin(), pern[d].end());
+    B.n_ptr.push_back(static_cast<int64_t>(B.n_tiles.size()));
+  }
+  // queries: the plan's single-path slots and two-branch pairs
+  B.queries.clear();
+  B.queries.reserve(static_cast<size_t>(S.nsorted + S.nq_two));
+  for (int32_t s = 0; s < ns; ++s) {
+    for (int64_t q = S.qbeg[s]; q < S.qbeg[s + 1]; ++q) {
+      BiQuery bq{};
+      bq.s1 = s;
+      bq.j1 = S.qa[q];
+      bq.out = S.qorig[q];
+      const int32_t b = S.qb[q];
+      if (b < 0) {
+        bq.s2 = -1;
+      } else {
+        const int32_t nc = sn_nc(S, s);
+        const int32_t hi = b < nc ? S.first[s] + b : S.rows[S.rows_off[s] + (b - nc)];
+        bq.s2 = S.col2sn[hi];
+        bq.j2 = hi - S.first[bq.s2];
+      }
+      B.queries.push_back(bq);
+    }
+  }
+  for (int64_t k = 0; k < S.nq_two; ++k) {
+    BiQuery bq{};
+    bq.s1 = S.col2sn[S.two_lo[k]];
+    bq.j1 = S.two_lo[k] - S.first[bq.s1];
+    bq.s2 = S.col2sn[S.two_hi[k]];
+    bq.j2 = S.two_hi[k] - S.first[bq.s2];
+    bq.out = S.two_idx[k];
+    B.queries.push_back(bq);
+  }
+  (void)err;
+  return PEERS_OK;
+}
+
+int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, Tile *d_mt,
+                 Tile *d_zt, Tile *d_nt, int32_t *d_dsn, int32_t *d_dblk, BiQuery *d_q, double *R,
+                 cudaStream_t st, int64_t *launches, std::vector<cudaEvent_t> *ev,
+                 std::string &err) {
+  BiArgs a = base;
+  auto mark = [&]() {
+    if (ev) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      cudaEventRecord(e, st);
+      ev->push_back(e);
+    }
+  };
+  mark();
+  if (S.nq > 0) CUDA_TRY(cudaMemsetAsync(R, 0, sizeof(double) * S.nq, st));
+  // entries above each block's diagonal are zero and are never written by the kernels
+  if (B.ztotal > 0) CUDA_TRY(cudaMemsetAsync(a.Z, 0, sizeof(double) * B.ztotal, st));
+  if (!B.diag_sn.empty()) {
+    k_bi_diag<<<static_cast<unsigned>(B.diag_sn.size()), 256, 0, st>>>(d_dsn, d_dblk, a);
+    ++*launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  mark();
+  if (!B.m_tiles.empty()) {
+    k_bi_m<<<static_cast<unsigned>(B.m_tiles.size()), kGemmThreads, 0, st>>>(d_mt, a);
+    ++*launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  mark();
+  for (size_t d = 0; d + 1 < B.z_ptr.size(); ++d) {
+    const int64_t n = B.z_ptr[d + 1] - B.z_ptr[d];
+    const int64_t nn = B.n_ptr[d + 1] - B.n_ptr[d];
+    if (n > 0) {
+      k_bi_z<<<static_cast<unsigned>(n), kGemmThreads, 0, st>>>(d_zt + B.z_ptr[d], a);
+      ++*launches;
+      CUDA_TRY(cudaGetLastError());
+    }
+    if (nn > 0) {
+      k_bi_z_narrow<<<static_cast<unsigned>(nn), kNarrowRows, kNarrowSmem, st>>>(
+          d_nt + B.n_ptr[d], a);
+      ++*launches;
+      CUDA_TRY(cudaGetLastError());
+    }
+    if (n > 0 || nn > 0) mark();
+  }
+  const int64_t nq = static_cast<int64_t>(B.queries.size());
+  if (nq > 0) {
+    const unsigned blocks = static_cast<unsigned>((nq * 32 + 255) / 256);
+    k_bi_query<<<blocks, 256, 0, st>>>(d_q, nq, a, R);
+    ++*launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  mark();
+  return PEERS_OK;
+}
+
+}  // namespace peers
+
+// ---------------------------------------------------------------- C ABI
+
+namespace {
+
+int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, double *R, int flags,
+             std::string &err) {
+  const Symbolic &S = sym->S;
+  cudaStream_t st = ctx->stream;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  peers::BlockInvPlan B;
+  int rc = peers::blockinv_plan(S, B, err);
+  if (rc != PEERS_OK) return rc;
+  std::vector<void *> mem;
+  auto cleanup = [&]() {
+    for (void *p : mem) cudaFree(p);
+  };
+  auto alloc = [&](void **p, size_t bytes) -> int {
+    *p = nullptr;
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      err = "cudaMalloc of " + std::to_string(bytes) + " bytes for the block inverse: " +
+            cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? PEERS_ENOMEM : PEERS_ECUDA;
+    }
+    mem.push_back(*p);
+    return PEERS_OK;
+  };
+  auto up = [&](void **p, const void *src, size_t bytes) -> int {
+    int r = alloc(p, bytes);
+    if (r != PEERS_OK) return r;
+    if (bytes && cudaMemcpyAsync(*p, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      err = "upload for the block inverse";
+      return PEERS_ECUDA;
+    }
+    return PEERS_OK;
+  };
+  peers::BiArgs a{};
+  void *p = nullptr;
+  rc = alloc(&p, sizeof(double) * B.ztotal);
+  if (rc) { cleanup(); return rc; }
+  a.Z = static_cast<double *>(p);
+  rc = alloc(&p, sizeof(double) * B.mtotal);
+  if (rc) { cleanup(); return rc; }
+  a.M = static_cast<double *>(p);
+  void *dz = nullptr, *dm = nullptr, *dpl = nullptr, *dpar = nullptr, *dgs = nullptr,
+       *dgsrc = nullptr, *dmt = nullptr, *dzt = nullptr, *dnt = nullptr, *ddsn = nullptr,
+       *ddblk = nullptr,
+       *dq = nullptr, *drows = nullptr, *dout = nullptr;
+  if ((rc = up(&dz, B.zoff.data(), sizeof(int64_t) * B.zoff.size())) ||
+      (rc = up(&dm, B.moff.data(), sizeof(int64_t) * B.moff.size())) ||
+      (rc = up(&dpl, B.plen.data(), sizeof(int32_t) * B.plen.size())) ||
+      (rc = up(&dpar, B.parent.data(), sizeof(int32_t) * B.parent.size())) ||
+      (rc = up(&dgs, B.gstart.data(), sizeof(int32_t) * B.gstart.size())) ||
+      (rc = up(&dgsrc, B.gsrc.data(), sizeof(int64_t) * B.gsrc.size())) ||
+      (rc = up(&dmt, B.m_tiles.data(), sizeof(peers::Tile) * B.m_tiles.size())) ||
+      (rc = up(&dzt, B.z_tiles.data(), sizeof(peers::Tile) * B.z_tiles.size())) ||
+      (rc = up(&dnt, B.n_tiles.data(), sizeof(peers::Tile) * B.n_tiles.size())) ||
+      (rc = up(&ddsn, B.diag_sn.data(), sizeof(int32_t) * B.diag_sn.size())) ||
+      (rc = up(&ddblk, B.diag_blk.data(), sizeof(int32_t) * B.diag_blk.size())) ||
+      (rc = up(&dq, B.queries.data(), sizeof(peers::BiQuery) * B.queries.size())) ||
+      (rc = up(&drows, S.rows.data(), sizeof(int32_t) * S.rows.size()))) {
+    cleanup();
+    return rc;
+  }
+  a.panel = num->panel;
+  a.tinv = num->tinv;
+  a.dinv = num->dinv;
+  a.first = num->first;
+  a.nb = num->nb;
+  a.rows = static_cast<int32_t *>(drows);
+  a.panel_off = num->panel_off;
+  a.tinv_off = num->tinv_off;
+  a.rows_off = num->rows_off;
+  a.zoff = static_cast<int64_t *>(dz);
+  a.moff = static_cast<int64_t *>(dm);
+  a.plen = static_cast<int32_t *>(dpl);
+  a.parent = static_cast<int32_t *>(dpar);
+  a.gstart = static_cast<int32_t *>(dgs);
+  a.gsrc = static_cast<int64_t *>(dgsrc);
+  double *Rdev = R;
+  const bool host_out = !(flags & PEERS_OUT_DEVICE);
+  if (host_out) {
+    rc = alloc(&dout, sizeof(double) * std::max<int64_t>(1, S.nq));
+    if (rc) { cleanup(); return rc; }
+    Rdev = static_cast<double *>(dout);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->timing) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> ev;
+  rc = peers::blockinv_run(S, B, a, static_cast<peers::Tile *>(dmt),
+                           static_cast<peers::Tile *>(dzt), static_cast<peers::Tile *>(dnt),
+                           static_cast<int32_t *>(ddsn),
+                           static_cast<int32_t *>(ddblk), static_cast<peers::BiQuery *>(dq),
+                           Rdev, st, &launches, ctx->timing ? &ev : nullptr, err);
+  if (ctx->timing) {
+    // per phase: diagonal inverses, M, one entry per depth of Z blocks, query pass
+    cudaStreamSynchronize(st);
+    ctx->level_ms.clear();
+    for (size_t i = 0; i + 1 < ev.size(); ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      ctx->level_ms.push_back(ms);
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  if (ctx->timing) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ctx->stats.sweep_s = ms * 1e-3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  ctx->stats.sweep_launches = launches;
+  ctx->stats.h2d_bytes = 0;
+  ctx->stats.d2h_bytes = 0;
+  if (rc == PEERS_OK && host_out && S.nq > 0) {
+    if (cudaMemcpyAsync(R, Rdev, sizeof(double) * S.nq, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess) {
+      rc = PEERS_ECUDA;
+      err = "result copy";
+    }
+    ctx->stats.d2h_bytes = int64_t(sizeof(double)) * S.nq;
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc == PEERS_OK && e != cudaSuccess) {
+    rc = PEERS_ECUDA;
+    err = cudaGetErrorString(e);
+  }
+  cleanup();
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t peers_blockinv_bytes(const peers_symbolic *sym) {
+  if (!sym) return -1;
+  peers::BlockInvPlan B;
+  std::string err;
+  if (peers::blockinv_plan(sym->S, B, err) != PEERS_OK) return -1;
+  return 8 * (B.ztotal + B.mtotal) + 12 * static_cast<int64_t>(B.gstart.size()) +
+         16 * static_cast<int64_t>(B.z_tiles.size() + B.n_tiles.size() + B.m_tiles.size()) +
+         24 * static_cast<int64_t>(B.queries.size());
+}
+
+int64_t peers_blockinv_fma(const peers_symbolic *sym) {
+  if (!sym) return -1;
+  peers::BlockInvPlan B;
+  std::string err;
+  if (peers::blockinv_plan(sym->S, B, err) != PEERS_OK) return -1;
+  return B.gemm_fma;
+}
+
+int peers_query_blockinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
+                         double *R, int flags) {
+  if (!ctx || !sym || !num || (!R && sym->S.nq > 0)) return peers_fail(PEERS_EINVAL, "null argument");
+  if (num->sym != sym) return peers_fail(PEERS_EINVAL, "numeric handle belongs to another plan");
+  std::string err;
+  int rc = bi_query(ctx, sym, const_cast<peers_numeric *>(num), R, flags, err);
+  return rc == PEERS_OK ? rc : peers_fail(rc, err);
+}
+
+}  // extern "C"

@@ -105,6 +105,9 @@ def load(path: str | None = None):
         "peers_server_get_stats": (ctypes.c_int, [vp, P(ServerStats)]),
         "peers_server_destroy": (None, [vp]),
         "peers_retile": (ctypes.c_int, [vp, vp, vp, vp]),
+        "peers_query_blockinv": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+        "peers_blockinv_bytes": (i64, [vp]),
+        "peers_blockinv_fma": (i64, [vp]),
         "peers_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_char_p, vp, vp]),
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "peers_last_stats": (ctypes.c_int, [vp, P(Stats)]),
@@ -265,6 +268,23 @@ class Numeric:
         d = np.empty(self._sym.info()["n_reduced"], np.float64)
         _check(load().peers_numeric_diag(self._ctx._h, self._h, _ptr(d)), "peers_numeric_diag")
         return d
+
+
+def query_blockinv(ctx: Context, sym: Symbolic, num: Numeric, out=None):
+    """Resistances of the plan's queries through the block implicit inverse (the paper's order
+    of work); same interface as :func:`query`."""
+    lib = load()
+    if out is None:
+        out = np.empty(sym.nq, dtype=np.float64)
+    flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
+    _check(lib.peers_query_blockinv(ctx._h, sym._h, num._h, _ptr(out), flags),
+           "peers_query_blockinv")
+    return out
+
+
+def blockinv_cost(sym: Symbolic) -> dict:
+    lib = load()
+    return {"bytes": int(lib.peers_blockinv_bytes(sym._h)), "fma": int(lib.peers_blockinv_fma(sym._h))}
 
 
 def retile(ctx: Context, sym: Symbolic, num: Numeric, qcap):

@@ -226,3 +226,43 @@ def test_autotune_and_retile_keep_results(P, ctx, tmp_path):
     assert len(lines) >= 2 and all("|class" in x for x in lines)
     res2 = P.autotune(ctx, sym, num, cache)
     assert res2["qcap"] == res["qcap"] and all(x == 1.0 for x in res2["gain"])
+
+
+@pytest.mark.parametrize("name", ["grid32", "pdn3-49", "rgg-6000", "grid-200"])
+def test_block_inverse_matches_oracle(P, ctx, oracle_mod, name):
+    """The block implicit inverse (the paper's order of work) against the oracle, on all
+    edges plus random pairs (two-branch) plus pairs touching the ground."""
+    g = CASES[name]()
+    u, v = g.all_edges()
+    pu, pv = I.random_pairs(g.n, 400, seed=28)
+    qu = np.concatenate([u, pu, [0, 3, 0]]).astype(np.int32)
+    qv = np.concatenate([v, pv, [5, 0, 0]]).astype(np.int32)
+    sym = P.Symbolic.of(g, 0, qu, qv)
+    num = P.Numeric(ctx, sym)
+    Rb = P.query_blockinv(ctx, sym, num)
+    Rw = P.query(ctx, sym, num)
+    Ro = oracle_mod.resistance(g, qu, qv)
+    nz = Ro != 0
+    assert np.all(Rb[~nz] == 0)
+    assert maxrel(Rb[nz], Ro[nz]) <= TOL
+    assert maxrel(Rb[nz], Rw[nz]) <= TOL
+
+
+def test_block_inverse_pairs_split_by_the_ground(P, ctx, oracle_mod):
+    a = I.grid2d(9, 11, seed=29)
+    ua, va = a.all_edges()
+    wa = a.edge_weights()
+    n = 2 * a.n + 1
+    g0 = 2 * a.n
+    g = I.from_edges(n, np.concatenate([ua, ua + a.n, [4, a.n + 50]]),
+                     np.concatenate([va, va + a.n, [g0, g0]]),
+                     np.concatenate([wa, wa[::-1], [2.0, 0.5]]))
+    rng = np.random.default_rng(30)
+    qu = rng.integers(0, n, 300).astype(np.int32)
+    qv = rng.integers(0, n, 300).astype(np.int32)
+    sym = P.Symbolic.of(g, g0, qu, qv, use_coords=False)
+    Rb = P.query_blockinv(ctx, sym, P.Numeric(ctx, sym))
+    Ro = oracle_mod.resistance(g, qu, qv, ground=g0, use_coords=False)
+    nz = Ro != 0
+    assert np.all(Rb[~nz] == 0)
+    assert maxrel(Rb[nz], Ro[nz]) <= TOL

@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=8000,
                     help="edges per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-blockinv", action="store_true",
+                    help="skip timing the block implicit inverse beside the walk")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the largest tiles instead of running the tile autotuner")
     return ap.parse_args()
@@ -272,6 +274,29 @@ def run_ours(args):
     value = nq * args.steps * world / t
 
     sweep_stats = ctx.last_stats()
+    # the same queries by the block implicit inverse (the paper's order of work)
+    blockinv = None
+    if not args.no_blockinv:
+        cost = P.blockinv_cost(sym)
+        Rb = torch.empty(nq, dtype=torch.float64, device=f"cuda:{local}")
+        for _ in range(args.warmup):
+            P.query_blockinv(ctx, sym, num, Rb)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            P.query_blockinv(ctx, sym, num, Rb)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        tb = b0.elapsed_time(b1) * 1e-3 / args.steps
+        rel = float(((Rb - R).abs() / R.abs()).max().item()) if nq else 0.0
+        blockinv = {"value": nq / tb, "unit": UNIT, "ms_per_step": 1e3 * tb,
+                    "gemm_fma": cost["fma"], "gemm_tflops": 2.0 * cost["fma"] / tb / 1e12,
+                    "frac_of_dfma_peak": 2.0 * cost["fma"] / tb / 1e12 / fp64_peak,
+                    "device_bytes": cost["bytes"], "max_rel_vs_walk": rel,
+                    "speedup_vs_walk": step_s / tb}
+        del Rb
     num.close()
     # end to end through the public API: pinned conductances -> factor -> sweep -> host R
     w_pin = torch.from_numpy(g.w).pin_memory()
@@ -329,6 +354,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "tiles": tiles,
+        "next1_blockinv": blockinv,
         "analysis": {"t_analyze_s": t_analyze, "nsuper": info["nsuper"],
                      "levels": info["levels"], "nnz_l": info["nnz_l"],
                      "walk_fma": info["walk_fma"]},

@@ -95,6 +95,46 @@ __global__ void __launch_bounds__(256) k_bi_diag(const int32_t *__restrict__ sns
   }
 }
 
+// Phase 1 for supernodes of at most 32 columns (one diagonal block): Z[C_t, C_t] is the
+// block inverse the factorization already formed, and M_t = L[B_t, C_t] T_t^{-1} takes one
+// row per thread.  grid = (supernode, chunk of 256 rows of B_t).
+__global__ void __launch_bounds__(256) k_bi_small(const int32_t *__restrict__ sns,
+                                                  const int32_t *__restrict__ chunk, BiArgs a) {
+  __shared__ double Ti[kBlock][kBlock + 1];
+  const int32_t t = sns[blockIdx.x], ch = chunk[blockIdx.x];
+  const int32_t nc = a.first[t + 1] - a.first[t], nbv = a.nb[t], N = nc + nbv;
+  const double *TI = a.tinv + a.tinv_off[t];
+  for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
+    const int i = e / kBlock, j = e % kBlock;
+    Ti[i][j] = (i < nc && j < nc) ? TI[i * nc + j] : 0.0;
+  }
+  __syncthreads();
+  if (ch == 0) {
+    double *Zt = a.Z + a.zoff[t];
+    const int32_t ld = a.plen[t];
+    for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+      const int i = e % nc, j = e / nc;
+      Zt[int64_t(j) * ld + i] = Ti[i][j];
+    }
+  }
+  const int i = ch * 256 + threadIdx.x;
+  if (i >= nbv) return;
+  const double *P = a.panel + a.panel_off[t];
+  double p[kBlock];
+#pragma unroll
+  for (int k = 0; k < kBlock; ++k) p[k] = k < nc ? P[int64_t(k) * N + nc + i] : 0.0;
+  double *Mrow = a.M + a.moff[t] + int64_t(i) * nc;
+#pragma unroll
+  for (int c = 0; c < kBlock; ++c) {
+    if (c >= nc) break;
+    double m = 0.0;
+#pragma unroll
+    for (int k = 0; k < kBlock; ++k)
+      if (k >= c) m = fma(p[k], Ti[k][c], m);
+    Mrow[c] = m;
+  }
+}
+
 // ---------------------------------------------------------------- GEMM tiles
 
 // Tile descriptor: supernode, row tile, column tile.
@@ -174,16 +214,24 @@ __global__ void __launch_bounds__(kGemmThreads) k_bi_z(const Tile *__restrict__ 
   const int32_t kend = kend_s;
   const double *Mt = a.M + a.moff[t];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  __shared__ int32_t sst[kK];
+  __shared__ int64_t ssrc[kK];
   double acc[4][4] = {};
   for (int k0 = 0; k0 < kend; k0 += kK) {
+    if (threadIdx.x < kK) {
+      const int kk = k0 + threadIdx.x;
+      sst[threadIdx.x] = kk < kend ? gs[kk] : INT32_MAX;
+      ssrc[threadIdx.x] = kk < kend ? gsrc[kk] : 0;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
       const int k = e / kT, r = e % kT;
       const int kk = k0 + k;
       double g = 0.0, m = 0.0;
       if (kk < kend) {
         const int row = R0 + r;
-        const int32_t st = gs[kk];
-        if (row < lp && row >= st) g = a.Z[gsrc[kk] + (row - st)];
+        const int32_t st = sst[k];
+        if (row < lp && row >= st) g = a.Z[ssrc[k] + (row - st)];
         if (C0 + r < nc) m = Mt[int64_t(kk) * nc + C0 + r];
       }
       As[k][r] = g;
@@ -372,7 +420,8 @@ struct BlockInvPlan {
   int64_t ztotal = 0, mtotal = 0;
   std::vector<int32_t> gstart;
   std::vector<int64_t> gsrc;
-  std::vector<int32_t> diag_sn, diag_blk;          // phase 1a CTAs
+  std::vector<int32_t> diag_sn, diag_blk;          // phase 1a CTAs (wide supernodes)
+  std::vector<int32_t> small_sn, small_chunk;      // phase 1 CTAs of narrow supernodes
   std::vector<Tile> m_tiles;                       // phase 1b tiles
   std::vector<Tile> z_tiles;                       // phase 2 tiles, grouped by depth
   std::vector<int64_t> z_ptr;                      // depth d: z_tiles[z_ptr[d] .. z_ptr[d+1])
@@ -421,8 +470,17 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
   B.diag_sn.clear();
   B.diag_blk.clear();
   B.m_tiles.clear();
+  B.small_sn.clear();
+  B.small_chunk.clear();
   for (int32_t t = 0; t < ns; ++t) {
     const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+    if (nc <= kBlock) {   // one diagonal block: its inverse already exists
+      for (int32_t ch = 0; ch == 0 || ch * 256 < nbv; ++ch) {
+        B.small_sn.push_back(t);
+        B.small_chunk.push_back(ch);
+      }
+      continue;
+    }
     for (int32_t J = 0; J * kBlock < nc; ++J) {
       B.diag_sn.push_back(t);
       B.diag_blk.push_back(J);
@@ -489,7 +547,8 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
 }
 
 int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, Tile *d_mt,
-                 Tile *d_zt, Tile *d_nt, int32_t *d_dsn, int32_t *d_dblk, BiQuery *d_q, double *R,
+                 Tile *d_zt, Tile *d_nt, int32_t *d_dsn, int32_t *d_dblk, int32_t *d_ssn,
+                 int32_t *d_sch, BiQuery *d_q, double *R,
                  cudaStream_t st, int64_t *launches, std::vector<cudaEvent_t> *ev,
                  std::string &err) {
   BiArgs a = base;
@@ -505,6 +564,11 @@ int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, T
   if (S.nq > 0) CUDA_TRY(cudaMemsetAsync(R, 0, sizeof(double) * S.nq, st));
   // entries above each block's diagonal are zero and are never written by the kernels
   if (B.ztotal > 0) CUDA_TRY(cudaMemsetAsync(a.Z, 0, sizeof(double) * B.ztotal, st));
+  if (!B.small_sn.empty()) {
+    k_bi_small<<<static_cast<unsigned>(B.small_sn.size()), 256, 0, st>>>(d_ssn, d_sch, a);
+    ++*launches;
+    CUDA_TRY(cudaGetLastError());
+  }
   if (!B.diag_sn.empty()) {
     k_bi_diag<<<static_cast<unsigned>(B.diag_sn.size()), 256, 0, st>>>(d_dsn, d_dblk, a);
     ++*launches;
@@ -594,7 +658,7 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   a.M = static_cast<double *>(p);
   void *dz = nullptr, *dm = nullptr, *dpl = nullptr, *dpar = nullptr, *dgs = nullptr,
        *dgsrc = nullptr, *dmt = nullptr, *dzt = nullptr, *dnt = nullptr, *ddsn = nullptr,
-       *ddblk = nullptr,
+       *ddblk = nullptr, *dssn = nullptr, *dsch = nullptr,
        *dq = nullptr, *drows = nullptr, *dout = nullptr;
   if ((rc = up(&dz, B.zoff.data(), sizeof(int64_t) * B.zoff.size())) ||
       (rc = up(&dm, B.moff.data(), sizeof(int64_t) * B.moff.size())) ||
@@ -607,6 +671,8 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
       (rc = up(&dnt, B.n_tiles.data(), sizeof(peers::Tile) * B.n_tiles.size())) ||
       (rc = up(&ddsn, B.diag_sn.data(), sizeof(int32_t) * B.diag_sn.size())) ||
       (rc = up(&ddblk, B.diag_blk.data(), sizeof(int32_t) * B.diag_blk.size())) ||
+      (rc = up(&dssn, B.small_sn.data(), sizeof(int32_t) * B.small_sn.size())) ||
+      (rc = up(&dsch, B.small_chunk.data(), sizeof(int32_t) * B.small_chunk.size())) ||
       (rc = up(&dq, B.queries.data(), sizeof(peers::BiQuery) * B.queries.size())) ||
       (rc = up(&drows, S.rows.data(), sizeof(int32_t) * S.rows.size()))) {
     cleanup();
@@ -644,8 +710,9 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   std::vector<cudaEvent_t> ev;
   rc = peers::blockinv_run(S, B, a, static_cast<peers::Tile *>(dmt),
                            static_cast<peers::Tile *>(dzt), static_cast<peers::Tile *>(dnt),
-                           static_cast<int32_t *>(ddsn),
-                           static_cast<int32_t *>(ddblk), static_cast<peers::BiQuery *>(dq),
+                           static_cast<int32_t *>(ddsn), static_cast<int32_t *>(ddblk),
+                           static_cast<int32_t *>(dssn), static_cast<int32_t *>(dsch),
+                           static_cast<peers::BiQuery *>(dq),
                            Rdev, st, &launches, ctx->timing ? &ev : nullptr, err);
   if (ctx->timing) {
     // per phase: diagonal inverses, M, one entry per depth of Z blocks, query pass

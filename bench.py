@@ -297,6 +297,28 @@ def run_ours(args):
                     "device_bytes": cost["bytes"], "max_rel_vs_walk": rel,
                     "speedup_vs_walk": step_s / tb}
         del Rb
+    # and from the selected inverse (Sigma on the pattern of L, Takahashi recurrences)
+    selinv = None
+    if not args.no_blockinv:
+        fma_si = int(P.load().peers_selinv_fma(sym._h))
+        Rs = torch.empty(nq, dtype=torch.float64, device=f"cuda:{local}")
+        for _ in range(args.warmup):
+            P.query_selinv(ctx, sym, num, Rs)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            P.query_selinv(ctx, sym, num, Rs)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ts = b0.elapsed_time(b1) * 1e-3 / args.steps
+        rel = float(((Rs - R).abs() / R.abs()).max().item()) if nq else 0.0
+        selinv = {"value": nq / ts, "unit": UNIT, "ms_per_step": 1e3 * ts, "fma": fma_si,
+                  "tflops": 2.0 * fma_si / ts / 1e12,
+                  "frac_of_dfma_peak": 2.0 * fma_si / ts / 1e12 / fp64_peak,
+                  "max_rel_vs_walk": rel, "speedup_vs_walk": step_s / ts}
+        del Rs
     num.close()
     # end to end through the public API: pinned conductances -> factor -> sweep -> host R
     w_pin = torch.from_numpy(g.w).pin_memory()
@@ -355,6 +377,7 @@ def run_ours(args):
         "clocks": clocks,
         "tiles": tiles,
         "next1_blockinv": blockinv,
+        "next2_selinv": selinv,
         "analysis": {"t_analyze_s": t_analyze, "nsuper": info["nsuper"],
                      "levels": info["levels"], "nnz_l": info["nnz_l"],
                      "walk_fma": info["walk_fma"]},

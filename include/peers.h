@@ -163,6 +163,21 @@ int64_t peers_blockinv_bytes(const peers_symbolic *sym);
 /* FMAs of its block GEMMs (the dominant kernel), counting the staircase's skipped zeros out. */
 int64_t peers_blockinv_fma(const peers_symbolic *sym);
 
+/* ---- selected inversion (all-edge resistances from the inverse on the pattern of L) ------- */
+
+/* The same results for every query that lies inside the pattern of L (every graph edge and
+ * every pair touching the ground): Sigma = L_r^{-1} is computed only on the pattern of L by
+ * Takahashi's recurrences in supernodal form, top-down, and R_uv = Sigma_uu + Sigma_vv -
+ * 2 Sigma_uv (eq. 2).  The work is about one factorization, far below both the walk and the
+ * block inverse; the memory is two depths of dense inverse fronts.  The paper does not use it
+ * (§II-C); it is an independent second route to the same numbers.  A plan with listed pairs
+ * outside the pattern is rejected with PEERS_EINVAL (use peers_query).  Errors: PEERS_EINVAL,
+ * PEERS_ENOMEM, PEERS_ECUDA. */
+int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
+                       double *R, int flags);
+/* FMAs of the selected inversion for this plan. */
+int64_t peers_selinv_fma(const peers_symbolic *sym);
+
 /* ---- tile shapes --------------------------------------------------------------------------- */
 
 /* Re-tiles a factored plan's sweep with new per-size-class caps (see peers_options.qcap) and

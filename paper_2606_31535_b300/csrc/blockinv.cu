@@ -410,6 +410,167 @@ __global__ void k_bi_query(const BiQuery *__restrict__ qs, int64_t nq, BiArgs a,
   if (lane == 0) R[q.out] = acc;
 }
 
+// ================================================================ selected inversion
+//
+// Sigma = L_r^{-1} on the pattern of L (Takahashi's recurrences in supernodal L D L^T form),
+// top-down by depth.  For supernode s with T = L[C,C], P = L[B,C], M = P T^{-1}, Zd = T^{-1}:
+//     Sigma[B,B] = the parent's inverse front restricted to B (a gather through rmap)
+//     Sigma[B,C] = -Sigma[B,B] M
+//     Sigma[C,C] = Zd^T D_C^{-1} Zd - M^T Sigma[B,C]
+// The inverse front F(s) = Sigma[rows(s), rows(s)] (both triangles, column-major) is all a
+// query starting at s needs: R = F[a,a] + F[b,b] - 2 F[b,a] (eq. 2 with L_r^{-1} = Sigma).
+
+struct SiArgs {
+  const double *dinv;
+  const int32_t *first, *nb, *rmap, *parent;
+  const int64_t *rows_off;
+  const double *Zd;       // T^{-1} per supernode, n_c x n_c column-major
+  const int64_t *doff;
+  const double *M;        // n_b x n_c row-major per supernode
+  const int64_t *moff;
+  const int64_t *foff;    // offset of F(s) in its depth's buffer
+  const double *Fprev;    // inverse fronts of the previous depth
+  double *Fcur;           // inverse fronts of this depth
+};
+
+// Sigma[B,B] of each supernode of this depth from its parent's front.  grid = (supernode,
+// chunk of 8 columns of B).
+__global__ void __launch_bounds__(256) k_si_gather(const int32_t *__restrict__ sns, SiArgs a) {
+  const int32_t s = sns[blockIdx.x];
+  const int32_t p = a.parent[s];
+  const int32_t nc = a.first[s + 1] - a.first[s], nbv = a.nb[s], N = nc + nbv;
+  const int32_t Np = a.first[p + 1] - a.first[p] + a.nb[p];
+  const int32_t j0 = blockIdx.y * 8;
+  if (j0 >= nbv) return;
+  const int32_t *rm = a.rmap + a.rows_off[s];
+  const double *Fp = a.Fprev + a.foff[p];
+  double *F = a.Fcur + a.foff[s];
+  for (int32_t j = j0; j < min(nbv, j0 + 8); ++j) {
+    const int64_t rj = rm[j];
+    for (int32_t i = threadIdx.x; i < nbv; i += blockDim.x)
+      F[int64_t(nc + j) * N + nc + i] = Fp[rj * Np + rm[i]];
+  }
+}
+
+// Sigma[B,C] = -Sigma[B,B] M (and its transpose Sigma[C,B]).  Tiles over n_b x n_c.
+__global__ void __launch_bounds__(kGemmThreads) k_si_bc(const Tile *__restrict__ tiles, SiArgs a) {
+  __shared__ double As[kK][kT];
+  __shared__ double Bs[kK][kT];
+  const Tile tl = tiles[blockIdx.x];
+  const int32_t s = tl.t;
+  const int32_t nc = a.first[s + 1] - a.first[s], nbv = a.nb[s], N = nc + nbv;
+  double *F = a.Fcur + a.foff[s];
+  const double *M = a.M + a.moff[s];
+  const int R0 = tl.r * kT, C0 = tl.c * kT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < nbv; k0 += kK) {
+    for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
+      const int k = e / kT, r = e % kT;
+      const int kk = k0 + k;
+      As[k][r] = (kk < nbv && R0 + r < nbv) ? F[int64_t(nc + kk) * N + nc + R0 + r] : 0.0;
+      Bs[k][r] = (kk < nbv && C0 + r < nc) ? M[int64_t(kk) * nc + C0 + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kK; ++k) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { av[u] = As[k][tx + 16 * u]; bv[u] = Bs[k][ty + 16 * u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int j = C0 + ty + 16 * v;
+    if (j >= nc) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = R0 + tx + 16 * u;
+      if (i < nbv) {
+        F[int64_t(j) * N + nc + i] = -acc[u][v];
+        F[int64_t(nc + i) * N + j] = -acc[u][v];
+      }
+    }
+  }
+}
+
+// Sigma[C,C] = Zd^T D^{-1} Zd - M^T Sigma[B,C].  Tiles over n_c x n_c.
+__global__ void __launch_bounds__(kGemmThreads) k_si_cc(const Tile *__restrict__ tiles, SiArgs a) {
+  __shared__ double As[kK][kT];
+  __shared__ double Bs[kK][kT];
+  const Tile tl = tiles[blockIdx.x];
+  const int32_t s = tl.t;
+  const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
+  double *F = a.Fcur + a.foff[s];
+  const double *Zd = a.Zd + a.doff[s];
+  const double *M = a.M + a.moff[s];
+  const int R0 = tl.r * kT, C0 = tl.c * kT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  // Zd^T D^{-1} Zd: Zd[k, i] Zd[k, j] is non-zero only for k >= max(i, j)
+  const int kstart = (max(R0, C0) / kK) * kK;
+  for (int k0 = kstart; k0 < nc + nbv; k0 += kK) {
+    for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
+      const int k = e / kT, r = e % kT;
+      const int kk = k0 + k;
+      double x = 0.0, y = 0.0;
+      if (kk < nc) {
+        if (R0 + r < nc) x = Zd[int64_t(R0 + r) * nc + kk] * a.dinv[f + kk];
+        if (C0 + r < nc) y = Zd[int64_t(C0 + r) * nc + kk];
+      } else if (kk < nc + nbv) {
+        const int b = kk - nc;
+        if (R0 + r < nc) x = M[int64_t(b) * nc + R0 + r];
+        if (C0 + r < nc) y = -F[int64_t(C0 + r) * N + nc + b];
+      }
+      As[k][r] = x;
+      Bs[k][r] = y;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kK; ++k) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { av[u] = As[k][tx + 16 * u]; bv[u] = Bs[k][ty + 16 * u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int j = C0 + ty + 16 * v;
+    if (j >= nc) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = R0 + tx + 16 * u;
+      if (i < nc) F[int64_t(j) * N + i] = acc[u][v];
+    }
+  }
+}
+
+struct SiQuery {
+  int32_t s, a, b, pad;   // start supernode, local rows of lo and hi in its front (b = -1: none)
+  int64_t out;
+};
+
+__global__ void k_si_query(const SiQuery *__restrict__ qs, int64_t nq, SiArgs args, double *R) {
+  const int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (k >= nq) return;
+  const SiQuery q = qs[k];
+  const int32_t N = args.first[q.s + 1] - args.first[q.s] + args.nb[q.s];
+  const double *F = args.Fcur + args.foff[q.s];
+  double r = F[int64_t(q.a) * N + q.a];
+  if (q.b >= 0) r += F[int64_t(q.b) * N + q.b] - 2.0 * F[int64_t(q.a) * N + q.b];
+  R[q.out] = r;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host plan
@@ -608,6 +769,111 @@ int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, T
   return PEERS_OK;
 }
 
+// ---------------------------------------------------------------- selected inversion plan
+
+struct SelInvPlan {
+  std::vector<int32_t> ncs;                        // n_c per supernode (ld of Zd)
+  std::vector<int64_t> doff, moff;
+  int64_t dtotal = 0, mtotal = 0;
+  std::vector<int64_t> foff;                       // offset of F(s) in its depth's buffer
+  int64_t fbuf = 0;                                // largest depth buffer (doubles)
+  std::vector<std::vector<int32_t>> depth_sn;      // supernodes by depth
+  std::vector<int32_t> gather_sn;                  // per depth, consecutive
+  std::vector<int64_t> gather_ptr;
+  std::vector<int32_t> gather_ych;                 // max column chunks per depth
+  std::vector<Tile> bc, cc;
+  std::vector<int64_t> bc_ptr, cc_ptr;
+  std::vector<SiQuery> queries;
+  std::vector<int64_t> q_ptr;
+  std::vector<int32_t> small_sn, small_chunk, diag_sn, diag_blk;
+  std::vector<Tile> m_tiles;
+  int64_t fma = 0;
+};
+
+int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
+  if (S.nq_two > 0) {
+    err = "the selected inverse covers pairs inside the pattern of L (every graph edge and "
+          "every pair touching the ground); this plan lists " + std::to_string(S.nq_two) +
+          " other pairs: use peers_query or peers_query_blockinv";
+    return PEERS_EINVAL;
+  }
+  const int32_t ns = S.nsuper;
+  std::vector<int32_t> depth(ns, 0);
+  int32_t maxd = 0;
+  for (int32_t t = ns - 1; t >= 0; --t) {
+    depth[t] = S.parent[t] >= 0 ? depth[S.parent[t]] + 1 : 0;
+    maxd = std::max(maxd, depth[t]);
+  }
+  P.ncs.resize(ns);
+  P.doff.assign(ns + 1, 0);
+  P.moff.assign(ns + 1, 0);
+  P.foff.assign(ns, 0);
+  P.depth_sn.assign(maxd + 1, {});
+  std::vector<int64_t> fsize(maxd + 1, 0);
+  P.fma = 0;
+  for (int32_t t = 0; t < ns; ++t) {
+    const int64_t nc = sn_nc(S, t), nbv = S.nb[t], N = nc + nbv;
+    P.ncs[t] = static_cast<int32_t>(nc);
+    P.doff[t + 1] = P.doff[t] + nc * nc;
+    P.moff[t + 1] = P.moff[t] + nbv * nc;
+    P.depth_sn[depth[t]].push_back(t);
+    P.foff[t] = fsize[depth[t]];
+    fsize[depth[t]] += N * N;
+    P.fma += nbv * nbv * nc + nc * nc * (nc + nbv) / 2;
+  }
+  P.dtotal = P.doff[ns];
+  P.mtotal = P.moff[ns];
+  P.fbuf = 0;
+  for (int64_t x : fsize) P.fbuf = std::max(P.fbuf, x);
+  // phase 1 (T^{-1} and M) as in the block inverse
+  for (int32_t t = 0; t < ns; ++t) {
+    const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+    if (nc <= kBlock) {
+      for (int32_t ch = 0; ch == 0 || ch * 256 < nbv; ++ch) {
+        P.small_sn.push_back(t);
+        P.small_chunk.push_back(ch);
+      }
+      continue;
+    }
+    for (int32_t J = 0; J * kBlock < nc; ++J) {
+      P.diag_sn.push_back(t);
+      P.diag_blk.push_back(J);
+    }
+    for (int32_t r = 0; r * kT < nbv; ++r)
+      for (int32_t c = 0; c * kT < nc; ++c) P.m_tiles.push_back({t, r, c, 0});
+  }
+  // per depth: gathers, tiles, queries
+  P.gather_ptr.assign(1, 0);
+  P.bc_ptr.assign(1, 0);
+  P.cc_ptr.assign(1, 0);
+  P.q_ptr.assign(1, 0);
+  std::vector<std::vector<SiQuery>> qd(maxd + 1);
+  for (int32_t s0 = 0; s0 < ns; ++s0)
+    for (int64_t q = S.qbeg[s0]; q < S.qbeg[s0 + 1]; ++q)
+      qd[depth[s0]].push_back({s0, S.qa[q], S.qb[q], 0, S.qorig[q]});
+  for (int32_t d = 0; d <= maxd; ++d) {
+    int32_t ych = 0;
+    for (int32_t t : P.depth_sn[d]) {
+      const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+      if (nbv > 0) {
+        P.gather_sn.push_back(t);
+        ych = std::max(ych, (nbv + 7) / 8);
+        for (int32_t r = 0; r * kT < nbv; ++r)
+          for (int32_t c = 0; c * kT < nc; ++c) P.bc.push_back({t, r, c, 0});
+      }
+      for (int32_t r = 0; r * kT < nc; ++r)
+        for (int32_t c = 0; c * kT < nc; ++c) P.cc.push_back({t, r, c, 0});
+    }
+    P.gather_ptr.push_back(static_cast<int64_t>(P.gather_sn.size()));
+    P.gather_ych.push_back(ych);
+    P.bc_ptr.push_back(static_cast<int64_t>(P.bc.size()));
+    P.cc_ptr.push_back(static_cast<int64_t>(P.cc.size()));
+    P.queries.insert(P.queries.end(), qd[d].begin(), qd[d].end());
+    P.q_ptr.push_back(static_cast<int64_t>(P.queries.size()));
+  }
+  return PEERS_OK;
+}
+
 }  // namespace peers
 
 // ---------------------------------------------------------------- C ABI
@@ -754,6 +1020,180 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   return rc;
 }
 
+// Device buffers of one call, freed together.
+struct DevMem {
+  std::vector<void *> ptrs;
+  std::string *err;
+  explicit DevMem(std::string *e) : err(e) {}
+  ~DevMem() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  int alloc(T **p, int64_t count) {
+    void *q = nullptr;
+    const size_t bytes = sizeof(T) * static_cast<size_t>(std::max<int64_t>(1, count));
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? PEERS_ENOMEM : PEERS_ECUDA;
+    }
+    ptrs.push_back(q);
+    *p = static_cast<T *>(q);
+    return PEERS_OK;
+  }
+  template <class T>
+  int upload(T **p, const std::vector<T> &v, cudaStream_t st) {
+    int rc = alloc(p, static_cast<int64_t>(v.size()));
+    if (rc != PEERS_OK || v.empty()) return rc;
+    if (cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+      *err = "upload";
+      return PEERS_ECUDA;
+    }
+    return PEERS_OK;
+  }
+};
+
+#define RC_TRY(x)                   \
+  do {                              \
+    int rc_ = (x);                  \
+    if (rc_ != PEERS_OK) return rc_; \
+  } while (0)
+
+int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, double *R, int flags,
+             std::string &err) {
+  const Symbolic &S = sym->S;
+  cudaStream_t st = ctx->stream;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  peers::SelInvPlan P;
+  RC_TRY(peers::selinv_plan(S, P, err));
+  DevMem mem(&err);
+  double *Zd, *M, *F0, *F1, *Rdev = R;
+  int32_t *ncs, *gsn, *ssn, *sch, *dsn, *dblk;
+  int64_t *doff, *moff, *foff;
+  peers::Tile *bc, *cc, *mt;
+  peers::SiQuery *qs;
+  RC_TRY(mem.alloc(&Zd, P.dtotal));
+  RC_TRY(mem.alloc(&M, P.mtotal));
+  RC_TRY(mem.alloc(&F0, P.fbuf));
+  RC_TRY(mem.alloc(&F1, P.fbuf));
+  RC_TRY(mem.upload(&ncs, P.ncs, st));
+  RC_TRY(mem.upload(&doff, P.doff, st));
+  RC_TRY(mem.upload(&moff, P.moff, st));
+  RC_TRY(mem.upload(&foff, P.foff, st));
+  RC_TRY(mem.upload(&gsn, P.gather_sn, st));
+  RC_TRY(mem.upload(&bc, P.bc, st));
+  RC_TRY(mem.upload(&cc, P.cc, st));
+  RC_TRY(mem.upload(&qs, P.queries, st));
+  RC_TRY(mem.upload(&ssn, P.small_sn, st));
+  RC_TRY(mem.upload(&sch, P.small_chunk, st));
+  RC_TRY(mem.upload(&dsn, P.diag_sn, st));
+  RC_TRY(mem.upload(&dblk, P.diag_blk, st));
+  RC_TRY(mem.upload(&mt, P.m_tiles, st));
+  const bool host_out = !(flags & PEERS_OUT_DEVICE);
+  if (host_out) RC_TRY(mem.alloc(&Rdev, S.nq));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->timing) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  int64_t launches = 0;
+  if (S.nq > 0) CUDA_TRY(cudaMemsetAsync(Rdev, 0, sizeof(double) * S.nq, st));
+  CUDA_TRY(cudaMemsetAsync(Zd, 0, sizeof(double) * std::max<int64_t>(1, P.dtotal), st));
+  // phase 1: T^{-1} (into Zd, ld = n_c) and M, by the block inverse's kernels
+  peers::BiArgs b{};
+  b.panel = num->panel;
+  b.tinv = num->tinv;
+  b.dinv = num->dinv;
+  b.first = num->first;
+  b.nb = num->nb;
+  b.panel_off = num->panel_off;
+  b.tinv_off = num->tinv_off;
+  b.rows_off = num->rows_off;
+  b.zoff = doff;
+  b.moff = moff;
+  b.plen = ncs;
+  b.Z = Zd;
+  b.M = M;
+  if (!P.small_sn.empty()) {
+    peers::k_bi_small<<<static_cast<unsigned>(P.small_sn.size()), 256, 0, st>>>(ssn, sch, b);
+    ++launches;
+  }
+  if (!P.diag_sn.empty()) {
+    peers::k_bi_diag<<<static_cast<unsigned>(P.diag_sn.size()), 256, 0, st>>>(dsn, dblk, b);
+    ++launches;
+  }
+  if (!P.m_tiles.empty()) {
+    peers::k_bi_m<<<static_cast<unsigned>(P.m_tiles.size()), peers::kGemmThreads, 0, st>>>(mt, b);
+    ++launches;
+  }
+  CUDA_TRY(cudaGetLastError());
+  // phase 2: top-down by depth
+  peers::SiArgs a{};
+  a.dinv = num->dinv;
+  a.first = num->first;
+  a.nb = num->nb;
+  a.rmap = num->rmap;
+  a.rows_off = num->rows_off;
+  a.Zd = Zd;
+  a.doff = doff;
+  a.M = M;
+  a.moff = moff;
+  a.foff = foff;
+  std::vector<int32_t> parent_host(S.parent);
+  int32_t *par;
+  RC_TRY(mem.upload(&par, parent_host, st));
+  a.parent = par;
+  const size_t D = P.depth_sn.size();
+  for (size_t d = 0; d < D; ++d) {
+    a.Fcur = (d % 2) ? F1 : F0;
+    a.Fprev = (d % 2) ? F0 : F1;
+    const int64_t g0 = P.gather_ptr[d], g1 = P.gather_ptr[d + 1];
+    if (g1 > g0) {
+      dim3 grid(static_cast<unsigned>(g1 - g0), static_cast<unsigned>(P.gather_ych[d]));
+      peers::k_si_gather<<<grid, 256, 0, st>>>(gsn + g0, a);
+      ++launches;
+    }
+    const int64_t b0 = P.bc_ptr[d], b1 = P.bc_ptr[d + 1];
+    if (b1 > b0) {
+      peers::k_si_bc<<<static_cast<unsigned>(b1 - b0), peers::kGemmThreads, 0, st>>>(bc + b0, a);
+      ++launches;
+    }
+    const int64_t c0 = P.cc_ptr[d], c1 = P.cc_ptr[d + 1];
+    if (c1 > c0) {
+      peers::k_si_cc<<<static_cast<unsigned>(c1 - c0), peers::kGemmThreads, 0, st>>>(cc + c0, a);
+      ++launches;
+    }
+    const int64_t q0 = P.q_ptr[d], q1 = P.q_ptr[d + 1];
+    if (q1 > q0) {
+      peers::k_si_query<<<static_cast<unsigned>((q1 - q0 + 255) / 256), 256, 0, st>>>(
+          qs + q0, q1 - q0, a, Rdev);
+      ++launches;
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
+  if (ctx->timing) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ctx->stats.sweep_s = ms * 1e-3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  ctx->stats.sweep_launches = launches;
+  ctx->stats.h2d_bytes = 0;
+  ctx->stats.d2h_bytes = 0;
+  if (host_out && S.nq > 0) {
+    CUDA_TRY(cudaMemcpyAsync(R, Rdev, sizeof(double) * S.nq, cudaMemcpyDeviceToHost, st));
+    ctx->stats.d2h_bytes = int64_t(sizeof(double)) * S.nq;
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return PEERS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -774,6 +1214,23 @@ int64_t peers_blockinv_fma(const peers_symbolic *sym) {
   std::string err;
   if (peers::blockinv_plan(sym->S, B, err) != PEERS_OK) return -1;
   return B.gemm_fma;
+}
+
+int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
+                       double *R, int flags) {
+  if (!ctx || !sym || !num || (!R && sym->S.nq > 0)) return peers_fail(PEERS_EINVAL, "null argument");
+  if (num->sym != sym) return peers_fail(PEERS_EINVAL, "numeric handle belongs to another plan");
+  std::string err;
+  int rc = si_query(ctx, sym, const_cast<peers_numeric *>(num), R, flags, err);
+  return rc == PEERS_OK ? rc : peers_fail(rc, err);
+}
+
+int64_t peers_selinv_fma(const peers_symbolic *sym) {
+  if (!sym) return -1;
+  peers::SelInvPlan P;
+  std::string err;
+  if (peers::selinv_plan(sym->S, P, err) != PEERS_OK) return -1;
+  return P.fma;
 }
 
 int peers_query_blockinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,

@@ -108,6 +108,8 @@ def load(path: str | None = None):
         "peers_query_blockinv": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
         "peers_blockinv_bytes": (i64, [vp]),
         "peers_blockinv_fma": (i64, [vp]),
+        "peers_query_selinv": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+        "peers_selinv_fma": (i64, [vp]),
         "peers_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_char_p, vp, vp]),
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "peers_last_stats": (ctypes.c_int, [vp, P(Stats)]),
@@ -279,6 +281,17 @@ def query_blockinv(ctx: Context, sym: Symbolic, num: Numeric, out=None):
     flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
     _check(lib.peers_query_blockinv(ctx._h, sym._h, num._h, _ptr(out), flags),
            "peers_query_blockinv")
+    return out
+
+
+def query_selinv(ctx: Context, sym: Symbolic, num: Numeric, out=None):
+    """Resistances of the plan's queries from the selected inverse (edges and pairs touching
+    the ground only); same interface as :func:`query`."""
+    lib = load()
+    if out is None:
+        out = np.empty(sym.nq, dtype=np.float64)
+    flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
+    _check(lib.peers_query_selinv(ctx._h, sym._h, num._h, _ptr(out), flags), "peers_query_selinv")
     return out
 
 

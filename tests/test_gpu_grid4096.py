@@ -43,3 +43,20 @@ def test_grid4096_sampled_parity(P):
     err = float(np.max(np.abs(R - Ro) / Ro))
     print(f"grid4096: factor {factor_s:.2f} s on the device, max rel err {err:.3e}")
     assert err <= TOL
+
+
+def test_grid4096_all_edges_by_selected_inversion(P):
+    """All 33 546 240 edges of the 16.7M-node grid from the selected inverse: the stored oracle
+    sample to 1e-9 and Foster's theorem over every edge."""
+    d = json.load(open(GOLDEN))
+    g = I.grid4096()
+    ctx = P.Context(0)
+    sym = P.Symbolic.of(g)
+    num = P.Numeric(ctx, sym)
+    R = P.query_selinv(ctx, sym, num)
+    assert R.size == 33546240
+    idx = np.array(d["edge_index"])
+    Ro = np.array(d["R"])
+    assert float(np.max(np.abs(R[idx] - Ro) / Ro)) <= TOL
+    foster = float(np.sum(g.edge_weights() * R) / (g.n - 1))
+    assert abs(foster - 1.0) < 1e-9

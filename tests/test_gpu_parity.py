@@ -266,3 +266,31 @@ def test_block_inverse_pairs_split_by_the_ground(P, ctx, oracle_mod):
     nz = Ro != 0
     assert np.all(Rb[~nz] == 0)
     assert maxrel(Rb[nz], Ro[nz]) <= TOL
+
+
+@pytest.mark.parametrize("name", ["grid32", "grid-rect", "pdn3-49", "rgg-6000", "grid-200"])
+def test_selected_inversion_matches_oracle(P, ctx, oracle_mod, name):
+    """Sigma = L_r^{-1} on the pattern of L (Takahashi recurrences): all edges and pairs
+    touching the ground."""
+    g = CASES[name]()
+    u, v = g.all_edges()
+    qu = np.concatenate([u, [0, 7, 0]]).astype(np.int32)
+    qv = np.concatenate([v, [9, 0, 0]]).astype(np.int32)
+    sym = P.Symbolic.of(g, 0, qu, qv)
+    num = P.Numeric(ctx, sym)
+    Rs = P.query_selinv(ctx, sym, num)
+    Ro = oracle_mod.resistance(g, qu, qv)
+    nz = Ro != 0
+    assert np.all(Rs[~nz] == 0)
+    assert maxrel(Rs[nz], Ro[nz]) <= TOL
+    assert maxrel(Rs[nz], P.query(ctx, sym, num)[nz]) <= TOL
+
+
+def test_selected_inversion_rejects_pairs_outside_the_pattern(P, ctx):
+    g = I.grid2d(20, 20, seed=31)
+    pu, pv = I.random_pairs(g.n, 50, seed=32)
+    sym = P.Symbolic.of(g, 0, pu, pv)
+    num = P.Numeric(ctx, sym)
+    with pytest.raises(P.PeersError) as e:
+        P.query_selinv(ctx, sym, num)
+    assert e.value.status == P.EINVAL

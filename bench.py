@@ -172,6 +172,23 @@ def tuning_cache():
                           os.path.join(tempfile.gettempdir(), "peers_tiles.txt"))
 
 
+def dist_max(value, dist=None, device=None):
+    """Largest `value` over all ranks (the job's time is its slowest rank's); the local value
+    when not distributed.  Works with gloo (CPU tensors) and nccl (device tensors)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each process `units_per_rank` units, when
+    the slowest took `seconds`."""
+    return units_per_rank * world / seconds
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -265,13 +282,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = stop_clocks(*clk)
-    t = e0.elapsed_time(e1) * 1e-3
-    if dist is not None:
-        tt = torch.tensor([t], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = dist_max(e0.elapsed_time(e1) * 1e-3, dist, f"cuda:{local}")
     step_s = t / args.steps
-    value = nq * args.steps * world / t
+    value = job_throughput(nq * args.steps, world, t)
 
     sweep_stats = ctx.last_stats()
     # the same queries by the block implicit inverse (the paper's order of work)
@@ -337,11 +350,7 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t0)
         num2.close()
         del num2
-    t_e2e = max(e2e_times)
-    if dist is not None:
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = dist_max(max(e2e_times), dist, f"cuda:{local}")
     # the e2e result must equal the device-resident result
     same = bool(np.array_equal(r_pin.numpy(), R.cpu().numpy()))
 
@@ -370,7 +379,8 @@ def run_ours(args):
                      "frac": walk_gbs / (hbm or HBM_FALLBACK_GBS),
                      "peak_source": "measured" if hbm else "fallback",
                      "bytes_per_step": 8 * info["walk_entries"]},
-        "e2e": {"value": nq * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": job_throughput(nq, world, t_e2e), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "includes": "factor + sweep",
                 "matches_device_result": same},
         "gpu_launches": int(launches),

@@ -178,6 +178,21 @@ int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_nu
 /* FMAs of the selected inversion for this plan. */
 int64_t peers_selinv_fma(const peers_symbolic *sym);
 
+/* ---- spectral sparsification (PEERS §II-B, Alg. 1) ---------------------------------------- */
+
+/* Draws q edges with probability p_e proportional to w_e R_e and weights each drawn edge by
+ * w_e / (q p_e), summed over its draws (Alg. 1).  All pointers are device pointers: w and R
+ * (m entries each, e.g. the conductances and the resistances of an all-edge peers_query),
+ * u (q uniform numbers in [0, 1) supplied by the caller: the call draws no random numbers of
+ * its own), count (m int64, the number of draws of each edge) and weight (m, the sparsifier's
+ * conductance of each edge; 0 for edges never drawn).
+ * Reproducibility: scores are quantised once in FP64 to k_e = floor(w_e R_e S) with
+ * S = floor(2^62 / m) / max_e(w_e R_e), so p_e = k_e / sum(k) and draw i picks the first edge
+ * whose cumulative weight exceeds floor(u_i sum(k)) -- exact integer work, the same on any
+ * machine.  Errors: PEERS_EINVAL, PEERS_ENOMEM, PEERS_ECUDA. */
+int peers_sparsify(peers_ctx *ctx, int64_t m, const double *w, const double *R, int64_t q,
+                   const double *u, int64_t *count, double *weight);
+
 /* ---- tile shapes --------------------------------------------------------------------------- */
 
 /* Re-tiles a factored plan's sweep with new per-size-class caps (see peers_options.qcap) and

@@ -152,3 +152,32 @@ def dense_resistance(g, qu, qv) -> np.ndarray:
     qu = np.asarray(qu, dtype=np.int64)
     qv = np.asarray(qv, dtype=np.int64)
     return Lp[qu, qu] + Lp[qv, qv] - 2.0 * Lp[qu, qv]
+
+
+def sparsify(w, R, q, u):
+    """Spectral sparsification by effective resistances, the paper's Alg. 1: q draws of an edge
+    with probability p_e proportional to w_e R_e; each draw adds w_e / (q p_e) to its edge.
+    The probabilities are the quantised ones the library documents (integer weights
+    k_e = floor(w_e R_e S), S = floor(2^62/m) / max(w R)), so that the draws -- an integer
+    decision -- are made from the same numbers on both sides; u holds the q uniform draws.
+    Returns (count per edge, sparsifier conductance per edge)."""
+    w = np.asarray(w, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    m = w.size
+    s = w * R
+    s = np.where(s > 0, s, 0.0)
+    smax = s.max()
+    scale_num = np.floor(np.ldexp(1.0, 62) / m)
+    S = scale_num / smax if smax > 0 else 0.0
+    k = np.floor(s * S).astype(np.int64)
+    C = np.cumsum(k)
+    K = int(C[-1])
+    t = np.floor(u * np.float64(K)).astype(np.int64)
+    t = np.clip(t, 0, K - 1)
+    idx = np.searchsorted(C, t, side="right")          # first edge with C > t
+    count = np.bincount(idx[idx < m], minlength=m).astype(np.int64)
+    weight = np.zeros(m)
+    nz = (count > 0) & (k > 0)
+    weight[nz] = count[nz] * w[nz] * np.float64(K) / (np.float64(q) * k[nz].astype(np.float64))
+    return count, weight

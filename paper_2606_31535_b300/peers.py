@@ -109,6 +109,7 @@ def load(path: str | None = None):
         "peers_blockinv_bytes": (i64, [vp]),
         "peers_blockinv_fma": (i64, [vp]),
         "peers_query_selinv": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+        "peers_sparsify": (ctypes.c_int, [vp, i64, vp, vp, i64, vp, vp, vp]),
         "peers_selinv_fma": (i64, [vp]),
         "peers_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_char_p, vp, vp]),
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -293,6 +294,18 @@ def query_selinv(ctx: Context, sym: Symbolic, num: Numeric, out=None):
     flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
     _check(lib.peers_query_selinv(ctx._h, sym._h, num._h, _ptr(out), flags), "peers_query_selinv")
     return out
+
+
+def sparsify(ctx: Context, w, R, u):
+    """Alg. 1 on the device: w, R (m) and u (q uniforms) are float64 CUDA tensors; returns
+    (count int64, weight float64) CUDA tensors of m entries."""
+    import torch
+    m, q = int(w.numel()), int(u.numel())
+    count = torch.empty(m, dtype=torch.int64, device=w.device)
+    weight = torch.empty(m, dtype=torch.float64, device=w.device)
+    _check(load().peers_sparsify(ctx._h, m, _ptr(w), _ptr(R), q, _ptr(u), _ptr(count),
+                                 _ptr(weight)), "peers_sparsify")
+    return count, weight
 
 
 def blockinv_cost(sym: Symbolic) -> dict:

@@ -185,3 +185,26 @@ def test_elimination_tree_is_valid(oracle_mod):
     assert np.all((par == -1) | (par > k))
     assert np.all(d > 0)
     assert np.array_equal(np.sort(perm), np.arange(par.size))
+
+
+def test_sparsifier_is_unbiased_and_preserves_the_quadratic_form(oracle_mod):
+    """Alg. 1: every draw lands on an edge (counts sum to q), E[weight_e] = w_e, and the
+    sparsifier's Laplacian approximates the graph's on random vectors."""
+    g = I.grid2d(14, 15, seed=81, law="loguniform", lo=1e-2, hi=1e2)
+    u, v = g.all_edges()
+    w = g.edge_weights()
+    R = oracle_mod.resistance(g, u, v)
+    q = 400_000
+    draws = np.random.default_rng(82).random(q)
+    count, weight = oracle_mod.sparsify(w, R, q, draws)
+    assert count.sum() == q
+    # p_e ~ w_e R_e / (n - 1) by Foster; the heaviest edges are drawn near q p_e times
+    p = w * R / np.sum(w * R)
+    assert np.all(np.abs(count - q * p) <= 6 * np.sqrt(q * p) + 2)
+    assert abs(weight.sum() / w.sum() - 1) < 0.05
+    rng = np.random.default_rng(83)
+    for _ in range(10):
+        x = rng.standard_normal(g.n)
+        full = np.sum(w * (x[u] - x[v]) ** 2)
+        spars = np.sum(weight * (x[u] - x[v]) ** 2)
+        assert 0.8 < spars / full < 1.2

@@ -432,6 +432,13 @@ def run_batch(args):
     nums = [P.Numeric(ctx, s) for s in syms]
     torch.cuda.synchronize()
     t_factor = time.time() - t0
+    tiles = None
+    if not args.no_autotune:
+        # tune on the largest graph, then tile every plan with the same caps
+        big = max(range(len(syms)), key=lambda i: syms[i].info()["walk_entries"])
+        tiles = P.autotune(ctx, syms[big], nums[big], tuning_cache())
+        for s, m in zip(syms, nums):
+            P.retile(ctx, s, m, tiles["qcap"])
     batch = P.Batch(ctx, syms, nums, cuda_graph=True)
     binfo = batch.info()
     nq = sum(s.nq for s in syms)
@@ -507,6 +514,7 @@ def run_batch(args):
                 "d2h_bytes_per_step": int(d2h), "includes": "factor all 256 + batched sweep"},
         "gpu_launches": int(binfo["launches"] * args.steps),
         "clocks": clocks,
+        "tiles": tiles,
         "analysis": {"t_generate_s": t_gen, "t_analyze_s": t_analyze, "t_factor_s": t_factor,
                      "walk_entries": W},
     }
@@ -583,13 +591,22 @@ def run_serve(args):
         P.query(ctx, sym, P.Numeric(ctx, sym))
     t_single = (time.perf_counter() - t0) / len(sample)
     workers = max(2, min(8, (os.cpu_count() or 4) // 2))
+    opt = None
+    if not args.no_autotune:
+        g0, qu0, qv0 = max(reqs, key=lambda r: r[0].n)
+        s0 = P.Symbolic.of(g0, 0, qu0, qv0)
+        caps = P.autotune(ctx, s0, P.Numeric(ctx, s0), tuning_cache())["qcap"]
+        opt = P.Options()
+        opt.qcap[:] = caps
     nq_total = sum((g.m if qu is None else qu.size) for g, qu, qv in reqs)
     loads = []
     for rho in [float(x) for x in args.rho.split(",")]:
         arrivals = I.poisson_arrivals(len(reqs), rho / t_single, seed=4)
         arrivals -= arrivals[0]
-        lat_b, st_b = _replay(P, reqs, arrivals, {"max_active": 64, "workers": workers})
-        lat_1, st_1 = _replay(P, reqs, arrivals, {"max_active": 1, "workers": workers})
+        lat_b, st_b = _replay(P, reqs, arrivals, {"max_active": 64, "workers": workers,
+                                                  "options": opt})
+        lat_1, st_1 = _replay(P, reqs, arrivals, {"max_active": 1, "workers": workers,
+                                                  "options": opt})
         lat_p, qps_p = _replay_plain(P, ctx, reqs, arrivals)
         loads.append({
             "rho": rho, "arrival_rate_per_s": rho / t_single,

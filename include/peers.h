@@ -291,8 +291,10 @@ typedef struct peers_server_stats {
   double qps;                   /* completed queries / wall_s */
   double p50_s, p99_s, mean_s;  /* request latency, submit to results ready */
 } peers_server_stats;
+/* `opt` (may be NULL) is applied to the analysis of every request (ordering, tile caps,
+ * carry budget). */
 int peers_server_create(int device, int64_t mem_budget_bytes, int32_t max_active,
-                        int32_t workers, peers_server **out);
+                        int32_t workers, const peers_options *opt, peers_server **out);
 /* Same graph/query arguments as peers_analyze; returns a ticket. */
 int peers_server_submit(peers_server *sv, int64_t n, const int64_t *indptr,
                         const int32_t *indices, const double *w, int32_t ground, int64_t nq,

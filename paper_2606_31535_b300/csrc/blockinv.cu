@@ -560,6 +560,79 @@ struct SiQuery {
   int64_t out;
 };
 
+// A whole small supernode (n_c <= 32 columns, front N <= 64 rows) in one CTA: M from the
+// factor's diagonal-block inverse, Sigma[B,B] gathered from the parent's front, Sigma[B,C],
+// Sigma[C,C], the front written for the children, and the supernode's own queries answered.
+constexpr int kSiSmallN = 64;
+struct SiSmallArgs {
+  const double *panel, *tinv;
+  const int64_t *panel_off, *tinv_off;
+  const int64_t *qbeg, *qorig;
+  const int32_t *qa, *qb;
+  double *R;
+};
+
+__global__ void __launch_bounds__(256) k_si_small(const int32_t *__restrict__ sns, SiArgs a,
+                                                  SiSmallArgs b) {
+  extern __shared__ double sm_si[];
+  const int32_t s = sns[blockIdx.x];
+  const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
+  double *F = sm_si;            // N x N
+  double *Ti = F + N * N;       // nc x nc
+  double *Mm = Ti + nc * nc;    // nbv x nc
+  double *dv = Mm + nbv * nc;   // nc
+  const int32_t p = a.parent[s];
+  const int tid = threadIdx.x;
+  const double *TI = b.tinv + b.tinv_off[s];
+  for (int e = tid; e < nc * nc; e += blockDim.x) Ti[e] = TI[e];
+  for (int e = tid; e < nc; e += blockDim.x) dv[e] = a.dinv[f + e];
+  if (p >= 0) {
+    const int32_t Np = a.first[p + 1] - a.first[p] + a.nb[p];
+    const int32_t *rm = a.rmap + a.rows_off[s];
+    const double *Fp = a.Fprev + a.foff[p];
+    for (int e = tid; e < nbv * nbv; e += blockDim.x) {
+      const int i = e % nbv, j = e / nbv;
+      F[(nc + j) * N + nc + i] = Fp[int64_t(rm[j]) * Np + rm[i]];
+    }
+  }
+  __syncthreads();
+  // M[i][c] = sum_{k >= c} P[i][k] T^{-1}[k][c]
+  const double *P = b.panel + b.panel_off[s];
+  for (int e = tid; e < nbv * nc; e += blockDim.x) {
+    const int i = e / nc, c = e % nc;
+    double m = 0.0;
+    for (int k = c; k < nc; ++k) m = fma(P[int64_t(k) * N + nc + i], Ti[k * nc + c], m);
+    Mm[i * nc + c] = m;
+  }
+  __syncthreads();
+  // Sigma[B,C] = -Sigma[B,B] M
+  for (int e = tid; e < nbv * nc; e += blockDim.x) {
+    const int i = e % nbv, j = e / nbv;
+    double acc = 0.0;
+    for (int k = 0; k < nbv; ++k) acc = fma(F[(nc + k) * N + nc + i], Mm[k * nc + j], acc);
+    F[j * N + nc + i] = -acc;
+    F[(nc + i) * N + j] = -acc;
+  }
+  __syncthreads();
+  // Sigma[C,C] = T^{-T} D^{-1} T^{-1} - M^T Sigma[B,C]
+  for (int e = tid; e < nc * nc; e += blockDim.x) {
+    const int i = e % nc, j = e / nc;
+    double acc = 0.0;
+    for (int k = max(i, j); k < nc; ++k) acc = fma(Ti[k * nc + i] * dv[k], Ti[k * nc + j], acc);
+    for (int k = 0; k < nbv; ++k) acc = fma(-Mm[k * nc + i], F[j * N + nc + k], acc);
+    F[j * N + i] = acc;
+  }
+  __syncthreads();
+  double *Fg = a.Fcur + a.foff[s];
+  for (int e = tid; e < N * N; e += blockDim.x) Fg[e] = F[e];
+  for (int64_t q = b.qbeg[s] + tid; q < b.qbeg[s + 1]; q += blockDim.x) {
+    const int32_t qa = b.qa[q], qb = b.qb[q];
+    double r = F[qa * N + qa];
+    if (qb >= 0) r += F[qb * N + qb] - 2.0 * F[qa * N + qb];
+    b.R[b.qorig[q]] = r;
+  }
+}
+
 __global__ void k_si_query(const SiQuery *__restrict__ qs, int64_t nq, SiArgs args, double *R) {
   const int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (k >= nq) return;
@@ -785,6 +858,9 @@ struct SelInvPlan {
   std::vector<int64_t> bc_ptr, cc_ptr;
   std::vector<SiQuery> queries;
   std::vector<int64_t> q_ptr;
+  std::vector<int32_t> fused_sn;                   // whole small supernodes, by depth
+  std::vector<int64_t> fused_ptr;
+  std::vector<int64_t> fused_smem;                 // dynamic shared memory per depth
   std::vector<int32_t> small_sn, small_chunk, diag_sn, diag_blk;
   std::vector<Tile> m_tiles;
   int64_t fma = 0;
@@ -825,9 +901,13 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
   P.mtotal = P.moff[ns];
   P.fbuf = 0;
   for (int64_t x : fsize) P.fbuf = std::max(P.fbuf, x);
-  // phase 1 (T^{-1} and M) as in the block inverse
+  auto fused = [&](int32_t t) {
+    return sn_nc(S, t) <= kBlock && sn_nc(S, t) + S.nb[t] <= kSiSmallN;
+  };
+  // phase 1 (T^{-1} and M) as in the block inverse, for the supernodes not fused
   for (int32_t t = 0; t < ns; ++t) {
     const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+    if (fused(t)) continue;
     if (nc <= kBlock) {
       for (int32_t ch = 0; ch == 0 || ch * 256 < nbv; ++ch) {
         P.small_sn.push_back(t);
@@ -848,12 +928,23 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
   P.cc_ptr.assign(1, 0);
   P.q_ptr.assign(1, 0);
   std::vector<std::vector<SiQuery>> qd(maxd + 1);
-  for (int32_t s0 = 0; s0 < ns; ++s0)
+  for (int32_t s0 = 0; s0 < ns; ++s0) {
+    if (fused(s0)) continue;   // answered inside the fused kernel
     for (int64_t q = S.qbeg[s0]; q < S.qbeg[s0 + 1]; ++q)
       qd[depth[s0]].push_back({s0, S.qa[q], S.qb[q], 0, S.qorig[q]});
+  }
+  P.fused_sn.clear();
+  P.fused_ptr.assign(1, 0);
   for (int32_t d = 0; d <= maxd; ++d) {
     int32_t ych = 0;
+    int64_t fsm = 0;
     for (int32_t t : P.depth_sn[d]) {
+      if (fused(t)) {
+        P.fused_sn.push_back(t);
+        const int64_t nc = sn_nc(S, t), nbv = S.nb[t], N = nc + nbv;
+        fsm = std::max(fsm, 8 * (N * N + nc * nc + nbv * nc + nc));
+        continue;
+      }
       const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
       if (nbv > 0) {
         P.gather_sn.push_back(t);
@@ -870,6 +961,8 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
     P.cc_ptr.push_back(static_cast<int64_t>(P.cc.size()));
     P.queries.insert(P.queries.end(), qd[d].begin(), qd[d].end());
     P.q_ptr.push_back(static_cast<int64_t>(P.queries.size()));
+    P.fused_ptr.push_back(static_cast<int64_t>(P.fused_sn.size()));
+    P.fused_smem.push_back(fsm);
   }
   return PEERS_OK;
 }
@@ -1091,6 +1184,10 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   RC_TRY(mem.upload(&dsn, P.diag_sn, st));
   RC_TRY(mem.upload(&dblk, P.diag_blk, st));
   RC_TRY(mem.upload(&mt, P.m_tiles, st));
+  int32_t *fsn;
+  int64_t *qbeg;
+  RC_TRY(mem.upload(&fsn, P.fused_sn, st));
+  RC_TRY(mem.upload(&qbeg, S.qbeg, st));
   const bool host_out = !(flags & PEERS_OUT_DEVICE);
   if (host_out) RC_TRY(mem.alloc(&Rdev, S.nq));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1130,6 +1227,16 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
     ++launches;
   }
   CUDA_TRY(cudaGetLastError());
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&]() {
+    if (ctx->timing) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      cudaEventRecord(e, st);
+      ev.push_back(e);
+    }
+  };
+  mark();
   // phase 2: top-down by depth
   peers::SiArgs a{};
   a.dinv = num->dinv;
@@ -1146,10 +1253,33 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   int32_t *par;
   RC_TRY(mem.upload(&par, parent_host, st));
   a.parent = par;
+  {
+    int64_t need = 0;
+    for (int64_t x : P.fused_smem) need = std::max(need, x);
+    if (need > 48 * 1024)
+      CUDA_TRY(cudaFuncSetAttribute(peers::k_si_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(need)));
+  }
+  peers::SiSmallArgs sb{};
+  sb.panel = num->panel;
+  sb.tinv = num->tinv;
+  sb.panel_off = num->panel_off;
+  sb.tinv_off = num->tinv_off;
+  sb.qbeg = qbeg;
+  sb.qorig = num->qorig;
+  sb.qa = num->qa;
+  sb.qb = num->qb;
+  sb.R = Rdev;
   const size_t D = P.depth_sn.size();
   for (size_t d = 0; d < D; ++d) {
     a.Fcur = (d % 2) ? F1 : F0;
     a.Fprev = (d % 2) ? F0 : F1;
+    const int64_t f0 = P.fused_ptr[d], f1 = P.fused_ptr[d + 1];
+    if (f1 > f0) {
+      peers::k_si_small<<<static_cast<unsigned>(f1 - f0), 256, P.fused_smem[d], st>>>(fsn + f0,
+                                                                                     a, sb);
+      ++launches;
+    }
     const int64_t g0 = P.gather_ptr[d], g1 = P.gather_ptr[d + 1];
     if (g1 > g0) {
       dim3 grid(static_cast<unsigned>(g1 - g0), static_cast<unsigned>(P.gather_ych[d]));
@@ -1173,6 +1303,7 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
       ++launches;
     }
     CUDA_TRY(cudaGetLastError());
+    mark();
   }
   if (ctx->timing) {
     cudaEventRecord(e1, st);
@@ -1180,6 +1311,15 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     ctx->stats.sweep_s = ms * 1e-3;
+    // phase 1 (T^{-1} and M), then one entry per depth
+    ctx->level_ms.clear();
+    cudaEventElapsedTime(&ms, e0, ev[0]);
+    ctx->level_ms.push_back(ms);
+    for (size_t i = 0; i + 1 < ev.size(); ++i) {
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      ctx->level_ms.push_back(ms);
+    }
+    for (auto e : ev) cudaEventDestroy(e);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }

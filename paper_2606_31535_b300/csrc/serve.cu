@@ -71,6 +71,7 @@ struct Request {
 
 struct peers_server {
   int device = 0;
+  peers_options opt{};
   int64_t budget = 0;
   int32_t max_active = 0;
   std::mutex mu;
@@ -132,7 +133,7 @@ void worker_main(peers_server *sv) {
                            r->ground, r->all_edges ? -1 : static_cast<int64_t>(r->qu.size()),
                            r->all_edges ? nullptr : r->qu.data(),
                            r->all_edges ? nullptr : r->qv.data(),
-                           r->coords.empty() ? nullptr : r->coords.data(), r->dim, nullptr,
+                           r->coords.empty() ? nullptr : r->coords.data(), r->dim, &sv->opt,
                            &r->sym);
     bool reserved = false;
     if (rc == PEERS_OK) {
@@ -465,7 +466,7 @@ double percentile(std::vector<double> v, double p) {
 extern "C" {
 
 int peers_server_create(int device, int64_t mem_budget_bytes, int32_t max_active,
-                        int32_t workers, peers_server **out) {
+                        int32_t workers, const peers_options *opt, peers_server **out) {
   if (!out) return peers_fail(PEERS_EINVAL, "null output pointer");
   *out = nullptr;
   int count = 0;
@@ -476,6 +477,7 @@ int peers_server_create(int device, int64_t mem_budget_bytes, int32_t max_active
   auto *sv = new (std::nothrow) peers_server;
   if (!sv) return peers_fail(PEERS_ENOMEM, "host allocation");
   sv->device = device;
+  if (opt) sv->opt = *opt;
   sv->budget = mem_budget_bytes > 0 ? mem_budget_bytes : (int64_t(64) << 30);
   sv->max_active = max_active > 0 ? max_active : 64;
   if (workers <= 0) workers = 4;

@@ -97,7 +97,7 @@ def load(path: str | None = None):
         "peers_batch_free": (None, [vp]),
         "peers_query_batch": (ctypes.c_int, [vp, ctypes.c_int32, vp, vp, vp, ctypes.c_int]),
         "peers_server_create": (ctypes.c_int, [ctypes.c_int, i64, ctypes.c_int32, ctypes.c_int32,
-                                               P(vp)]),
+                                               vp, P(vp)]),
         "peers_server_submit": (ctypes.c_int, [vp, i64, vp, vp, vp, i32, i64, vp, vp, vp,
                                                ctypes.c_int, P(i64)]),
         "peers_server_poll": (ctypes.c_int, [vp, i64]),
@@ -387,11 +387,13 @@ class Server:
     """Continuous-batching request loop on one device (see peers_server_* in peers.h)."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0,
-                 workers: int = 0):
+                 workers: int = 0, options: Options | None = None):
         lib = load()
         h = ctypes.c_void_p()
+        self._opt = options
+        opt = ctypes.byref(options) if options is not None else None
         _check(lib.peers_server_create(int(device), int(mem_budget_bytes), int(max_active),
-                                       int(workers), ctypes.byref(h)), "peers_server_create")
+                                       int(workers), opt, ctypes.byref(h)), "peers_server_create")
         self._h = h
         self._nq = {}
 

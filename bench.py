@@ -373,7 +373,8 @@ def run_ours(args):
                      "traffic": profiled_traffic(args.workload),
                      "traffic_note": "DRAM bytes per k_sweep launch (ncu, profiles/)",
                      "kernel": "k_sweep (FP64 DFMA; peak = DFMA throughput measured live; "
-                               "mma.sync f64 measured %.3f TFLOP/s)" % peaks64["dmma"],
+                               "mma.sync f64 measured %.3f TFLOP/s, both at once %.3f)"
+                               % (peaks64["dmma"], peaks64["dfma_with_dmma"]),
                      "algorithmic": "2 flops x W walk entries per step, W = %d" % info["walk_entries"]},
         "hbm_walk": {"achieved_gbs": walk_gbs, "peak_gbs": hbm or HBM_FALLBACK_GBS,
                      "frac": walk_gbs / (hbm or HBM_FALLBACK_GBS),

@@ -330,10 +330,14 @@ int peers_last_stats(const peers_ctx *ctx, peers_stats *out);
 int peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap);
 
 /* Measures the FP64 throughput of the context's device with short register-only kernels
- * (about 50 ms): tflops[0] = DFMA on the CUDA cores, tflops[1] = mma.sync m8n8k4 f64 (the
- * FP64 tensor path), both in TFLOP/s with 2 flops per multiply-add.  tflops[0] is the sweep's
- * roofline denominator: the sweep is bound by FP64 FMA throughput. */
-int peers_fp64_peak(peers_ctx *ctx, double tflops[2]);
+ * (about 0.2 s), in TFLOP/s with 2 flops per multiply-add, into the caller's array of 3:
+ *   tflops[0]  DFMA on the CUDA cores;
+ *   tflops[1]  mma.sync m8n8k4 f64 (the FP64 tensor path);
+ *   tflops[2]  both at once, alternate warps of one kernel: near tflops[0] + tflops[1] if the
+ *              two use separate hardware, near max(tflops[0], tflops[1]) if they share it.
+ * tflops[0] is the sweep's roofline denominator: the sweep is bound by FP64 FMA throughput.
+ * Returns PEERS_EINVAL for a null argument, PEERS_ECUDA if a launch fails. */
+int peers_fp64_peak(peers_ctx *ctx, double tflops[3]);
 
 /* ---- misc ------------------------------------------------------------------------------- */
 const char *peers_strerror(int status);

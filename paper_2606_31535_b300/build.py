@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpeers.so")
-SOURCES = ["analyze.cpp", "factor.cu", "sweep.cu", "sweep_static.cu", "batch.cu", "serve.cu", "autotune.cu", "blockinv.cu", "sparsify.cu", "capi.cu"]
+SOURCES = ["analyze.cpp", "factor.cu", "sweep.cu", "peaks.cu", "sweep_static.cu", "batch.cu", "serve.cu", "autotune.cu", "blockinv.cu", "sparsify.cu", "capi.cu"]
 HEADERS = ["internal.h", "device.cuh", "handles.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

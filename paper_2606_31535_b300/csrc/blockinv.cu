@@ -417,8 +417,10 @@ __global__ void k_bi_query(const BiQuery *__restrict__ qs, int64_t nq, BiArgs a,
 //     Sigma[B,B] = the parent's inverse front restricted to B (a gather through rmap)
 //     Sigma[B,C] = -Sigma[B,B] M
 //     Sigma[C,C] = Zd^T D_C^{-1} Zd - M^T Sigma[B,C]
-// The inverse front F(s) = Sigma[rows(s), rows(s)] (both triangles, column-major) is all a
-// query starting at s needs: R = F[a,a] + F[b,b] - 2 F[b,a] (eq. 2 with L_r^{-1} = Sigma).
+// The inverse front F(s) = Sigma[rows(s), rows(s)] (column-major) is all a query starting at s
+// needs: R = F[a,a] + F[b,b] - 2 F[b,a] (eq. 2 with L_r^{-1} = Sigma).  Sigma is symmetric and
+// only the lower triangle of F is formed (its B,B block in full, as the product's operand);
+// every read of a front takes entry (max(i,j), min(i,j)).
 
 struct SiArgs {
   const double *dinv;
@@ -446,77 +448,110 @@ __global__ void __launch_bounds__(256) k_si_gather(const int32_t *__restrict__ s
   const double *Fp = a.Fprev + a.foff[p];
   double *F = a.Fcur + a.foff[s];
   for (int32_t j = j0; j < min(nbv, j0 + 8); ++j) {
-    const int64_t rj = rm[j];
-    for (int32_t i = threadIdx.x; i < nbv; i += blockDim.x)
-      F[int64_t(nc + j) * N + nc + i] = Fp[rj * Np + rm[i]];
+    const int32_t rj = rm[j];
+    for (int32_t i = threadIdx.x; i < nbv; i += blockDim.x) {
+      const int32_t ri = rm[i];
+      F[int64_t(nc + j) * N + nc + i] = Fp[int64_t(min(ri, rj)) * Np + max(ri, rj)];
+    }
   }
 }
 
-// Sigma[B,C] = -Sigma[B,B] M (and its transpose Sigma[C,B]).  Tiles over n_b x n_c.
-__global__ void __launch_bounds__(kGemmThreads) k_si_bc(const Tile *__restrict__ tiles, SiArgs a) {
-  __shared__ double As[kK][kT];
-  __shared__ double Bs[kK][kT];
-  const Tile tl = tiles[blockIdx.x];
+// Sigma[B,C] = -Sigma[B,B] M for one column chunk [c0, c0 + W) of C: one row of B per thread
+// with the chunk's W columns in registers, rows of M staged in shared memory.  The supernodes
+// are mostly narrow (a few to a few tens of columns over hundreds of rows), so the chunk width
+// follows n_c instead of padding to a square tile.  Tile = (supernode, row chunk, c0, W).
+constexpr int kBcRows = 128;
+constexpr int kBcK = 64;
+constexpr int kBcMaxW = 64;
+
+template <int W>
+__device__ __forceinline__ void si_bc_rows(const Tile &tl, const SiArgs &a, double *Ms) {
   const int32_t s = tl.t;
   const int32_t nc = a.first[s + 1] - a.first[s], nbv = a.nb[s], N = nc + nbv;
+  const int c0 = tl.c, wn = min(W, nc - c0);
   double *F = a.Fcur + a.foff[s];
   const double *M = a.M + a.moff[s];
-  const int R0 = tl.r * kT, C0 = tl.c * kT;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
-  for (int k0 = 0; k0 < nbv; k0 += kK) {
-    for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
-      const int k = e / kT, r = e % kT;
-      const int kk = k0 + k;
-      As[k][r] = (kk < nbv && R0 + r < nbv) ? F[int64_t(nc + kk) * N + nc + R0 + r] : 0.0;
-      Bs[k][r] = (kk < nbv && C0 + r < nc) ? M[int64_t(kk) * nc + C0 + r] : 0.0;
+  const int i = tl.r * kBcRows + threadIdx.x;
+  double acc[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) acc[c] = 0.0;
+  for (int k0 = 0; k0 < nbv; k0 += kBcK) {
+    const int kn = min(kBcK, nbv - k0);
+    for (int e = threadIdx.x; e < kBcK * W; e += kBcRows) {
+      const int kk = e / W, c = e - (e / W) * W;
+      Ms[e] = (kk < kn && c < wn) ? M[int64_t(k0 + kk) * nc + c0 + c] : 0.0;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < kK; ++k) {
-      double av[4], bv[4];
+    if (i < nbv) {
+      const double *Fk = F + int64_t(nc + k0) * N + nc + i;   // Sigma[B,B][i, k0 ..]
+      for (int kk = 0; kk < kn; ++kk) {
+        const double g = Fk[int64_t(kk) * N];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { av[u] = As[k][tx + 16 * u]; bv[u] = Bs[k][ty + 16 * u]; }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+        for (int c = 0; c < W; ++c) acc[c] = fma(g, Ms[kk * W + c], acc[c]);
+      }
     }
     __syncthreads();
   }
+  if (i < nbv) {
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int j = C0 + ty + 16 * v;
-    if (j >= nc) continue;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = R0 + tx + 16 * u;
-      if (i < nbv) {
-        F[int64_t(j) * N + nc + i] = -acc[u][v];
-        F[int64_t(nc + i) * N + j] = -acc[u][v];
-      }
-    }
+    for (int c = 0; c < W; ++c)
+      if (c < wn) F[int64_t(c0 + c) * N + nc + i] = -acc[c];
   }
 }
 
-// Sigma[C,C] = Zd^T D^{-1} Zd - M^T Sigma[B,C].  Tiles over n_c x n_c.
-__global__ void __launch_bounds__(kGemmThreads) k_si_cc(const Tile *__restrict__ tiles, SiArgs a) {
-  __shared__ double As[kK][kT];
-  __shared__ double Bs[kK][kT];
+// Three kernels by chunk width, so that narrow chunks are not held to the register count of
+// the widest: group 0 = widths 1..8, group 1 = 12..32, group 2 = 48..64.
+template <int G>
+__global__ void __launch_bounds__(kBcRows) k_si_bc(const Tile *__restrict__ tiles, SiArgs a) {
+  __shared__ double Ms[kBcK * (G == 0 ? 8 : G == 1 ? 32 : kBcMaxW)];
   const Tile tl = tiles[blockIdx.x];
+  if (G == 0) {
+    switch (tl.pad) {
+      case 1: si_bc_rows<1>(tl, a, Ms); break;
+      case 2: si_bc_rows<2>(tl, a, Ms); break;
+      case 4: si_bc_rows<4>(tl, a, Ms); break;
+      default: si_bc_rows<8>(tl, a, Ms); break;
+    }
+  } else if (G == 1) {
+    switch (tl.pad) {
+      case 12: si_bc_rows<12>(tl, a, Ms); break;
+      case 16: si_bc_rows<16>(tl, a, Ms); break;
+      case 24: si_bc_rows<24>(tl, a, Ms); break;
+      default: si_bc_rows<32>(tl, a, Ms); break;
+    }
+  } else {
+    if (tl.pad == 48) si_bc_rows<48>(tl, a, Ms); else si_bc_rows<64>(tl, a, Ms);
+  }
+}
+
+inline int bc_group(int w) { return w <= 8 ? 0 : w <= 32 ? 1 : 2; }
+
+inline int bc_width(int32_t cols) {
+  constexpr int kW[] = {1, 2, 4, 8, 12, 16, 24, 32, 48, 64};
+  for (int w : kW)
+    if (cols <= w) return w;
+  return kBcMaxW;
+}
+
+// Sigma[C,C] = Zd^T D^{-1} Zd - M^T Sigma[B,C], lower triangle: tiles (r >= c) of TS x TS over
+// n_c x n_c, TS = 16, 32 or 64 following n_c (Tile.pad); 16 x 16 threads, (TS/16)^2 outputs each.
+template <int TS>
+__device__ __forceinline__ void si_cc_tile(const Tile &tl, const SiArgs &a, double *As,
+                                           double *Bs) {
+  constexpr int U = TS / 16;
   const int32_t s = tl.t;
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
   double *F = a.Fcur + a.foff[s];
   const double *Zd = a.Zd + a.doff[s];
   const double *M = a.M + a.moff[s];
-  const int R0 = tl.r * kT, C0 = tl.c * kT;
+  const int R0 = tl.r * TS, C0 = tl.c * TS;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
+  double acc[U][U] = {};
   // Zd^T D^{-1} Zd: Zd[k, i] Zd[k, j] is non-zero only for k >= max(i, j)
   const int kstart = (max(R0, C0) / kK) * kK;
   for (int k0 = kstart; k0 < nc + nbv; k0 += kK) {
-    for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
-      const int k = e / kT, r = e % kT;
+    for (int e = threadIdx.x; e < kK * TS; e += kGemmThreads) {
+      const int k = e / TS, r = e - (e / TS) * TS;
       const int kk = k0 + k;
       double x = 0.0, y = 0.0;
       if (kk < nc) {
@@ -527,33 +562,46 @@ __global__ void __launch_bounds__(kGemmThreads) k_si_cc(const Tile *__restrict__
         if (R0 + r < nc) x = M[int64_t(b) * nc + R0 + r];
         if (C0 + r < nc) y = -F[int64_t(C0 + r) * N + nc + b];
       }
-      As[k][r] = x;
-      Bs[k][r] = y;
+      As[k * TS + r] = x;
+      Bs[k * TS + r] = y;
     }
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < kK; ++k) {
-      double av[4], bv[4];
+      double av[U], bv[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { av[u] = As[k][tx + 16 * u]; bv[u] = Bs[k][ty + 16 * u]; }
+      for (int u = 0; u < U; ++u) { av[u] = As[k * TS + tx + 16 * u]; bv[u] = Bs[k * TS + ty + 16 * u]; }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < U; ++v) {
     const int j = C0 + ty + 16 * v;
     if (j >= nc) continue;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int i = R0 + tx + 16 * u;
-      if (i < nc) F[int64_t(j) * N + i] = acc[u][v];
+      if (i < nc && i >= j) F[int64_t(j) * N + i] = acc[u][v];
     }
   }
 }
+
+__global__ void __launch_bounds__(kGemmThreads) k_si_cc(const Tile *__restrict__ tiles, SiArgs a) {
+  __shared__ double As[kK * kT];
+  __shared__ double Bs[kK * kT];
+  const Tile tl = tiles[blockIdx.x];
+  switch (tl.pad) {
+    case 16: si_cc_tile<16>(tl, a, As, Bs); break;
+    case 32: si_cc_tile<32>(tl, a, As, Bs); break;
+    default: si_cc_tile<64>(tl, a, As, Bs); break;
+  }
+}
+
+inline int cc_tile(int32_t nc) { return nc <= 16 ? 16 : nc <= 32 ? 32 : kT; }
 
 struct SiQuery {
   int32_t s, a, b, pad;   // start supernode, local rows of lo and hi in its front (b = -1: none)
@@ -592,7 +640,8 @@ __global__ void __launch_bounds__(256) k_si_small(const int32_t *__restrict__ sn
     const double *Fp = a.Fprev + a.foff[p];
     for (int e = tid; e < nbv * nbv; e += blockDim.x) {
       const int i = e % nbv, j = e / nbv;
-      F[(nc + j) * N + nc + i] = Fp[int64_t(rm[j]) * Np + rm[i]];
+      const int32_t ri = rm[i], rj = rm[j];
+      F[(nc + j) * N + nc + i] = Fp[int64_t(min(ri, rj)) * Np + max(ri, rj)];
     }
   }
   __syncthreads();
@@ -628,7 +677,7 @@ __global__ void __launch_bounds__(256) k_si_small(const int32_t *__restrict__ sn
   for (int64_t q = b.qbeg[s] + tid; q < b.qbeg[s + 1]; q += blockDim.x) {
     const int32_t qa = b.qa[q], qb = b.qb[q];
     double r = F[qa * N + qa];
-    if (qb >= 0) r += F[qb * N + qb] - 2.0 * F[qa * N + qb];
+    if (qb >= 0) r += F[qb * N + qb] - 2.0 * F[min(qa, qb) * N + max(qa, qb)];
     b.R[b.qorig[q]] = r;
   }
 }
@@ -640,7 +689,7 @@ __global__ void k_si_query(const SiQuery *__restrict__ qs, int64_t nq, SiArgs ar
   const int32_t N = args.first[q.s + 1] - args.first[q.s] + args.nb[q.s];
   const double *F = args.Fcur + args.foff[q.s];
   double r = F[int64_t(q.a) * N + q.a];
-  if (q.b >= 0) r += F[int64_t(q.b) * N + q.b] - 2.0 * F[int64_t(q.a) * N + q.b];
+  if (q.b >= 0) r += F[int64_t(q.b) * N + q.b] - 2.0 * F[int64_t(min(q.a, q.b)) * N + max(q.a, q.b)];
   R[q.out] = r;
 }
 
@@ -855,7 +904,7 @@ struct SelInvPlan {
   std::vector<int64_t> gather_ptr;
   std::vector<int32_t> gather_ych;                 // max column chunks per depth
   std::vector<Tile> bc, cc;
-  std::vector<int64_t> bc_ptr, cc_ptr;
+  std::vector<int64_t> bc_ptr, cc_ptr;             // bc_ptr: 3 width groups per depth
   std::vector<SiQuery> queries;
   std::vector<int64_t> q_ptr;
   std::vector<int32_t> fused_sn;                   // whole small supernodes, by depth
@@ -938,6 +987,7 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
   for (int32_t d = 0; d <= maxd; ++d) {
     int32_t ych = 0;
     int64_t fsm = 0;
+    std::vector<Tile> bcg[3];
     for (int32_t t : P.depth_sn[d]) {
       if (fused(t)) {
         P.fused_sn.push_back(t);
@@ -949,15 +999,22 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
       if (nbv > 0) {
         P.gather_sn.push_back(t);
         ych = std::max(ych, (nbv + 7) / 8);
-        for (int32_t r = 0; r * kT < nbv; ++r)
-          for (int32_t c = 0; c * kT < nc; ++c) P.bc.push_back({t, r, c, 0});
+        for (int32_t r = 0; r * kBcRows < nbv; ++r)
+          for (int32_t c0 = 0; c0 < nc; c0 += kBcMaxW) {
+            const int w = bc_width(std::min(kBcMaxW, nc - c0));
+            bcg[bc_group(w)].push_back({t, r, c0, w});
+          }
       }
-      for (int32_t r = 0; r * kT < nc; ++r)
-        for (int32_t c = 0; c * kT < nc; ++c) P.cc.push_back({t, r, c, 0});
+      const int ts = cc_tile(nc);
+      for (int32_t r = 0; r * ts < nc; ++r)
+        for (int32_t c = 0; c <= r; ++c) P.cc.push_back({t, r, c, ts});
     }
     P.gather_ptr.push_back(static_cast<int64_t>(P.gather_sn.size()));
     P.gather_ych.push_back(ych);
-    P.bc_ptr.push_back(static_cast<int64_t>(P.bc.size()));
+    for (int g = 0; g < 3; ++g) {
+      P.bc.insert(P.bc.end(), bcg[g].begin(), bcg[g].end());
+      P.bc_ptr.push_back(static_cast<int64_t>(P.bc.size()));
+    }
     P.cc_ptr.push_back(static_cast<int64_t>(P.cc.size()));
     P.queries.insert(P.queries.end(), qd[d].begin(), qd[d].end());
     P.q_ptr.push_back(static_cast<int64_t>(P.queries.size()));
@@ -1286,9 +1343,13 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
       peers::k_si_gather<<<grid, 256, 0, st>>>(gsn + g0, a);
       ++launches;
     }
-    const int64_t b0 = P.bc_ptr[d], b1 = P.bc_ptr[d + 1];
-    if (b1 > b0) {
-      peers::k_si_bc<<<static_cast<unsigned>(b1 - b0), peers::kGemmThreads, 0, st>>>(bc + b0, a);
+    for (int g = 0; g < 3; ++g) {
+      const int64_t b0 = P.bc_ptr[3 * d + g], b1 = P.bc_ptr[3 * d + g + 1];
+      if (b1 <= b0) continue;
+      const unsigned nb = static_cast<unsigned>(b1 - b0);
+      if (g == 0) peers::k_si_bc<0><<<nb, peers::kBcRows, 0, st>>>(bc + b0, a);
+      if (g == 1) peers::k_si_bc<1><<<nb, peers::kBcRows, 0, st>>>(bc + b0, a);
+      if (g == 2) peers::k_si_bc<2><<<nb, peers::kBcRows, 0, st>>>(bc + b0, a);
       ++launches;
     }
     const int64_t c0 = P.cc_ptr[d], c1 = P.cc_ptr[d + 1];

@@ -508,7 +508,7 @@ int peers_last_stats(const peers_ctx *ctx, peers_stats *out) {
   return PEERS_OK;
 }
 
-int peers_fp64_peak(peers_ctx *ctx, double tflops[2]) {
+int peers_fp64_peak(peers_ctx *ctx, double tflops[3]) {
   if (!ctx || !tflops) return fail(PEERS_EINVAL, "null argument");
   std::string err;
   auto run = [&]() -> int {

@@ -96,6 +96,6 @@ int query_noalloc(cudaStream_t stream, int device, const Symbolic &S, const Swee
 
 // FP64 throughput probes (TFLOP/s) on the current device: out[0] DFMA (CUDA cores),
 // out[1] mma.sync m8n8k4 f64 (the FP64 tensor path).
-int fp64_peak(cudaStream_t stream, double out[2], std::string &err);
+int fp64_peak(cudaStream_t stream, double out[3], std::string &err);
 
 }  // namespace peers

@@ -317,75 +317,4 @@ int run_two_branch_combine(const SweepArgs &args, const int64_t *two_user, const
   return PEERS_OK;
 }
 
-// Register-only DFMA chains: 8 independent accumulators per thread.
-__global__ void k_fp64_peak(double *out, int iters, double b, double c) {
-  double a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
-  double a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
-  for (int i = 0; i < iters; ++i) {
-    a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
-    a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
-  }
-  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
-}
-
-__device__ __forceinline__ void dmma_m8n8k4(double &d0, double &d1, double x, double y) {
-  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
-               : "+d"(d0), "+d"(d1)
-               : "d"(x), "d"(y));
-}
-
-// Four independent m8n8k4 FP64 MMA chains per warp.
-__global__ void k_dmma_peak(double *out, int iters, double x, double y) {
-  double c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, c6 = 0, c7 = 0;
-  for (int i = 0; i < iters; ++i) {
-    dmma_m8n8k4(c0, c1, x, y);
-    dmma_m8n8k4(c2, c3, x, y);
-    dmma_m8n8k4(c4, c5, x, y);
-    dmma_m8n8k4(c6, c7, x, y);
-  }
-  out[blockIdx.x * blockDim.x + threadIdx.x] = c0 + c1 + c2 + c3 + c4 + c5 + c6 + c7;
-}
-
-int fp64_peak(cudaStream_t stream, double out2[2], std::string &err) {
-  int dev = 0, sms = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int blocks = sms * 4, threads = 256, iters = 4096;
-  double *out = nullptr;
-  CUDA_TRY(cudaMalloc(&out, sizeof(double) * blocks * threads));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  double best = 0.0, best_mma = 0.0;
-  for (int rep = 0; rep < 4; ++rep) {
-    cudaEventRecord(e0, stream);
-    k_fp64_peak<<<blocks, threads, 0, stream>>>(out, iters, 1.0000001, 1e-9);
-    cudaEventRecord(e1, stream);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (rep > 0 && ms > 0) best = std::max(best, 2.0 * 8 * iters * double(blocks) * threads / (ms * 1e9));
-  }
-  for (int rep = 0; rep < 4; ++rep) {
-    const int mthreads = 128, miters = 1024;
-    cudaEventRecord(e0, stream);
-    k_dmma_peak<<<blocks, mthreads, 0, stream>>>(out, miters, 1.0, 1.0);
-    cudaEventRecord(e1, stream);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    // 4 MMAs of 8x8x4 per iteration per warp, 2 flops per multiply-add
-    const double flops = 2.0 * 8 * 8 * 4 * 4 * double(miters) * blocks * (mthreads / 32);
-    if (rep > 0 && ms > 0) best_mma = std::max(best_mma, flops / (ms * 1e9));
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaError_t e = cudaGetLastError();
-  cudaFree(out);
-  if (e != cudaSuccess) { err = cudaGetErrorString(e); return PEERS_ECUDA; }
-  out2[0] = best;
-  out2[1] = best_mma;
-  return PEERS_OK;
-}
-
 }  // namespace peers

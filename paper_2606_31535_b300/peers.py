@@ -177,10 +177,10 @@ class Context:
         return st.as_dict()
 
     def fp64_peaks(self) -> dict:
-        """Measured FP64 throughput (TFLOP/s): DFMA and mma.sync m8n8k4 f64."""
-        out = (ctypes.c_double * 2)()
+        """Measured FP64 throughput (TFLOP/s): DFMA, mma.sync m8n8k4 f64, and both at once."""
+        out = (ctypes.c_double * 3)()
         _check(load().peers_fp64_peak(self._h, out), "peers_fp64_peak")
-        return {"dfma": out[0], "dmma": out[1]}
+        return {"dfma": out[0], "dmma": out[1], "dfma_with_dmma": out[2]}
 
     def last_level_times(self) -> np.ndarray:
         buf = (ctypes.c_double * 4096)()

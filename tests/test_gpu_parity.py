@@ -294,3 +294,12 @@ def test_selected_inversion_rejects_pairs_outside_the_pattern(P, ctx):
     with pytest.raises(P.PeersError) as e:
         P.query_selinv(ctx, sym, num)
     assert e.value.status == P.EINVAL
+
+
+def test_fp64_peaks_are_measured(P, ctx):
+    """The roofline denominators: DFMA, the FP64 tensor path, and both issued together.  A
+    B300 runs FP64 at about 1.2 TFLOP/s (2 lane-ops per SM per cycle at 2 GHz); the bounds
+    are loose enough for any clock the part may run at."""
+    pk = ctx.fp64_peaks()
+    for key in ("dfma", "dmma", "dfma_with_dmma"):
+        assert 0.2 < pk[key] < 5.0, pk

@@ -51,45 +51,62 @@ struct BiArgs {
 
 // ---------------------------------------------------------------- phase 1a: T_t^{-1}
 
-// One CTA per (supernode, 32-column block J): columns J of T_t^{-1} by block forward
-// substitution, X_I = inv(T_II) (E_IJ - sum_{J<=K<I} T_IK X_K), written to Z[C_t, J].
-__global__ void __launch_bounds__(256) k_bi_diag(const int32_t *__restrict__ sns,
-                                                 const int32_t *__restrict__ blk, BiArgs a) {
+// One CTA per (supernode, 32-column block J, 8-column slice of it): those columns of T_t^{-1}
+// by block forward substitution, X_I = inv(T_II) (E_IJ - sum_{J<=K<I} T_IK X_K), written to
+// Z[C_t, cols].  A thread owns one row of a 32 x 8 output block: the warp's 32 rows read T
+// coalesced, and the X_K value they share is one broadcast load.  Slicing J four ways cuts the
+// longest CTA (the root's first block, whose substitution runs down all of C) to a quarter.
+constexpr int kDiagSlice = 8;
+constexpr int kDiagSlices = kBlock / kDiagSlice;
+
+__global__ void __launch_bounds__(kBlock * kDiagSlice) k_bi_diag(const int32_t *__restrict__ sns,
+                                                                 const int32_t *__restrict__ blk,
+                                                                 BiArgs a) {
   __shared__ double Ti[kBlock][kBlock + 1];
-  __shared__ double acc[kBlock][kBlock + 1];
-  const int32_t t = sns[blockIdx.x], J = blk[blockIdx.x];
+  __shared__ double acc[kBlock][kDiagSlice + 1];
+  const int32_t t = sns[blockIdx.x];
+  const int32_t J = blk[blockIdx.x] / kDiagSlices, sl = blk[blockIdx.x] % kDiagSlices;
   const int32_t nc = a.first[t + 1] - a.first[t], N = nc + a.nb[t];
   const int32_t ld = a.plen[t];
   const double *P = a.panel + a.panel_off[t];
   double *Zt = a.Z + a.zoff[t];
-  const int c0 = J * kBlock, bwJ = min(kBlock, nc - c0);
+  const int c0 = J * kBlock;                        // the block's first column
+  const int s0 = c0 + sl * kDiagSlice;              // this slice's first column
+  const int sw = min(kDiagSlice, nc - s0);          // columns in the slice
   const int nblk = (nc + kBlock - 1) / kBlock;
+  const int i = threadIdx.x % kBlock, j = threadIdx.x / kBlock;
   for (int I = J; I < nblk; ++I) {
     const int r0 = I * kBlock, bwI = min(kBlock, nc - r0);
-    // acc = E_IJ - sum_K T[I rows, K cols] X_K   (X_K = Z[K rows, J cols], already written)
-    for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
-      const int i = e / kBlock, j = e % kBlock;
-      double s = 0.0;
-      if (i < bwI && j < bwJ) {
-        s = (I == J && i == j) ? 1.0 : 0.0;
-        for (int k = c0; k < r0; ++k)
-          s = fma(-P[int64_t(k) * N + r0 + i], Zt[int64_t(c0 + j) * ld + k], s);
+    // acc = E_IJ - sum_K T[I rows, K cols] X_K   (X_K = Z[K rows, slice], already written)
+    double s = 0.0;
+    if (i < bwI && j < sw) {
+      s = (r0 + i == s0 + j) ? 1.0 : 0.0;
+      const double *Tp = P + r0 + i;
+      const double *Xp = Zt + int64_t(s0 + j) * ld;
+      // X[k, s0 + j] is zero above the slice's own rows (k < s0 + j): start there
+      int k = s0 + j;
+      for (; k + 4 <= r0; k += 4) {
+        const double t0 = Tp[int64_t(k) * N], t1 = Tp[int64_t(k + 1) * N];
+        const double t2 = Tp[int64_t(k + 2) * N], t3 = Tp[int64_t(k + 3) * N];
+        const double x0 = Xp[k], x1 = Xp[k + 1], x2 = Xp[k + 2], x3 = Xp[k + 3];
+        s = fma(-t0, x0, s);
+        s = fma(-t1, x1, s);
+        s = fma(-t2, x2, s);
+        s = fma(-t3, x3, s);
       }
-      acc[i][j] = s;
+      for (; k < r0; ++k) s = fma(-Tp[int64_t(k) * N], Xp[k], s);
     }
+    acc[i][j] = s;
     const double *TI = a.tinv + a.tinv_off[t] + int64_t(I) * kBlock * kBlock;
     for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
-      const int i = e / kBlock, j = e % kBlock;
-      Ti[i][j] = (i < bwI && j < bwI) ? TI[i * bwI + j] : 0.0;
+      const int ii = e / kBlock, jj = e % kBlock;
+      Ti[ii][jj] = (ii < bwI && jj < bwI) ? TI[ii * bwI + jj] : 0.0;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
-      const int i = e / kBlock, j = e % kBlock;
-      if (i < bwI && j < bwJ) {
-        double s = 0.0;
-        for (int k = 0; k <= i; ++k) s = fma(Ti[i][k], acc[k][j], s);
-        Zt[int64_t(c0 + j) * ld + r0 + i] = s;
-      }
+    if (i < bwI && j < sw) {
+      double y = 0.0;
+      for (int k = 0; k <= i; ++k) y = fma(Ti[i][k], acc[k][j], y);
+      Zt[int64_t(s0 + j) * ld + r0 + i] = y;
     }
     __syncthreads();
   }
@@ -459,32 +476,49 @@ __global__ void __launch_bounds__(256) k_si_gather(const int32_t *__restrict__ s
 // Sigma[B,C] = -Sigma[B,B] M for one column chunk [c0, c0 + W) of C: one row of B per thread
 // with the chunk's W columns in registers, rows of M staged in shared memory.  The supernodes
 // are mostly narrow (a few to a few tens of columns over hundreds of rows), so the chunk width
-// follows n_c instead of padding to a square tile.  Tile = (supernode, row chunk, c0, W).
-constexpr int kBcRows = 128;
+// follows n_c instead of padding to a square tile.  Tile = (supernode, row chunk, c0, W); the
+// CTA covers `rows` rows (32, 64 or 128, chosen per depth so that the launch has enough warps
+// to occupy every SM sub-partition's FP64 unit).
+constexpr int kBcMaxRows = 128;
 constexpr int kBcK = 64;
 constexpr int kBcMaxW = 64;
 
 template <int W>
-__device__ __forceinline__ void si_bc_rows(const Tile &tl, const SiArgs &a, double *Ms) {
+__device__ __forceinline__ void si_bc_rows(const Tile &tl, const SiArgs &a, int rows, double *Ms) {
   const int32_t s = tl.t;
   const int32_t nc = a.first[s + 1] - a.first[s], nbv = a.nb[s], N = nc + nbv;
   const int c0 = tl.c, wn = min(W, nc - c0);
   double *F = a.Fcur + a.foff[s];
   const double *M = a.M + a.moff[s];
-  const int i = tl.r * kBcRows + threadIdx.x;
+  const int i = tl.r * rows + threadIdx.x;
   double acc[W];
 #pragma unroll
   for (int c = 0; c < W; ++c) acc[c] = 0.0;
   for (int k0 = 0; k0 < nbv; k0 += kBcK) {
     const int kn = min(kBcK, nbv - k0);
-    for (int e = threadIdx.x; e < kBcK * W; e += kBcRows) {
+    for (int e = threadIdx.x; e < kBcK * W; e += rows) {
       const int kk = e / W, c = e - (e / W) * W;
       Ms[e] = (kk < kn && c < wn) ? M[int64_t(k0 + kk) * nc + c0 + c] : 0.0;
     }
     __syncthreads();
     if (i < nbv) {
       const double *Fk = F + int64_t(nc + k0) * N + nc + i;   // Sigma[B,B][i, k0 ..]
-      for (int kk = 0; kk < kn; ++kk) {
+      int kk = 0;
+      // four loads in flight before their multiply-adds (narrow chunks are latency bound)
+      for (; kk + 4 <= kn; kk += 4) {
+        const double g0 = Fk[int64_t(kk) * N], g1 = Fk[int64_t(kk + 1) * N];
+        const double g2 = Fk[int64_t(kk + 2) * N], g3 = Fk[int64_t(kk + 3) * N];
+        const double *m = Ms + kk * W;
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(g0, m[c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(g1, m[W + c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(g2, m[2 * W + c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(g3, m[3 * W + c], acc[c]);
+      }
+      for (; kk < kn; ++kk) {
         const double g = Fk[int64_t(kk) * N];
 #pragma unroll
         for (int c = 0; c < W; ++c) acc[c] = fma(g, Ms[kk * W + c], acc[c]);
@@ -502,29 +536,28 @@ __device__ __forceinline__ void si_bc_rows(const Tile &tl, const SiArgs &a, doub
 // Three kernels by chunk width, so that narrow chunks are not held to the register count of
 // the widest: group 0 = widths 1..8, group 1 = 12..32, group 2 = 48..64.
 template <int G>
-__global__ void __launch_bounds__(kBcRows) k_si_bc(const Tile *__restrict__ tiles, SiArgs a) {
+__global__ void __launch_bounds__(kBcMaxRows) k_si_bc(const Tile *__restrict__ tiles, SiArgs a,
+                                                      int rows) {
   __shared__ double Ms[kBcK * (G == 0 ? 8 : G == 1 ? 32 : kBcMaxW)];
   const Tile tl = tiles[blockIdx.x];
   if (G == 0) {
     switch (tl.pad) {
-      case 1: si_bc_rows<1>(tl, a, Ms); break;
-      case 2: si_bc_rows<2>(tl, a, Ms); break;
-      case 4: si_bc_rows<4>(tl, a, Ms); break;
-      default: si_bc_rows<8>(tl, a, Ms); break;
+      case 1: si_bc_rows<1>(tl, a, rows, Ms); break;
+      case 2: si_bc_rows<2>(tl, a, rows, Ms); break;
+      case 4: si_bc_rows<4>(tl, a, rows, Ms); break;
+      default: si_bc_rows<8>(tl, a, rows, Ms); break;
     }
   } else if (G == 1) {
     switch (tl.pad) {
-      case 12: si_bc_rows<12>(tl, a, Ms); break;
-      case 16: si_bc_rows<16>(tl, a, Ms); break;
-      case 24: si_bc_rows<24>(tl, a, Ms); break;
-      default: si_bc_rows<32>(tl, a, Ms); break;
+      case 12: si_bc_rows<12>(tl, a, rows, Ms); break;
+      case 16: si_bc_rows<16>(tl, a, rows, Ms); break;
+      case 24: si_bc_rows<24>(tl, a, rows, Ms); break;
+      default: si_bc_rows<32>(tl, a, rows, Ms); break;
     }
   } else {
-    if (tl.pad == 48) si_bc_rows<48>(tl, a, Ms); else si_bc_rows<64>(tl, a, Ms);
+    if (tl.pad == 48) si_bc_rows<48>(tl, a, rows, Ms); else si_bc_rows<64>(tl, a, rows, Ms);
   }
 }
-
-inline int bc_group(int w) { return w <= 8 ? 0 : w <= 32 ? 1 : 2; }
 
 inline int bc_width(int32_t cols) {
   constexpr int kW[] = {1, 2, 4, 8, 12, 16, 24, 32, 48, 64};
@@ -532,6 +565,8 @@ inline int bc_width(int32_t cols) {
     if (cols <= w) return w;
   return kBcMaxW;
 }
+
+inline int bc_group(int w) { return w <= 8 ? 0 : w <= 32 ? 1 : 2; }
 
 // Sigma[C,C] = Zd^T D^{-1} Zd - M^T Sigma[B,C], lower triangle: tiles (r >= c) of TS x TS over
 // n_c x n_c, TS = 16, 32 or 64 following n_c (Tile.pad); 16 x 16 threads, (TS/16)^2 outputs each.
@@ -764,10 +799,11 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
       }
       continue;
     }
-    for (int32_t J = 0; J * kBlock < nc; ++J) {
-      B.diag_sn.push_back(t);
-      B.diag_blk.push_back(J);
-    }
+    for (int32_t J = 0; J * kBlock < nc; ++J)
+      for (int32_t sl = 0; sl < kDiagSlices && J * kBlock + sl * kDiagSlice < nc; ++sl) {
+        B.diag_sn.push_back(t);
+        B.diag_blk.push_back(J * kDiagSlices + sl);
+      }
     for (int32_t r = 0; r * kT < nbv; ++r)
       for (int32_t c = 0; c * kT < nc; ++c) B.m_tiles.push_back({t, r, c, 0});
   }
@@ -853,7 +889,7 @@ int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, T
     CUDA_TRY(cudaGetLastError());
   }
   if (!B.diag_sn.empty()) {
-    k_bi_diag<<<static_cast<unsigned>(B.diag_sn.size()), 256, 0, st>>>(d_dsn, d_dblk, a);
+    k_bi_diag<<<static_cast<unsigned>(B.diag_sn.size()), kBlock * kDiagSlice, 0, st>>>(d_dsn, d_dblk, a);
     ++*launches;
     CUDA_TRY(cudaGetLastError());
   }
@@ -905,6 +941,7 @@ struct SelInvPlan {
   std::vector<int32_t> gather_ych;                 // max column chunks per depth
   std::vector<Tile> bc, cc;
   std::vector<int64_t> bc_ptr, cc_ptr;             // bc_ptr: 3 width groups per depth
+  std::vector<int32_t> bc_rows;                    // rows per Sigma[B,C] CTA, per depth
   std::vector<SiQuery> queries;
   std::vector<int64_t> q_ptr;
   std::vector<int32_t> fused_sn;                   // whole small supernodes, by depth
@@ -915,7 +952,9 @@ struct SelInvPlan {
   int64_t fma = 0;
 };
 
-int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
+// sms: the device's multiprocessor count (sizes the Sigma[B,C] launches).
+int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
+  const int64_t target_ctas = int64_t(std::max(sms, 1)) * 16;
   if (S.nq_two > 0) {
     err = "the selected inverse covers pairs inside the pattern of L (every graph edge and "
           "every pair touching the ground); this plan lists " + std::to_string(S.nq_two) +
@@ -964,10 +1003,11 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
       }
       continue;
     }
-    for (int32_t J = 0; J * kBlock < nc; ++J) {
-      P.diag_sn.push_back(t);
-      P.diag_blk.push_back(J);
-    }
+    for (int32_t J = 0; J * kBlock < nc; ++J)
+      for (int32_t sl = 0; sl < kDiagSlices && J * kBlock + sl * kDiagSlice < nc; ++sl) {
+        P.diag_sn.push_back(t);
+        P.diag_blk.push_back(J * kDiagSlices + sl);
+      }
     for (int32_t r = 0; r * kT < nbv; ++r)
       for (int32_t c = 0; c * kT < nc; ++c) P.m_tiles.push_back({t, r, c, 0});
   }
@@ -999,11 +1039,6 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
       if (nbv > 0) {
         P.gather_sn.push_back(t);
         ych = std::max(ych, (nbv + 7) / 8);
-        for (int32_t r = 0; r * kBcRows < nbv; ++r)
-          for (int32_t c0 = 0; c0 < nc; c0 += kBcMaxW) {
-            const int w = bc_width(std::min(kBcMaxW, nc - c0));
-            bcg[bc_group(w)].push_back({t, r, c0, w});
-          }
       }
       const int ts = cc_tile(nc);
       for (int32_t r = 0; r * ts < nc; ++r)
@@ -1011,6 +1046,33 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, std::string &err) {
     }
     P.gather_ptr.push_back(static_cast<int64_t>(P.gather_sn.size()));
     P.gather_ych.push_back(ych);
+    // Sigma[B,C] chunks: the widest chunks and tallest CTAs that still give the launch many
+    // waves of CTAs (at least 16 per SM).  FP64 issue is so slow that one warp with W
+    // independent multiply-adds keeps an SM sub-partition's unit busy, so small CTAs lose
+    // little; a launch of few large CTAs loses up to half its time to the last, partial wave.
+    constexpr int kOpts[][2] = {{128, 64}, {64, 64}, {64, 32}, {32, 32}, {32, 16}, {32, 8}};
+    constexpr int kNOpts = sizeof(kOpts) / sizeof(kOpts[0]);
+    int opt = 0;
+    for (; opt < kNOpts - 1; ++opt) {
+      const int rows = kOpts[opt][0], wcap = kOpts[opt][1];
+      int64_t ctas = 0;
+      for (int32_t t : P.depth_sn[d]) {
+        if (fused(t) || S.nb[t] == 0) continue;
+        ctas += int64_t((S.nb[t] + rows - 1) / rows) * ((sn_nc(S, t) + wcap - 1) / wcap);
+      }
+      if (ctas >= target_ctas) break;
+    }
+    const int rows = kOpts[opt][0], wcap = kOpts[opt][1];
+    for (int32_t t : P.depth_sn[d]) {
+      if (fused(t) || S.nb[t] == 0) continue;
+      const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+      for (int32_t r = 0; r * rows < nbv; ++r)
+        for (int32_t c0 = 0; c0 < nc; c0 += wcap) {
+          const int w = bc_width(std::min(wcap, nc - c0));
+          bcg[bc_group(w)].push_back({t, r, c0, w});
+        }
+    }
+    P.bc_rows.push_back(rows);
     for (int g = 0; g < 3; ++g) {
       P.bc.insert(P.bc.end(), bcg[g].begin(), bcg[g].end());
       P.bc_ptr.push_back(static_cast<int64_t>(P.bc.size()));
@@ -1217,7 +1279,9 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   cudaStream_t st = ctx->stream;
   CUDA_TRY(cudaSetDevice(ctx->device));
   peers::SelInvPlan P;
-  RC_TRY(peers::selinv_plan(S, P, err));
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  RC_TRY(peers::selinv_plan(S, P, sms, err));
   DevMem mem(&err);
   double *Zd, *M, *F0, *F1, *Rdev = R;
   int32_t *ncs, *gsn, *ssn, *sch, *dsn, *dblk;
@@ -1276,7 +1340,8 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
     ++launches;
   }
   if (!P.diag_sn.empty()) {
-    peers::k_bi_diag<<<static_cast<unsigned>(P.diag_sn.size()), 256, 0, st>>>(dsn, dblk, b);
+    peers::k_bi_diag<<<static_cast<unsigned>(P.diag_sn.size()), peers::kBlock * peers::kDiagSlice, 0, st>>>(
+        dsn, dblk, b);
     ++launches;
   }
   if (!P.m_tiles.empty()) {
@@ -1347,9 +1412,10 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
       const int64_t b0 = P.bc_ptr[3 * d + g], b1 = P.bc_ptr[3 * d + g + 1];
       if (b1 <= b0) continue;
       const unsigned nb = static_cast<unsigned>(b1 - b0);
-      if (g == 0) peers::k_si_bc<0><<<nb, peers::kBcRows, 0, st>>>(bc + b0, a);
-      if (g == 1) peers::k_si_bc<1><<<nb, peers::kBcRows, 0, st>>>(bc + b0, a);
-      if (g == 2) peers::k_si_bc<2><<<nb, peers::kBcRows, 0, st>>>(bc + b0, a);
+      const int rows = P.bc_rows[d];
+      if (g == 0) peers::k_si_bc<0><<<nb, rows, 0, st>>>(bc + b0, a, rows);
+      if (g == 1) peers::k_si_bc<1><<<nb, rows, 0, st>>>(bc + b0, a, rows);
+      if (g == 2) peers::k_si_bc<2><<<nb, rows, 0, st>>>(bc + b0, a, rows);
       ++launches;
     }
     const int64_t c0 = P.cc_ptr[d], c1 = P.cc_ptr[d + 1];
@@ -1430,7 +1496,7 @@ int64_t peers_selinv_fma(const peers_symbolic *sym) {
   if (!sym) return -1;
   peers::SelInvPlan P;
   std::string err;
-  if (peers::selinv_plan(sym->S, P, err) != PEERS_OK) return -1;
+  if (peers::selinv_plan(sym->S, P, 148, err) != PEERS_OK) return -1;   // work does not depend on it
   return P.fma;
 }
 

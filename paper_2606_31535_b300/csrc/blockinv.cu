@@ -1035,12 +1035,29 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
         fsm = std::max(fsm, 8 * (N * N + nc * nc + nbv * nc + nc));
         continue;
       }
-      const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+      const int32_t nbv = S.nb[t];
       if (nbv > 0) {
         P.gather_sn.push_back(t);
         ych = std::max(ych, (nbv + 7) / 8);
       }
-      const int ts = cc_tile(nc);
+    }
+    // Sigma[C,C] tiles: the largest tile (64, 32, 16; never wider than n_c needs) that still
+    // gives the launch many CTAs, as for Sigma[B,C]
+    int cc_cap = kT;
+    for (; cc_cap > 16; cc_cap /= 2) {
+      int64_t ctas = 0;
+      for (int32_t t : P.depth_sn[d]) {
+        if (fused(t)) continue;
+        const int64_t nt = (sn_nc(S, t) + std::min(cc_cap, cc_tile(sn_nc(S, t))) - 1) /
+                           std::min(cc_cap, cc_tile(sn_nc(S, t)));
+        ctas += nt * (nt + 1) / 2;
+      }
+      if (ctas >= target_ctas) break;
+    }
+    for (int32_t t : P.depth_sn[d]) {
+      if (fused(t)) continue;
+      const int32_t nc = sn_nc(S, t);
+      const int ts = std::min(cc_cap, cc_tile(nc));
       for (int32_t r = 0; r * ts < nc; ++r)
         for (int32_t c = 0; c <= r; ++c) P.cc.push_back({t, r, c, ts});
     }

@@ -159,50 +159,181 @@ struct Tile {
   int32_t t, r, c, pad;
 };
 
-// Phase 1b: M_t = L[B_t, C_t] * Z[C_t, C_t] (lower-triangular right factor: k >= j).
-__global__ void __launch_bounds__(kGemmThreads) k_bi_m(const Tile *__restrict__ tiles, BiArgs a) {
-  __shared__ double As[kK][kT];
-  __shared__ double Bs[kK][kT];
+// ---------------------------------------------------------------- row-per-thread products
+//
+// out(i, c) = (+/-) sum_{k = kb}^{ke-1} A[k * lda + i] * B(k, c) for the rows i of one chunk
+// and the columns [c0, c0 + W) of one chunk: one row per thread with its W sums in registers,
+// B staged in shared memory kRowsK rows at a time, A read coalesced across the warp.  The
+// products on this path are tall and narrow (hundreds to thousands of rows, a few to a few
+// tens of columns), where square tiles would spend most of their multiply-adds on padding.
+// Each sum runs in increasing k, so a result does not depend on the chunking.
+// Tile = (block, row chunk, c0, W).
+constexpr int kRowsMaxThreads = 128;
+constexpr int kRowsK = 64;
+constexpr int kRowsMaxW = 64;
+
+struct RowsGemm {
+  const double *A;
+  int64_t lda;            // A[k * lda + i]
+  const double *B;
+  int64_t bk, bc;         // B(k, c) = B[k * bk + c * bc]
+  double *out;
+  int64_t oi, oc;         // out(i, c) = out[i * oi + c * oc]
+  int32_t nrows, kb, ke, ncols;
+  bool negate;
+};
+
+template <int W>
+__device__ __forceinline__ void rows_gemm(const RowsGemm &g, int r, int c0, int rows, double *Ms) {
+  const int wn = min(W, g.ncols - c0);
+  const int i = r * rows + threadIdx.x;
+  double acc[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) acc[c] = 0.0;
+  for (int k0 = g.kb; k0 < g.ke; k0 += kRowsK) {
+    const int kn = min(kRowsK, g.ke - k0);
+    for (int e = threadIdx.x; e < kRowsK * W; e += rows) {
+      // read B along whichever of its two dimensions is contiguous
+      int kk, c;
+      if (g.bk == 1) { c = e / kRowsK; kk = e - c * kRowsK; }
+      else { kk = e / W; c = e - kk * W; }
+      Ms[kk * W + c] = (kk < kn && c < wn) ? g.B[int64_t(k0 + kk) * g.bk + int64_t(c0 + c) * g.bc]
+                                           : 0.0;
+    }
+    __syncthreads();
+    if (i < g.nrows) {
+      const double *Ak = g.A + int64_t(k0) * g.lda + i;
+      int kk = 0;
+      // four loads in flight before their multiply-adds (narrow chunks are latency bound)
+      for (; kk + 4 <= kn; kk += 4) {
+        const double g0 = Ak[int64_t(kk) * g.lda], g1 = Ak[int64_t(kk + 1) * g.lda];
+        const double g2 = Ak[int64_t(kk + 2) * g.lda], g3 = Ak[int64_t(kk + 3) * g.lda];
+        const double *m = Ms + kk * W;
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(g0, m[c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(g1, m[W + c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(g2, m[2 * W + c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(g3, m[3 * W + c], acc[c]);
+      }
+      for (; kk < kn; ++kk) {
+        const double a0 = Ak[int64_t(kk) * g.lda];
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(a0, Ms[kk * W + c], acc[c]);
+      }
+    }
+    __syncthreads();
+  }
+  if (i < g.nrows) {
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+      if (c < wn) g.out[int64_t(i) * g.oi + int64_t(c0 + c) * g.oc] = g.negate ? -acc[c] : acc[c];
+  }
+}
+
+// Chunk widths, in three groups compiled as separate kernels so that narrow chunks are not
+// held to the register count of the widest: group 0 = 1..8, group 1 = 12..32, group 2 = 48..64.
+inline int rows_width(int32_t cols) {
+  constexpr int kW[] = {1, 2, 4, 8, 12, 16, 24, 32, 48, 64};
+  for (int w : kW)
+    if (cols <= w) return w;
+  return kRowsMaxW;
+}
+inline int rows_group(int w) { return w <= 8 ? 0 : w <= 32 ? 1 : 2; }
+__host__ __device__ constexpr int rows_group_width(int g) { return g == 0 ? 8 : g == 1 ? 32 : kRowsMaxW; }
+
+template <int G>
+__device__ __forceinline__ void rows_gemm_dispatch(const RowsGemm &g, const Tile &tl, int rows,
+                                                   double *Ms) {
+  if (G == 0) {
+    switch (tl.pad) {
+      case 1: rows_gemm<1>(g, tl.r, tl.c, rows, Ms); break;
+      case 2: rows_gemm<2>(g, tl.r, tl.c, rows, Ms); break;
+      case 4: rows_gemm<4>(g, tl.r, tl.c, rows, Ms); break;
+      default: rows_gemm<8>(g, tl.r, tl.c, rows, Ms); break;
+    }
+  } else if (G == 1) {
+    switch (tl.pad) {
+      case 12: rows_gemm<12>(g, tl.r, tl.c, rows, Ms); break;
+      case 16: rows_gemm<16>(g, tl.r, tl.c, rows, Ms); break;
+      case 24: rows_gemm<24>(g, tl.r, tl.c, rows, Ms); break;
+      default: rows_gemm<32>(g, tl.r, tl.c, rows, Ms); break;
+    }
+  } else {
+    if (tl.pad == 48) rows_gemm<48>(g, tl.r, tl.c, rows, Ms);
+    else rows_gemm<64>(g, tl.r, tl.c, rows, Ms);
+  }
+}
+
+// Phase 1b: M_t = L[B_t, C_t] * Z[C_t, C_t] (row-major n_b x n_c) by the row-per-thread
+// product.  Z[C_t, C_t] = T_t^{-1} is lower triangular, so a column chunk starting at c0 only
+// needs k >= c0 (the entries above the diagonal are stored zeros).
+constexpr int kMRows = 64;
+template <int G>
+__global__ void __launch_bounds__(kRowsMaxThreads) k_bi_m(const Tile *__restrict__ tiles, BiArgs a) {
+  __shared__ double Ms[kRowsK * rows_group_width(G)];
   const Tile tl = tiles[blockIdx.x];
   const int32_t t = tl.t;
   const int32_t nc = a.first[t + 1] - a.first[t], nbv = a.nb[t], N = nc + nbv;
-  const int32_t ld = a.plen[t];
-  const double *P = a.panel + a.panel_off[t];
-  const double *Zt = a.Z + a.zoff[t];
-  const int R0 = tl.r * kT, C0 = tl.c * kT;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
-  for (int k0 = C0; k0 < nc; k0 += kK) {   // Z[k, j] = 0 for k < j
-    for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
-      const int k = e / kT, r = e % kT;
-      const int kk = k0 + k;
-      As[k][r] = (kk < nc && R0 + r < nbv) ? P[int64_t(kk) * N + nc + R0 + r] : 0.0;
-      Bs[k][r] = (kk < nc && C0 + r < nc) ? Zt[int64_t(C0 + r) * ld + kk] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < kK; ++k) {
-      double av[4], bv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) { av[u] = As[k][tx + 16 * u]; bv[u] = Bs[k][ty + 16 * u]; }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
-    }
-    __syncthreads();
+  RowsGemm g;
+  g.A = a.panel + a.panel_off[t] + nc;
+  g.lda = N;
+  g.B = a.Z + a.zoff[t];
+  g.bk = 1;
+  g.bc = a.plen[t];
+  g.out = a.M + a.moff[t];
+  g.oi = nc;
+  g.oc = 1;
+  g.nrows = nbv;
+  g.kb = tl.c;
+  g.ke = nc;
+  g.ncols = nc;
+  g.negate = false;
+  rows_gemm_dispatch<G>(g, tl, kMRows, Ms);
+}
+
+// The tiles of M_t for every wide supernode, grouped by width, the largest products first
+// (the launch's last wave then holds only small ones).
+inline void m_tiles_of(const Symbolic &S, const std::vector<int32_t> &wide,
+                       std::vector<Tile> &tiles, std::vector<int64_t> &ptr) {
+  std::vector<Tile> grp[3];
+  for (int32_t t : wide) {
+    const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+    for (int32_t r = 0; r * kMRows < nbv; ++r)
+      for (int32_t c0 = 0; c0 < nc; c0 += kRowsMaxW) {
+        const int w = rows_width(std::min(kRowsMaxW, nc - c0));
+        grp[rows_group(w)].push_back({t, r, c0, w});
+      }
   }
-  double *Mt = a.M + a.moff[t];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int j = C0 + ty + 16 * v;
-    if (j >= nc) continue;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = R0 + tx + 16 * u;
-      if (i < nbv) Mt[int64_t(i) * nc + j] = acc[u][v];   // row-major n_b x n_c
-    }
+  tiles.clear();
+  ptr.assign(1, 0);
+  for (auto &g : grp) {
+    std::stable_sort(g.begin(), g.end(), [&](const Tile &x, const Tile &y) {
+      return int64_t(sn_nc(S, x.t) - x.c) * x.pad > int64_t(sn_nc(S, y.t) - y.c) * y.pad;
+    });
+    tiles.insert(tiles.end(), g.begin(), g.end());
+    ptr.push_back(static_cast<int64_t>(tiles.size()));
   }
+}
+
+template <int G>
+int launch_m(const Tile *d_tiles, const std::vector<int64_t> &ptr, const BiArgs &a,
+             cudaStream_t st, int64_t *launches, std::string &err) {
+  const int64_t n = ptr[G + 1] - ptr[G];
+  if (n <= 0) return PEERS_OK;
+  k_bi_m<G><<<static_cast<unsigned>(n), kMRows, 0, st>>>(d_tiles + ptr[G], a);
+  ++*launches;
+  CUDA_TRY(cudaGetLastError());
+  return PEERS_OK;
+}
+int launch_m_all(const Tile *d_tiles, const std::vector<int64_t> &ptr, const BiArgs &a,
+                 cudaStream_t st, int64_t *launches, std::string &err) {
+  int rc = launch_m<0>(d_tiles, ptr, a, st, launches, err);
+  if (rc == PEERS_OK) rc = launch_m<1>(d_tiles, ptr, a, st, launches, err);
+  if (rc == PEERS_OK) rc = launch_m<2>(d_tiles, ptr, a, st, launches, err);
+  return rc;
 }
 
 // Phase 2: Z[P_par, C_t] = -Z[P_par, B_t] * M_t for the supernodes of one depth.  Row tile r
@@ -473,100 +604,32 @@ __global__ void __launch_bounds__(256) k_si_gather(const int32_t *__restrict__ s
   }
 }
 
-// Sigma[B,C] = -Sigma[B,B] M for one column chunk [c0, c0 + W) of C: one row of B per thread
-// with the chunk's W columns in registers, rows of M staged in shared memory.  The supernodes
-// are mostly narrow (a few to a few tens of columns over hundreds of rows), so the chunk width
-// follows n_c instead of padding to a square tile.  Tile = (supernode, row chunk, c0, W); the
-// CTA covers `rows` rows (32, 64 or 128, chosen per depth so that the launch has enough warps
-// to occupy every SM sub-partition's FP64 unit).
-constexpr int kBcMaxRows = 128;
-constexpr int kBcK = 64;
-constexpr int kBcMaxW = 64;
-
-template <int W>
-__device__ __forceinline__ void si_bc_rows(const Tile &tl, const SiArgs &a, int rows, double *Ms) {
+// Sigma[B,C] = -Sigma[B,B] M by the row-per-thread product (rows_gemm): A = Sigma[B,B] (the
+// front's B,B block, column-major), B = M (row-major n_b x n_c), out = the front's B,C block.
+template <int G>
+__global__ void __launch_bounds__(kRowsMaxThreads) k_si_bc(const Tile *__restrict__ tiles,
+                                                           SiArgs a, int rows) {
+  __shared__ double Ms[kRowsK * rows_group_width(G)];
+  const Tile tl = tiles[blockIdx.x];
   const int32_t s = tl.t;
   const int32_t nc = a.first[s + 1] - a.first[s], nbv = a.nb[s], N = nc + nbv;
-  const int c0 = tl.c, wn = min(W, nc - c0);
   double *F = a.Fcur + a.foff[s];
-  const double *M = a.M + a.moff[s];
-  const int i = tl.r * rows + threadIdx.x;
-  double acc[W];
-#pragma unroll
-  for (int c = 0; c < W; ++c) acc[c] = 0.0;
-  for (int k0 = 0; k0 < nbv; k0 += kBcK) {
-    const int kn = min(kBcK, nbv - k0);
-    for (int e = threadIdx.x; e < kBcK * W; e += rows) {
-      const int kk = e / W, c = e - (e / W) * W;
-      Ms[e] = (kk < kn && c < wn) ? M[int64_t(k0 + kk) * nc + c0 + c] : 0.0;
-    }
-    __syncthreads();
-    if (i < nbv) {
-      const double *Fk = F + int64_t(nc + k0) * N + nc + i;   // Sigma[B,B][i, k0 ..]
-      int kk = 0;
-      // four loads in flight before their multiply-adds (narrow chunks are latency bound)
-      for (; kk + 4 <= kn; kk += 4) {
-        const double g0 = Fk[int64_t(kk) * N], g1 = Fk[int64_t(kk + 1) * N];
-        const double g2 = Fk[int64_t(kk + 2) * N], g3 = Fk[int64_t(kk + 3) * N];
-        const double *m = Ms + kk * W;
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[c] = fma(g0, m[c], acc[c]);
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[c] = fma(g1, m[W + c], acc[c]);
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[c] = fma(g2, m[2 * W + c], acc[c]);
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[c] = fma(g3, m[3 * W + c], acc[c]);
-      }
-      for (; kk < kn; ++kk) {
-        const double g = Fk[int64_t(kk) * N];
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[c] = fma(g, Ms[kk * W + c], acc[c]);
-      }
-    }
-    __syncthreads();
-  }
-  if (i < nbv) {
-#pragma unroll
-    for (int c = 0; c < W; ++c)
-      if (c < wn) F[int64_t(c0 + c) * N + nc + i] = -acc[c];
-  }
+  RowsGemm g;
+  g.A = F + int64_t(nc) * N + nc;
+  g.lda = N;
+  g.B = a.M + a.moff[s];
+  g.bk = nc;
+  g.bc = 1;
+  g.out = F + nc;
+  g.oi = 1;
+  g.oc = N;
+  g.nrows = nbv;
+  g.kb = 0;
+  g.ke = nbv;
+  g.ncols = nc;
+  g.negate = true;
+  rows_gemm_dispatch<G>(g, tl, rows, Ms);
 }
-
-// Three kernels by chunk width, so that narrow chunks are not held to the register count of
-// the widest: group 0 = widths 1..8, group 1 = 12..32, group 2 = 48..64.
-template <int G>
-__global__ void __launch_bounds__(kBcMaxRows) k_si_bc(const Tile *__restrict__ tiles, SiArgs a,
-                                                      int rows) {
-  __shared__ double Ms[kBcK * (G == 0 ? 8 : G == 1 ? 32 : kBcMaxW)];
-  const Tile tl = tiles[blockIdx.x];
-  if (G == 0) {
-    switch (tl.pad) {
-      case 1: si_bc_rows<1>(tl, a, rows, Ms); break;
-      case 2: si_bc_rows<2>(tl, a, rows, Ms); break;
-      case 4: si_bc_rows<4>(tl, a, rows, Ms); break;
-      default: si_bc_rows<8>(tl, a, rows, Ms); break;
-    }
-  } else if (G == 1) {
-    switch (tl.pad) {
-      case 12: si_bc_rows<12>(tl, a, rows, Ms); break;
-      case 16: si_bc_rows<16>(tl, a, rows, Ms); break;
-      case 24: si_bc_rows<24>(tl, a, rows, Ms); break;
-      default: si_bc_rows<32>(tl, a, rows, Ms); break;
-    }
-  } else {
-    if (tl.pad == 48) si_bc_rows<48>(tl, a, rows, Ms); else si_bc_rows<64>(tl, a, rows, Ms);
-  }
-}
-
-inline int bc_width(int32_t cols) {
-  constexpr int kW[] = {1, 2, 4, 8, 12, 16, 24, 32, 48, 64};
-  for (int w : kW)
-    if (cols <= w) return w;
-  return kBcMaxW;
-}
-
-inline int bc_group(int w) { return w <= 8 ? 0 : w <= 32 ? 1 : 2; }
 
 // Sigma[C,C] = Zd^T D^{-1} Zd - M^T Sigma[B,C], lower triangle: tiles (r >= c) of TS x TS over
 // n_c x n_c, TS = 16, 32 or 64 following n_c (Tile.pad); 16 x 16 threads, (TS/16)^2 outputs each.
@@ -740,7 +803,8 @@ struct BlockInvPlan {
   std::vector<int64_t> gsrc;
   std::vector<int32_t> diag_sn, diag_blk;          // phase 1a CTAs (wide supernodes)
   std::vector<int32_t> small_sn, small_chunk;      // phase 1 CTAs of narrow supernodes
-  std::vector<Tile> m_tiles;                       // phase 1b tiles
+  std::vector<Tile> m_tiles;                       // phase 1b tiles, by width group
+  std::vector<int64_t> m_ptr;
   std::vector<Tile> z_tiles;                       // phase 2 tiles, grouped by depth
   std::vector<int64_t> z_ptr;                      // depth d: z_tiles[z_ptr[d] .. z_ptr[d+1])
   std::vector<Tile> n_tiles;                       // phase 2 narrow tiles (n_c <= 32)
@@ -790,6 +854,7 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
   B.m_tiles.clear();
   B.small_sn.clear();
   B.small_chunk.clear();
+  std::vector<int32_t> wide;
   for (int32_t t = 0; t < ns; ++t) {
     const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
     if (nc <= kBlock) {   // one diagonal block: its inverse already exists
@@ -804,9 +869,9 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
         B.diag_sn.push_back(t);
         B.diag_blk.push_back(J * kDiagSlices + sl);
       }
-    for (int32_t r = 0; r * kT < nbv; ++r)
-      for (int32_t c = 0; c * kT < nc; ++c) B.m_tiles.push_back({t, r, c, 0});
+    wide.push_back(t);
   }
+  m_tiles_of(S, wide, B.m_tiles, B.m_ptr);
   // phase 2 tiles by depth: 64 x 64 tiles for wide supernodes, one row per thread for
   // narrow ones (at most 32 columns)
   std::vector<std::vector<Tile>> per(maxd + 1), pern(maxd + 1);
@@ -894,10 +959,9 @@ int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, T
     CUDA_TRY(cudaGetLastError());
   }
   mark();
-  if (!B.m_tiles.empty()) {
-    k_bi_m<<<static_cast<unsigned>(B.m_tiles.size()), kGemmThreads, 0, st>>>(d_mt, a);
-    ++*launches;
-    CUDA_TRY(cudaGetLastError());
+  {
+    const int rc = launch_m_all(d_mt, B.m_ptr, a, st, launches, err);
+    if (rc != PEERS_OK) return rc;
   }
   mark();
   for (size_t d = 0; d + 1 < B.z_ptr.size(); ++d) {
@@ -949,6 +1013,7 @@ struct SelInvPlan {
   std::vector<int64_t> fused_smem;                 // dynamic shared memory per depth
   std::vector<int32_t> small_sn, small_chunk, diag_sn, diag_blk;
   std::vector<Tile> m_tiles;
+  std::vector<int64_t> m_ptr;
   int64_t fma = 0;
 };
 
@@ -993,6 +1058,7 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
     return sn_nc(S, t) <= kBlock && sn_nc(S, t) + S.nb[t] <= kSiSmallN;
   };
   // phase 1 (T^{-1} and M) as in the block inverse, for the supernodes not fused
+  std::vector<int32_t> wide;
   for (int32_t t = 0; t < ns; ++t) {
     const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
     if (fused(t)) continue;
@@ -1008,9 +1074,9 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
         P.diag_sn.push_back(t);
         P.diag_blk.push_back(J * kDiagSlices + sl);
       }
-    for (int32_t r = 0; r * kT < nbv; ++r)
-      for (int32_t c = 0; c * kT < nc; ++c) P.m_tiles.push_back({t, r, c, 0});
+    wide.push_back(t);
   }
+  m_tiles_of(S, wide, P.m_tiles, P.m_ptr);
   // per depth: gathers, tiles, queries
   P.gather_ptr.assign(1, 0);
   P.bc_ptr.assign(1, 0);
@@ -1085,8 +1151,8 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
       const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
       for (int32_t r = 0; r * rows < nbv; ++r)
         for (int32_t c0 = 0; c0 < nc; c0 += wcap) {
-          const int w = bc_width(std::min(wcap, nc - c0));
-          bcg[bc_group(w)].push_back({t, r, c0, w});
+          const int w = rows_width(std::min(wcap, nc - c0));
+          bcg[rows_group(w)].push_back({t, r, c0, w});
         }
     }
     P.bc_rows.push_back(rows);
@@ -1361,10 +1427,7 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
         dsn, dblk, b);
     ++launches;
   }
-  if (!P.m_tiles.empty()) {
-    peers::k_bi_m<<<static_cast<unsigned>(P.m_tiles.size()), peers::kGemmThreads, 0, st>>>(mt, b);
-    ++launches;
-  }
+  RC_TRY(peers::launch_m_all(mt, P.m_ptr, b, st, &launches, err));
   CUDA_TRY(cudaGetLastError());
   std::vector<cudaEvent_t> ev;
   auto mark = [&]() {

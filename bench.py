@@ -54,8 +54,11 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=8000,
                     help="edges per step of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--routes", default="blockinv,selinv",
+                    help="other exact routes to time on the same queries after the walk: a "
+                         "comma list of blockinv, selinv (empty: none)")
     ap.add_argument("--no-blockinv", action="store_true",
-                    help="skip timing the block implicit inverse beside the walk")
+                    help="same as --routes ''")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the largest tiles instead of running the tile autotuner")
     return ap.parse_args()
@@ -288,8 +291,9 @@ def run_ours(args):
 
     sweep_stats = ctx.last_stats()
     # the same queries by the block implicit inverse (the paper's order of work)
+    routes = set() if args.no_blockinv else {r for r in args.routes.split(",") if r}
     blockinv = None
-    if not args.no_blockinv:
+    if "blockinv" in routes:
         cost = P.blockinv_cost(sym)
         Rb = torch.empty(nq, dtype=torch.float64, device=f"cuda:{local}")
         for _ in range(args.warmup):
@@ -312,7 +316,7 @@ def run_ours(args):
         del Rb
     # and from the selected inverse (Sigma on the pattern of L, Takahashi recurrences)
     selinv = None
-    if not args.no_blockinv:
+    if "selinv" in routes:
         fma_si = int(P.load().peers_selinv_fma(sym._h))
         Rs = torch.empty(nq, dtype=torch.float64, device=f"cuda:{local}")
         for _ in range(args.warmup):

@@ -53,6 +53,8 @@ def parse():
                     help="edges in the oracle's CPU-baseline sample (0 = skip)")
     ap.add_argument("--ref-sample", type=int, default=8000,
                     help="edges per step of --impl reference")
+    ap.add_argument("--ref-threads", type=int, default=None,
+                    help="host threads of --impl reference (default: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--routes", default="blockinv,selinv",
                     help="other exact routes to time on the same queries after the walk: a "
@@ -82,9 +84,9 @@ def workload_name(name):
 
 # ------------------------------------------------------------------ CPU oracle (host cores)
 
-def _oracle_sample(workload, sample, steps, warmup, seed, out_q):
+def _oracle_sample(workload, sample, steps, warmup, seed, out_q, threads=None):
     """Runs in a spawned process: factors with the oracle (untimed), then times the per-query
-    path solves on `sample` seeded edges per step, on all host cores."""
+    path solves on `sample` seeded edges per step, on `threads` host cores (default all)."""
     import oracle
     g = make_graph(workload)
     t0 = time.time()
@@ -93,7 +95,7 @@ def _oracle_sample(workload, sample, steps, warmup, seed, out_q):
     u, v = g.all_edges()
     rng = np.random.default_rng(seed)
     idx = rng.choice(u.size, min(sample, u.size), replace=False)
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     times = []
     for i in range(warmup + steps):
         t0 = time.perf_counter()
@@ -104,10 +106,11 @@ def _oracle_sample(workload, sample, steps, warmup, seed, out_q):
     out_q.put({"t_factor_s": t_fact, "times": times, "sample": int(idx.size), "cores": cores})
 
 
-def start_oracle(workload, sample, steps, warmup, seed):
+def start_oracle(workload, sample, steps, warmup, seed, threads=None):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_oracle_sample, args=(workload, sample, steps, warmup, seed, q))
+    p = ctx.Process(target=_oracle_sample,
+                    args=(workload, sample, steps, warmup, seed, q, threads))
     p.start()
     return p, q
 
@@ -206,7 +209,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    p, q = start_oracle(args.workload, args.ref_sample, args.steps, args.warmup, seed=7)
+    p, q = start_oracle(args.workload, args.ref_sample, args.steps, args.warmup, seed=7,
+                        threads=args.ref_threads)
     res = q.get()
     p.join()
     t = sum(res["times"])

@@ -250,9 +250,10 @@ int peers_query_noalloc(peers_ctx *ctx, const peers_symbolic *sym, const peers_n
 /* ---- batched sweep of many graphs -------------------------------------------------------- */
 
 /* Many independent graphs, each with its own plan and factor, swept together: the graphs'
- * level sequences are aligned and the t-th level of every graph becomes one persistent
- * kernel launch (CTAs pull work items of all graphs until the level is done), so G graphs of
- * heights H_g take max_g H_g launches.  With PEERS_BATCH_CUDA_GRAPH the launch sequence is
+ * level sequences are aligned at the top (every graph's root level in the last launch) and
+ * the t-th level from the top of every graph becomes one persistent kernel launch (CTAs pull
+ * work items of all graphs until the level is done), so G graphs of heights H_g take
+ * max_g H_g launches.  With PEERS_BATCH_CUDA_GRAPH the launch sequence is
  * captured into a CUDA graph on the first peers_batch_query and replayed afterwards.  Each
  * graph's results are bit-identical to its own peers_query (an item's arithmetic depends
  * only on its supernode and queries).  The handles must outlive the batch.  This is the

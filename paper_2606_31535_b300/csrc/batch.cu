@@ -2,9 +2,9 @@
 // of them, captured once in a CUDA graph and replayed.
 //
 // Each graph keeps its own plan and factor (peers_analyze / peers_factor).  The batch
-// aligns the graphs' level sequences (wave by wave, level by level, plus the two-branch
-// combine of a wave) and merges the t-th step of every graph into one list of work items,
-// each tagged with its graph's argument block.  A launch covers one merged step, so a batch
+// aligns the graphs' step sequences (wave by wave, level by level, plus the two-branch
+// combine of a wave) at their last step, and merges the t-th step from the end of every
+// graph into one list of work items, each tagged with its graph's argument block.  A launch covers one merged step, so a batch
 // of G graphs of height H needs max_g H_g launches instead of sum_g H_g.  Results are
 // identical to the single-graph sweep bit for bit: an item's arithmetic depends only on its
 // own supernode and queries.
@@ -119,8 +119,12 @@ int build(peers_ctx *ctx, peers_batch *b, std::string &err) {
     step.clear();
     int64_t smem = 0;
     for (int32_t i = 0; i < b->count; ++i) {
-      if (t >= seq[i].size()) continue;
-      const Step &st = seq[i][t];
+      // graphs are aligned at the top: every graph's last step (its roots) runs in the last
+      // launch, so the heavy top levels of all graphs share launches instead of the deepest
+      // graphs' top levels running nearly alone at the end
+      const size_t lead = T - seq[i].size();
+      if (t < lead) continue;
+      const Step &st = seq[i][t - lead];
       const Symbolic &S = b->syms[i]->S;
       if (st.items) {
         for (int64_t k = st.i0; k < st.i1; ++k) {

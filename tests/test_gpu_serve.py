@@ -87,3 +87,23 @@ def test_failing_request_does_not_stop_the_server(P):
     st = sv.stats()
     assert st["completed"] == 1 and st["failed"] == 1
     sv.close()
+
+
+def test_server_analysis_options_keep_results(P):
+    """Options given to the server (here small tile caps and a small carry budget, which split
+    the queries into more items and waves) apply to every request's analysis; column blocks
+    stay aligned, so each result is still bit-identical to the default single sweep."""
+    reqs = requests()[:6]
+    ctx = P.Context(0)
+    ref = [alone(P, ctx, *r)[0] for r in reqs]
+    opt = P.Options()
+    opt.qcap[:] = [4, 8, 2, 16]
+    opt.carry_budget = 8 << 20
+    sv = P.Server(0, workers=2, options=opt)
+    tickets = [sv.submit(g, qu, qv) for g, qu, qv in reqs]
+    for i, t in enumerate(tickets):
+        R, _ = sv.wait(t)
+        assert np.array_equal(R, ref[i]), i
+    st = sv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    sv.close()

@@ -473,24 +473,38 @@ __device__ __forceinline__ void bi_z_narrow(const Tile &tl, const BiArgs &a, dou
   }
 }
 
-// Narrow tiles of one depth; Tile.pad selects the register width (2, 4, 8, 16 or 32 columns).
+// Narrow tiles of one depth; Tile.pad selects the register width.  Two kernels, so that the
+// narrowest chunks are not held to the register count of the widest: group 0 = 1, 2, 4, 8
+// columns, group 1 = 12, 16, 24, 32.
+template <int G>
 __global__ void __launch_bounds__(kNarrowRows) k_bi_z_narrow(const Tile *__restrict__ tiles,
                                                              BiArgs a) {
   extern __shared__ double sm[];
   const Tile tl = tiles[blockIdx.x];
-  switch (tl.pad) {
-    case 2: bi_z_narrow<2>(tl, a, sm); break;
-    case 4: bi_z_narrow<4>(tl, a, sm); break;
-    case 8: bi_z_narrow<8>(tl, a, sm); break;
-    case 16: bi_z_narrow<16>(tl, a, sm); break;
-    default: bi_z_narrow<32>(tl, a, sm); break;
+  if (G == 0) {
+    switch (tl.pad) {
+      case 1: bi_z_narrow<1>(tl, a, sm); break;
+      case 2: bi_z_narrow<2>(tl, a, sm); break;
+      case 4: bi_z_narrow<4>(tl, a, sm); break;
+      default: bi_z_narrow<8>(tl, a, sm); break;
+    }
+  } else {
+    switch (tl.pad) {
+      case 12: bi_z_narrow<12>(tl, a, sm); break;
+      case 16: bi_z_narrow<16>(tl, a, sm); break;
+      case 24: bi_z_narrow<24>(tl, a, sm); break;
+      default: bi_z_narrow<32>(tl, a, sm); break;
+    }
   }
 }
 
 inline int narrow_width(int32_t nc) {
-  return nc <= 2 ? 2 : nc <= 4 ? 4 : nc <= 8 ? 8 : nc <= 16 ? 16 : 32;
+  return nc <= 1 ? 1 : nc <= 2 ? 2 : nc <= 4 ? 4 : nc <= 8 ? 8 : nc <= 12 ? 12
+         : nc <= 16 ? 16 : nc <= 24 ? 24 : 32;
 }
-constexpr size_t kNarrowSmem = size_t(kNarrowK) * 32 * 8 + kNarrowK * 4 + kNarrowK * 8;
+constexpr size_t narrow_smem(int group) {
+  return size_t(kNarrowK) * (group == 0 ? 8 : 32) * 8 + kNarrowK * 4 + kNarrowK * 8;
+}
 
 // ---------------------------------------------------------------- query pass
 
@@ -808,7 +822,7 @@ struct BlockInvPlan {
   std::vector<Tile> z_tiles;                       // phase 2 tiles, grouped by depth
   std::vector<int64_t> z_ptr;                      // depth d: z_tiles[z_ptr[d] .. z_ptr[d+1])
   std::vector<Tile> n_tiles;                       // phase 2 narrow tiles (n_c <= 32)
-  std::vector<int64_t> n_ptr;
+  std::vector<int64_t> n_ptr;                      // 2 width groups per depth
   std::vector<BiQuery> queries;
   int64_t gemm_fma = 0;                            // phase-2 FMAs with the staircase
 };
@@ -874,13 +888,14 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
   m_tiles_of(S, wide, B.m_tiles, B.m_ptr);
   // phase 2 tiles by depth: 64 x 64 tiles for wide supernodes, one row per thread for
   // narrow ones (at most 32 columns)
-  std::vector<std::vector<Tile>> per(maxd + 1), pern(maxd + 1);
+  std::vector<std::vector<Tile>> per(maxd + 1), pern(2 * (maxd + 1));   // pern: 2 groups per depth
   for (int32_t t = 0; t < ns; ++t) {
     const int32_t nc = sn_nc(S, t), lp = B.plen[t] - nc;
     if (lp == 0 || S.nb[t] == 0) continue;
     if (nc <= 32) {
+      const int w = narrow_width(nc);
       for (int32_t r = 0; r * kNarrowRows < lp; ++r)
-        pern[B.depth[t]].push_back({t, r, 0, narrow_width(nc)});
+        pern[2 * B.depth[t] + (w <= 8 ? 0 : 1)].push_back({t, r, 0, w});
     } else {
       for (int32_t r = 0; r * kT < lp; ++r)
         for (int32_t c = 0; c * kT < nc; ++c) per[B.depth[t]].push_back({t, r, c, 0});
@@ -893,8 +908,10 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
   for (int32_t d = 0; d <= maxd; ++d) {
     B.z_tiles.insert(B.z_tiles.end(), per[d].begin(), per[d].end());
     B.z_ptr.push_back(static_cast<int64_t>(B.z_tiles.size()));
-    B.n_tiles.insert(B.n_tiles.end(), pern[d].begin(), pern[d].end());
-    B.n_ptr.push_back(static_cast<int64_t>(B.n_tiles.size()));
+    for (int g = 0; g < 2; ++g) {
+      B.n_tiles.insert(B.n_tiles.end(), pern[2 * d + g].begin(), pern[2 * d + g].end());
+      B.n_ptr.push_back(static_cast<int64_t>(B.n_tiles.size()));
+    }
   }
   // queries: the plan's single-path slots and two-branch pairs
   B.queries.clear();
@@ -966,19 +983,26 @@ int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, T
   mark();
   for (size_t d = 0; d + 1 < B.z_ptr.size(); ++d) {
     const int64_t n = B.z_ptr[d + 1] - B.z_ptr[d];
-    const int64_t nn = B.n_ptr[d + 1] - B.n_ptr[d];
+    const int64_t n0 = B.n_ptr[2 * d + 1] - B.n_ptr[2 * d];
+    const int64_t n1 = B.n_ptr[2 * d + 2] - B.n_ptr[2 * d + 1];
     if (n > 0) {
       k_bi_z<<<static_cast<unsigned>(n), kGemmThreads, 0, st>>>(d_zt + B.z_ptr[d], a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
     }
-    if (nn > 0) {
-      k_bi_z_narrow<<<static_cast<unsigned>(nn), kNarrowRows, kNarrowSmem, st>>>(
-          d_nt + B.n_ptr[d], a);
+    if (n0 > 0) {
+      k_bi_z_narrow<0><<<static_cast<unsigned>(n0), kNarrowRows, narrow_smem(0), st>>>(
+          d_nt + B.n_ptr[2 * d], a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
     }
-    if (n > 0 || nn > 0) mark();
+    if (n1 > 0) {
+      k_bi_z_narrow<1><<<static_cast<unsigned>(n1), kNarrowRows, narrow_smem(1), st>>>(
+          d_nt + B.n_ptr[2 * d + 1], a);
+      ++*launches;
+      CUDA_TRY(cudaGetLastError());
+    }
+    if (n > 0 || n0 > 0 || n1 > 0) mark();
   }
   const int64_t nq = static_cast<int64_t>(B.queries.size());
   if (nq > 0) {

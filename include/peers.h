@@ -154,8 +154,12 @@ void peers_free_numeric(peers_numeric *num);
  * its two columns: R_st = sum_i (Z[i,s] - Z[i,t])^2 / d_i (eq. 12, eq. 18).  Work is about the
  * paper's O(n^alpha nnz(L)) (Thm 4), far below the per-query walk, but device memory holds all
  * of nnz(Z) at once (peers_blockinv_bytes); the call fails with PEERS_ENOMEM when it does not
- * fit.  The device memory is allocated and freed inside the call.  Errors: PEERS_EINVAL,
- * PEERS_ENOMEM, PEERS_ECUDA. */
+ * fit.  The device memory is allocated and freed inside the call.  The host-side plan (block
+ * offsets, tiles, the per-query column list; about 24 bytes per query plus 12 per entry of
+ * the factor's row structure) is built by the first call on `sym` (or by peers_blockinv_bytes
+ * / _fma) and kept with the handle for later calls, until peers_retile or peers_autotune
+ * rebuild the sweep plan or the handle is freed.  Calls on one `sym` from several threads
+ * are safe.  Errors: PEERS_EINVAL, PEERS_ENOMEM, PEERS_ECUDA. */
 int peers_query_blockinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
                          double *R, int flags);
 /* Device bytes peers_query_blockinv needs for this plan. */
@@ -171,8 +175,10 @@ int64_t peers_blockinv_fma(const peers_symbolic *sym);
  * 2 Sigma_uv (eq. 2).  The work is about one factorization, far below both the walk and the
  * block inverse; the memory is two depths of dense inverse fronts.  The paper does not use it
  * (§II-C); it is an independent second route to the same numbers.  A plan with listed pairs
- * outside the pattern is rejected with PEERS_EINVAL (use peers_query).  Errors: PEERS_EINVAL,
- * PEERS_ENOMEM, PEERS_ECUDA. */
+ * outside the pattern is rejected with PEERS_EINVAL (use peers_query).  Device memory is
+ * allocated and freed inside the call; the host-side plan is kept with `sym` after the first
+ * call, as for peers_query_blockinv (rebuilt for a device with another SM count).  Errors:
+ * PEERS_EINVAL, PEERS_ENOMEM, PEERS_ECUDA. */
 int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
                        double *R, int flags);
 /* FMAs of the selected inversion for this plan. */

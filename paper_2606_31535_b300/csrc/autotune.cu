@@ -235,6 +235,7 @@ int peers_retile(peers_ctx *ctx, peers_symbolic *sym, peers_numeric *num, const 
   if (!ctx || !sym || !num || !qcap) return peers_fail(PEERS_EINVAL, "null argument");
   if (num->sym != sym) return peers_fail(PEERS_EINVAL, "numeric handle belongs to another plan");
   std::string err;
+  forget_route_plans(sym);
   int rc = peers::build_sweep_plan(sym->S, qcap, err);
   if (rc == PEERS_OK) rc = refresh_tiles(ctx, sym->S, num, err);
   return rc == PEERS_OK ? rc : peers_fail(rc, err);
@@ -247,6 +248,7 @@ int peers_autotune(peers_ctx *ctx, peers_symbolic *sym, peers_numeric *num,
   int32_t caps[4];
   double gain[4];
   std::string err;
+  forget_route_plans(sym);
   int rc = tune(ctx, sym, num, cache_path, caps, gain, err);
   if (rc != PEERS_OK) return peers_fail(rc, err);
   for (int c = 0; c < 4; ++c) {

@@ -1193,6 +1193,35 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
   return PEERS_OK;
 }
 
+// The route plans of a symbolic handle, built on first use and kept with it (the selected
+// inversion's plan also depends on the device's SM count, so it is rebuilt for another one).
+int cached_blockinv_plan(const peers_symbolic *sym, std::shared_ptr<const BlockInvPlan> &out,
+                         std::string &err) {
+  std::lock_guard<std::mutex> lock(sym->route_mu);
+  if (!sym->blockinv_plan) {
+    auto p = std::make_shared<BlockInvPlan>();
+    const int rc = blockinv_plan(sym->S, *p, err);
+    if (rc != PEERS_OK) return rc;
+    sym->blockinv_plan = p;
+  }
+  out = std::static_pointer_cast<const BlockInvPlan>(sym->blockinv_plan);
+  return PEERS_OK;
+}
+
+int cached_selinv_plan(const peers_symbolic *sym, int sms, std::shared_ptr<const SelInvPlan> &out,
+                       std::string &err) {
+  std::lock_guard<std::mutex> lock(sym->route_mu);
+  if (!sym->selinv_plan || (sms > 0 && sym->selinv_sms != sms)) {
+    auto p = std::make_shared<SelInvPlan>();
+    const int rc = selinv_plan(sym->S, *p, sms > 0 ? sms : 148, err);
+    if (rc != PEERS_OK) return rc;
+    sym->selinv_plan = p;
+    sym->selinv_sms = sms > 0 ? sms : 148;
+  }
+  out = std::static_pointer_cast<const SelInvPlan>(sym->selinv_plan);
+  return PEERS_OK;
+}
+
 }  // namespace peers
 
 // ---------------------------------------------------------------- C ABI
@@ -1204,9 +1233,10 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   const Symbolic &S = sym->S;
   cudaStream_t st = ctx->stream;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  peers::BlockInvPlan B;
-  int rc = peers::blockinv_plan(S, B, err);
+  std::shared_ptr<const peers::BlockInvPlan> plan;
+  int rc = peers::cached_blockinv_plan(sym, plan, err);
   if (rc != PEERS_OK) return rc;
+  const peers::BlockInvPlan &B = *plan;
   std::vector<void *> mem;
   auto cleanup = [&]() {
     for (void *p : mem) cudaFree(p);
@@ -1385,10 +1415,11 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   const Symbolic &S = sym->S;
   cudaStream_t st = ctx->stream;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  peers::SelInvPlan P;
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  RC_TRY(peers::selinv_plan(S, P, sms, err));
+  std::shared_ptr<const peers::SelInvPlan> plan;
+  RC_TRY(peers::cached_selinv_plan(sym, sms, plan, err));
+  const peers::SelInvPlan &P = *plan;
   DevMem mem(&err);
   double *Zd, *M, *F0, *F1, *Rdev = R;
   int32_t *ncs, *gsn, *ssn, *sch, *dsn, *dblk;
@@ -1571,9 +1602,10 @@ extern "C" {
 
 int64_t peers_blockinv_bytes(const peers_symbolic *sym) {
   if (!sym) return -1;
-  peers::BlockInvPlan B;
+  std::shared_ptr<const peers::BlockInvPlan> plan;
   std::string err;
-  if (peers::blockinv_plan(sym->S, B, err) != PEERS_OK) return -1;
+  if (peers::cached_blockinv_plan(sym, plan, err) != PEERS_OK) return -1;
+  const peers::BlockInvPlan &B = *plan;
   return 8 * (B.ztotal + B.mtotal) + 12 * static_cast<int64_t>(B.gstart.size()) +
          16 * static_cast<int64_t>(B.z_tiles.size() + B.n_tiles.size() + B.m_tiles.size()) +
          24 * static_cast<int64_t>(B.queries.size());
@@ -1581,10 +1613,10 @@ int64_t peers_blockinv_bytes(const peers_symbolic *sym) {
 
 int64_t peers_blockinv_fma(const peers_symbolic *sym) {
   if (!sym) return -1;
-  peers::BlockInvPlan B;
+  std::shared_ptr<const peers::BlockInvPlan> plan;
   std::string err;
-  if (peers::blockinv_plan(sym->S, B, err) != PEERS_OK) return -1;
-  return B.gemm_fma;
+  if (peers::cached_blockinv_plan(sym, plan, err) != PEERS_OK) return -1;
+  return plan->gemm_fma;
 }
 
 int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
@@ -1598,10 +1630,11 @@ int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_nu
 
 int64_t peers_selinv_fma(const peers_symbolic *sym) {
   if (!sym) return -1;
-  peers::SelInvPlan P;
+  // the work does not depend on the SM count: any cached plan (or one for 148 SMs) serves
+  std::shared_ptr<const peers::SelInvPlan> plan;
   std::string err;
-  if (peers::selinv_plan(sym->S, P, 148, err) != PEERS_OK) return -1;   // work does not depend on it
-  return P.fma;
+  if (peers::cached_selinv_plan(sym, 0, plan, err) != PEERS_OK) return -1;
+  return plan->fma;
 }
 
 int peers_query_blockinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,

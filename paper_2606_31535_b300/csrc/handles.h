@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "device.cuh"
@@ -23,7 +25,20 @@ struct peers_ctx {
 
 struct peers_symbolic {
   Symbolic S;
+  // Host plans of the block-inverse and selected-inversion routes, built by their first call
+  // and reused by later ones (blockinv.cu).  They read the query slots, which a rebuild of the
+  // sweep plan rewrites, so peers_retile and peers_autotune drop them (forget_route_plans).
+  mutable std::mutex route_mu;
+  mutable std::shared_ptr<const void> blockinv_plan, selinv_plan;
+  mutable int selinv_sms = 0;
 };
+
+inline void forget_route_plans(peers_symbolic *sym) {
+  std::lock_guard<std::mutex> lock(sym->route_mu);
+  sym->blockinv_plan.reset();
+  sym->selinv_plan.reset();
+  sym->selinv_sms = 0;
+}
 
 struct peers_numeric {
   int device = 0;

@@ -303,3 +303,30 @@ def test_fp64_peaks_are_measured(P, ctx):
     pk = ctx.fp64_peaks()
     for key in ("dfma", "dmma", "dfma_with_dmma"):
         assert 0.2 < pk[key] < 5.0, pk
+
+
+def test_route_plans_survive_retile(P, ctx, oracle_mod):
+    """The block-inverse and selected-inversion plans are kept with the symbolic handle after
+    their first call.  Retiling rewrites the query slots they read, so it drops them; calls
+    after a retile must give the same results as before it, and both match the oracle."""
+    g = I.pdn3(side=25, seed=71)
+    sym = P.Symbolic.of(g)
+    num = P.Numeric(ctx, sym)
+    Rb1, Rs1 = P.query_blockinv(ctx, sym, num), P.query_selinv(ctx, sym, num)
+    Rb1b, Rs1b = P.query_blockinv(ctx, sym, num), P.query_selinv(ctx, sym, num)
+    assert np.array_equal(Rb1, Rb1b) and np.array_equal(Rs1, Rs1b)
+    P.retile(ctx, sym, num, [2, 4, 1, 8])
+    Rb2, Rs2 = P.query_blockinv(ctx, sym, num), P.query_selinv(ctx, sym, num)
+    assert np.array_equal(Rb1, Rb2) and np.array_equal(Rs1, Rs2)
+    u, v = g.all_edges()
+    Ro = oracle_mod.resistance(g, u, v)
+    assert maxrel(Rb2, Ro) <= TOL and maxrel(Rs2, Ro) <= TOL
+    # listed pairs (two-branch slots, rewritten by the retile) through the block inverse
+    pu, pv = I.random_pairs(g.n, 300, seed=72)
+    sym2 = P.Symbolic.of(g, 0, pu, pv)
+    num2 = P.Numeric(ctx, sym2)
+    Rp1 = P.query_blockinv(ctx, sym2, num2)
+    P.retile(ctx, sym2, num2, [1, 2, 2, 2])
+    Rp2 = P.query_blockinv(ctx, sym2, num2)
+    assert np.array_equal(Rp1, Rp2)
+    assert maxrel(Rp2, oracle_mod.resistance(g, pu, pv)) <= TOL

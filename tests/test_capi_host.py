@@ -178,3 +178,35 @@ def test_wave_budget_option(P):
     big = P.Symbolic.of(g)
     assert small.footprint_bytes() < big.footprint_bytes()
     assert small.info()["walk_entries"] == big.info()["walk_entries"]
+
+
+def test_route_plan_costs_concurrent_and_cached(P):
+    """The block-inverse and selected-inversion plans are built once per symbolic handle and
+    shared; cost queries from several host threads at once (ctypes releases the GIL) must all
+    see the same numbers as a fresh handle, built or cached."""
+    import threading
+    g = I.pdn3(side=65, seed=91)
+    lib = P.load()
+    a, b = P.Symbolic.of(g), P.Symbolic.of(g)   # keep the handles alive across the calls
+    fresh = [(lib.peers_blockinv_fma(a._h), lib.peers_selinv_fma(b._h))]
+    sym = P.Symbolic.of(g)
+    out, errs = [], []
+
+    def worker():
+        try:
+            for _ in range(3):
+                out.append((lib.peers_blockinv_fma(sym._h), lib.peers_selinv_fma(sym._h),
+                            lib.peers_blockinv_bytes(sym._h)))
+        except Exception as e:   # pragma: no cover - reported below
+            errs.append(e)
+
+    threads = [threading.Thread(target=worker) for _ in range(6)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errs
+    assert len(out) == 18
+    assert all(o[:2] == fresh[0] for o in out)
+    assert len({o[2] for o in out}) == 1 and out[0][2] > 0
+    assert fresh[0][0] > 0 and fresh[0][1] > 0

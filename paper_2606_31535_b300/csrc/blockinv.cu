@@ -336,35 +336,34 @@ int launch_m_all(const Tile *d_tiles, const std::vector<int64_t> &ptr, const BiA
   return rc;
 }
 
-// Phase 2: Z[P_par, C_t] = -Z[P_par, B_t] * M_t for the supernodes of one depth.  Row tile r
-// covers rows [64 r, 64 r + 64) of P_par; only the columns of B_t whose staircase starts
-// above the tile's last row contribute (a prefix of B_t, found by binary search).
-__global__ void __launch_bounds__(kGemmThreads) k_bi_z(const Tile *__restrict__ tiles, BiArgs a) {
-  __shared__ double As[kK][kT];
-  __shared__ double Bs[kK][kT];
-  __shared__ int32_t kend_s;
-  const Tile tl = tiles[blockIdx.x];
+// Phase 2: Z[P_par, C_t] = -Z[P_par, B_t] * M_t for the supernodes of one depth, in tiles of
+// TS x TS (TS = 16, 32 or 64 in Tile.pad, chosen per depth so that the launch has enough
+// CTAs).  Row tile r covers rows [TS r, TS r + TS) of P_par; only the columns of B_t whose
+// staircase starts above the tile's last row contribute (a prefix of B_t, found by binary
+// search).  Every output sums over k in increasing order whatever TS is.
+template <int TS>
+__device__ __forceinline__ void bi_z_tile(const Tile &tl, const BiArgs &a, double *As, double *Bs,
+                                          int32_t *sst, int64_t *ssrc, int32_t *kend_s) {
+  constexpr int U = TS / 16;
   const int32_t t = tl.t;
   const int32_t nc = a.first[t + 1] - a.first[t], nbv = a.nb[t];
   const int32_t ldt = a.plen[t], lp = ldt - nc;   // |P_par|
-  const int R0 = tl.r * kT, C0 = tl.c * kT;
+  const int R0 = tl.r * TS, C0 = tl.c * TS;
   const int32_t *gs = a.gstart + a.rows_off[t];
   const int64_t *gsrc = a.gsrc + a.rows_off[t];
-  if (threadIdx.x == 0) {   // first B_t column whose staircase starts at or below row R0+64
+  if (threadIdx.x == 0) {   // first B_t column whose staircase starts at or below row R0+TS
     int lo = 0, hi = nbv;
     while (lo < hi) {
       const int mid = (lo + hi) / 2;
-      if (gs[mid] < R0 + kT) lo = mid + 1; else hi = mid;
+      if (gs[mid] < R0 + TS) lo = mid + 1; else hi = mid;
     }
-    kend_s = lo;
+    *kend_s = lo;
   }
   __syncthreads();
-  const int32_t kend = kend_s;
+  const int32_t kend = *kend_s;
   const double *Mt = a.M + a.moff[t];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  __shared__ int32_t sst[kK];
-  __shared__ int64_t ssrc[kK];
-  double acc[4][4] = {};
+  double acc[U][U] = {};
   for (int k0 = 0; k0 < kend; k0 += kK) {
     if (threadIdx.x < kK) {
       const int kk = k0 + threadIdx.x;
@@ -372,8 +371,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_bi_z(const Tile *__restrict__ 
       ssrc[threadIdx.x] = kk < kend ? gsrc[kk] : 0;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kK * kT; e += kGemmThreads) {
-      const int k = e / kT, r = e % kT;
+    for (int e = threadIdx.x; e < kK * TS; e += kGemmThreads) {
+      const int k = e / TS, r = e - (e / TS) * TS;
       const int kk = k0 + k;
       double g = 0.0, m = 0.0;
       if (kk < kend) {
@@ -382,32 +381,46 @@ __global__ void __launch_bounds__(kGemmThreads) k_bi_z(const Tile *__restrict__ 
         if (row < lp && row >= st) g = a.Z[ssrc[k] + (row - st)];
         if (C0 + r < nc) m = Mt[int64_t(kk) * nc + C0 + r];
       }
-      As[k][r] = g;
-      Bs[k][r] = m;
+      As[k * TS + r] = g;
+      Bs[k * TS + r] = m;
     }
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < kK; ++k) {
-      double av[4], bv[4];
+      double av[U], bv[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { av[u] = As[k][tx + 16 * u]; bv[u] = Bs[k][ty + 16 * u]; }
+      for (int u = 0; u < U; ++u) { av[u] = As[k * TS + tx + 16 * u]; bv[u] = Bs[k * TS + ty + 16 * u]; }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
     }
     __syncthreads();
   }
   double *Zt = a.Z + a.zoff[t];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < U; ++v) {
     const int j = C0 + ty + 16 * v;
     if (j >= nc) continue;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int i = R0 + tx + 16 * u;
       if (i < lp) Zt[int64_t(j) * ldt + nc + i] = -acc[u][v];
     }
+  }
+}
+
+__global__ void __launch_bounds__(kGemmThreads) k_bi_z(const Tile *__restrict__ tiles, BiArgs a) {
+  __shared__ double As[kK * kT];
+  __shared__ double Bs[kK * kT];
+  __shared__ int32_t sst[kK];
+  __shared__ int64_t ssrc[kK];
+  __shared__ int32_t kend_s;
+  const Tile tl = tiles[blockIdx.x];
+  switch (tl.pad) {
+    case 16: bi_z_tile<16>(tl, a, As, Bs, sst, ssrc, &kend_s); break;
+    case 32: bi_z_tile<32>(tl, a, As, Bs, sst, ssrc, &kend_s); break;
+    default: bi_z_tile<kT>(tl, a, As, Bs, sst, ssrc, &kend_s); break;
   }
 }
 
@@ -886,9 +899,10 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
     wide.push_back(t);
   }
   m_tiles_of(S, wide, B.m_tiles, B.m_ptr);
-  // phase 2 tiles by depth: 64 x 64 tiles for wide supernodes, one row per thread for
-  // narrow ones (at most 32 columns)
+  // phase 2 tiles by depth: square tiles for wide supernodes, one row per thread for narrow
+  // ones (at most 32 columns)
   std::vector<std::vector<Tile>> per(maxd + 1), pern(2 * (maxd + 1));   // pern: 2 groups per depth
+  std::vector<std::vector<int32_t>> wide_by_depth(maxd + 1);
   for (int32_t t = 0; t < ns; ++t) {
     const int32_t nc = sn_nc(S, t), lp = B.plen[t] - nc;
     if (lp == 0 || S.nb[t] == 0) continue;
@@ -897,8 +911,24 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
       for (int32_t r = 0; r * kNarrowRows < lp; ++r)
         pern[2 * B.depth[t] + (w <= 8 ? 0 : 1)].push_back({t, r, 0, w});
     } else {
-      for (int32_t r = 0; r * kT < lp; ++r)
-        for (int32_t c = 0; c * kT < nc; ++c) per[B.depth[t]].push_back({t, r, c, 0});
+      wide_by_depth[B.depth[t]].push_back(t);
+    }
+  }
+  // wide tiles: per depth, the largest tile (64, 32, 16) that still gives the launch at least
+  // 16 CTAs per SM of a 148-SM B300 (few large tiles leave most SMs idle at the top levels)
+  constexpr int64_t kTargetCtas = 148 * 16;
+  for (int32_t d = 0; d <= maxd; ++d) {
+    int ts = kT;
+    for (; ts > 16; ts /= 2) {
+      int64_t ctas = 0;
+      for (int32_t t : wide_by_depth[d])
+        ctas += int64_t((B.plen[t] - sn_nc(S, t) + ts - 1) / ts) * ((sn_nc(S, t) + ts - 1) / ts);
+      if (ctas >= kTargetCtas) break;
+    }
+    for (int32_t t : wide_by_depth[d]) {
+      const int32_t nc = sn_nc(S, t), lp = B.plen[t] - nc;
+      for (int32_t r = 0; r * ts < lp; ++r)
+        for (int32_t c = 0; c * ts < nc; ++c) per[d].push_back({t, r, c, ts});
     }
   }
   B.z_tiles.clear();

@@ -164,20 +164,27 @@ def stop_clocks(p, f):
             "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def k_sweep_source_sha(text):
+    """Hash of the k_sweep kernel source: sweep.cu from kSweepThreads through the end of
+    k_sweep_multi (the device code the DRAM counters were taken on; host helpers excluded)."""
+    import hashlib
+    a = text.index("constexpr int kSweepThreads")
+    b = text.index("\n}\n", text.index("k_sweep_multi(const SweepItem")) + 3
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
+
+
 def profiled_traffic(workload):
     """DRAM bytes per k_sweep launch from the committed ncu capture of this workload, or None
     when there is none or the kernel source has changed since it was taken."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "k_sweep_dram_%s.json" % workload)
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        with open(os.path.join(ROOT, "paper_2606_31535_b300", "csrc", "sweep.cu"), "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+        with open(os.path.join(ROOT, "paper_2606_31535_b300", "csrc", "sweep.cu")) as fh:
+            sha = k_sweep_source_sha(fh.read())
     except (OSError, ValueError):
         return None
-    return rec["dram_bytes_per_launch"] if rec.get("sweep_cu_sha256_16") == sha else None
-
+    return rec["dram_bytes_per_launch"] if rec.get("k_sweep_source_sha256_16") == sha else None
 
 def tuning_cache():
     """Tile-autotuner cache file: $PEERS_TUNING_CACHE, else one in the system temp dir."""

@@ -1543,9 +1543,9 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   {
     int64_t need = 0;
     for (int64_t x : P.fused_smem) need = std::max(need, x);
-    if (need > 48 * 1024)
-      CUDA_TRY(cudaFuncSetAttribute(peers::k_si_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(need)));
+    static int si_small_smem[64] = {};   // limit set so far, per device
+    RC_TRY(peers::raise_smem_limit(reinterpret_cast<const void *>(peers::k_si_small),
+                                   si_small_smem, need, err));
   }
   peers::SiSmallArgs sb{};
   sb.panel = num->panel;

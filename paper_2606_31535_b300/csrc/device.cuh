@@ -86,6 +86,9 @@ int run_multi_step(const SweepItem *items, int64_t nitems, const SweepArgs *tabl
 // Grid of a persistent multi-graph launch (CTAs that fit the GPU at once, at most nitems);
 // also raises the kernel's dynamic shared-memory limit to smem.  Call outside stream capture.
 int multi_step_grid(int64_t smem, int64_t nitems, int64_t *grid, std::string &err);
+// Raises `kernel`'s dynamic shared-memory limit on the current device to at least `bytes`;
+// `configured` holds the limit set so far per device (64 entries).  Thread-safe (sweep.cu).
+int raise_smem_limit(const void *kernel, int *configured, int64_t bytes, std::string &err);
 
 // The sweep with its scratch in the library's static device array (sweep_static.cu); no
 // device memory is allocated or freed.  R is a device array of S.nq doubles.

@@ -21,6 +21,8 @@
 // The path is FP64 arithmetic bound (about 2 flops per 8-byte panel entry per query).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -221,22 +223,31 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_multi(const SweepItem *
   }
 }
 
-// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`
-// (the limit only ever grows, so launches configured earlier stay valid).
-template <class K>
-int ensure_smem(K kernel, int *configured, int64_t bytes, std::string &err) {
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`.
+// The limit only ever grows, so launches configured earlier stay valid; the check and the
+// raise happen under one lock, so a thread needing less can never lower the limit after a
+// thread needing more has raised it (sweeps may run from several host threads).
+std::mutex g_smem_lock;
+
+int raise_smem_limit(const void *kernel, int *configured, int64_t bytes, std::string &err) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) {
     err = "device index out of range";
     return PEERS_EINVAL;
   }
+  std::lock_guard<std::mutex> lock(g_smem_lock);
   if (bytes > configured[dev]) {
     CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(bytes)));
     configured[dev] = static_cast<int>(bytes);
   }
   return PEERS_OK;
+}
+
+template <class K>
+int ensure_smem(K kernel, int *configured, int64_t bytes, std::string &err) {
+  return raise_smem_limit(reinterpret_cast<const void *>(kernel), configured, bytes, err);
 }
 int g_sweep_smem[64] = {};
 int g_multi_smem[64] = {};

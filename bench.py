@@ -53,9 +53,13 @@ def parse():
     ap.add_argument("--workload", default="pdn1m",
                     choices=["pdn1m", "grid32", "grid512", "batch256", "serve"])
     ap.add_argument("--requests", type=int, default=80,
-                    help="serve workload: requests in the stream (the full stream is 500)")
-    ap.add_argument("--rho", default="0.9",
-                    help="serve workload: offered loads, comma separated (e.g. 0.5,0.9,1.5)")
+                    help="serving stream: requests in the stream (the full stream is 500)")
+    ap.add_argument("--rho", default="0.7,1.3",
+                    help="serving stream: offered loads as fractions of the GPU's one-at-a-time "
+                         "service rate, comma separated")
+    ap.add_argument("--extras", default="batch,serve",
+                    help="with the default workload at N=1, also measure the 256-graph batch "
+                         "and the serving stream (comma list of batch, serve; empty: neither)")
     ap.add_argument("--cpu-sample", type=int, default=16000,
                     help="edges in the oracle's CPU-baseline sample (0 = skip)")
     ap.add_argument("--ref-sample", type=int, default=8000,
@@ -271,6 +275,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = P.Context(local, stream)
     peaks64 = ctx.fp64_peaks()
+    shapes64 = ctx.fp64_mma_shapes()
     fp64_peak = peaks64["dfma"]
     num = P.Numeric(ctx, sym)
     nq = sym.nq
@@ -375,6 +380,18 @@ def run_ours(args):
     t_e2e = dist_max(max(e2e_times), dist, f"cuda:{local}")
     # the e2e result must equal the device-resident result
     same = bool(np.array_equal(r_pin.numpy(), R.cpu().numpy()))
+    del R
+    # the other two patterns of the path on the same GPU (one replica only: they are
+    # measured once, not per rank)
+    extras = {x for x in args.extras.split(",") if x} if (world == 1 and
+                                                         args.workload == "pdn1m") else set()
+    batch256 = serve = None
+    if "batch" in extras:
+        torch.cuda.empty_cache()
+        batch256 = measure_batch(args, ctx, stream, fp64_peak)
+    if "serve" in extras:
+        torch.cuda.empty_cache()
+        serve = measure_serve(args, ctx, tiles["qcap"] if tiles else None)
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
@@ -395,8 +412,13 @@ def run_ours(args):
                      "traffic": profiled_traffic(args.workload),
                      "traffic_note": "DRAM bytes per k_sweep launch (ncu, profiles/)",
                      "kernel": "k_sweep (FP64 DFMA; peak = DFMA throughput measured live; "
-                               "mma.sync f64 measured %.3f TFLOP/s, both at once %.3f)"
-                               % (peaks64["dmma"], peaks64["dfma_with_dmma"]),
+                               "mma.sync f64 m8n8k4 %.3f, m16n8k4 %.3f, m16n8k8 %.3f, "
+                               "m16n8k16 %.3f TFLOP/s, DFMA and m8n8k4 at once %.3f)"
+                               % (shapes64["m8n8k4"], shapes64["m16n8k4"], shapes64["m16n8k8"],
+                                  shapes64["m16n8k16"], peaks64["dfma_with_dmma"]),
+                     "fp64_tflops": {"dfma": fp64_peak, **{"mma_" + k: v
+                                                           for k, v in shapes64.items()},
+                                     "dfma_with_mma_m8n8k4": peaks64["dfma_with_dmma"]},
                      "algorithmic": "2 flops x W walk entries per step, W = %d" % info["walk_entries"]},
         "hbm_walk": {"achieved_gbs": walk_gbs, "peak_gbs": hbm or HBM_FALLBACK_GBS,
                      "frac": walk_gbs / (hbm or HBM_FALLBACK_GBS),
@@ -405,12 +427,18 @@ def run_ours(args):
         "e2e": {"value": job_throughput(nq, world, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "includes": "factor + sweep",
-                "matches_device_result": same},
+                "matches_device_result": same,
+                "e2e_with_analyze": {"value": job_throughput(nq, world, t_e2e + t_analyze),
+                                     "unit": UNIT, "t_analyze_s": t_analyze,
+                                     "includes": "host analysis (peers_analyze) + factor + "
+                                                 "sweep"}},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "tiles": tiles,
         "next1_blockinv": blockinv,
         "next2_selinv": selinv,
+        "batch256": batch256,
+        "serve": serve,
         "analysis": {"t_analyze_s": t_analyze, "nsuper": info["nsuper"],
                      "levels": info["levels"], "nnz_l": info["nnz_l"],
                      "walk_fma": info["walk_fma"]},
@@ -434,9 +462,10 @@ def run_ours(args):
 
 # ------------------------------------------------------------------ batched graphs
 
-def run_batch(args):
+def measure_batch(args, ctx, stream, dfma_peak, tiles_cache=True):
     """256 independent graphs swept together (one persistent launch per aligned level, CUDA
-    graph replay), against the same graphs swept one at a time on the same GPU."""
+    graph replay), against the same graphs swept one at a time on the same GPU.  Returns the
+    measurement as a dict (the `batch256` object of the default line)."""
     import torch
     from paper_2606_31535_b300 import inputs as I
     from paper_2606_31535_b300 import peers as P
@@ -447,17 +476,13 @@ def run_batch(args):
     t0 = time.time()
     syms = [P.Symbolic.of(g) for g in graphs]
     t_analyze = time.time() - t0
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
-    ctx = P.Context(0, stream)
-    peaks64 = ctx.fp64_peaks()
     t0 = time.time()
     nums = [P.Numeric(ctx, s) for s in syms]
     torch.cuda.synchronize()
     t_factor = time.time() - t0
     tiles = None
     if not args.no_autotune:
-        # tune on the largest graph, then tile every plan with the same caps
+        # tune on the largest graph (cached per GPU and size class), then tile every plan alike
         big = max(range(len(syms)), key=lambda i: syms[i].info()["walk_entries"])
         tiles = P.autotune(ctx, syms[big], nums[big], tuning_cache())
         for s, m in zip(syms, nums):
@@ -515,32 +540,56 @@ def run_batch(args):
     b2.close()
     for m in nums2:
         m.close()
+    same_e2e = all(bool(np.array_equal(h, r.cpu().numpy())) for h, r in zip(hosts, ref))
+    batch.close()
+    for m in nums:
+        m.close()
+    del outs, ref
 
     achieved_tf = 2.0 * W / t_batch / 1e12
-    line = {
-        "metric": "edge queries/s, batched all-edge sweep of 256 graphs (FP64)",
-        "value": nq / t_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name("batch256"), "graphs": len(graphs),
-                   "nodes": int(sum(g.n for g in graphs)), "edges": nq,
-                   "l2": "inputs larger than L2: %.2f GB of factors and fronts"
-                         % (1e-9 * binfo["device_bytes"])},
+    return {
+        "workload": workload_name("batch256"), "graphs": len(graphs),
+        "nodes": int(sum(g.n for g in graphs)), "edges": nq,
+        "value": nq / t_batch, "unit": UNIT, "ms_per_step": 1e3 * t_batch,
+        "steps": args.steps, "warmup": args.warmup,
         "one_at_a_time": {"value": nq / t_single, "ms_per_step": 1e3 * t_single,
-                          "launches": levels, "same_results": same},
-        "batched": {"launches": binfo["launches"], "items": binfo["items"],
-                    "cuda_graph": True},
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peaks64["dfma"],
-                     "unit": "TFLOP/s", "frac": achieved_tf / peaks64["dfma"], "traffic": None,
-                     "kernel": "k_sweep_multi"},
+                          "launches": levels},
+        "speedup_vs_one_at_a_time": t_single / t_batch,
+        "same_results": same,
+        "batched": {"launches": binfo["launches"], "items": binfo["items"], "cuda_graph": True},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": dfma_peak,
+                     "unit": "TFLOP/s", "frac": achieved_tf / dfma_peak,
+                     "kernel": "k_sweep_multi (2 flops x W walk entries per step, W = %d)" % W},
         "e2e": {"value": nq / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "includes": "factor all 256 + batched sweep"},
+                "d2h_bytes_per_step": int(d2h), "includes": "factor all 256 + batched sweep",
+                "matches_device_result": same_e2e},
         "gpu_launches": int(binfo["launches"] * args.steps),
         "clocks": clocks,
         "tiles": tiles,
+        "l2": "inputs larger than L2: %.2f GB of factors and fronts" % (1e-9 * binfo["device_bytes"]),
         "analysis": {"t_generate_s": t_gen, "t_analyze_s": t_analyze, "t_factor_s": t_factor,
                      "walk_entries": W},
     }
+
+
+def run_batch(args):
+    import torch
+    from paper_2606_31535_b300 import peers as P
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = P.Context(0, stream)
+    res = measure_batch(args, ctx, stream, ctx.fp64_peaks()["dfma"])
+    line = {
+        "metric": "edge queries/s, batched all-edge sweep of 256 graphs (FP64)",
+        "value": res["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": res["workload"], "graphs": res["graphs"], "nodes": res["nodes"],
+                   "edges": res["edges"], "l2": res["l2"]},
+    }
+    line.update({k: res[k] for k in ("one_at_a_time", "speedup_vs_one_at_a_time",
+                                     "same_results", "batched", "roofline", "e2e",
+                                     "gpu_launches", "clocks", "tiles", "analysis")})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -596,35 +645,53 @@ def _replay_plain(P, ctx, reqs, arrivals):
     return np.array(lat), nq / wall
 
 
-def run_serve(args):
-    import torch
+def _lat(lat, qps, extra=None):
+    d = {"qps": qps, "p50_s": float(np.percentile(lat, 50)),
+         "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+         "max_s": float(lat.max())}
+    d.update(extra or {})
+    return d
+
+
+def measure_serve(args, ctx, qcap=None):
+    """The serving stream (Poisson arrivals of graph + query-set requests) at the offered
+    loads of --rho, served three ways on the same GPU: the server with continuous batching,
+    the same server admitting one request at a time, and the plain API one request at a time
+    in arrival order.  The load is a fraction of the GPU's one-at-a-time service rate: rho =
+    arrival rate x mean device seconds of a request's factorization + sweep, measured first,
+    request by request, with the library's own CUDA-event timing.  Returns a dict (the
+    `serve` object of the default line)."""
     from paper_2606_31535_b300 import inputs as I
     from paper_2606_31535_b300 import peers as P
 
     t0 = time.time()
     reqs = [I.serve_request(i) for i in range(args.requests)]
     t_gen = time.time() - t0
-    torch.cuda.set_device(0)
-    ctx = P.Context(0)
-    # t_single: the plain API on a few requests, one at a time
-    sample = reqs[:min(8, len(reqs))]
-    t0 = time.perf_counter()
-    for g, qu, qv in sample:
-        sym = P.Symbolic.of(g, 0, qu, qv)
-        P.query(ctx, sym, P.Numeric(ctx, sym))
-    t_single = (time.perf_counter() - t0) / len(sample)
-    workers = max(2, min(8, (os.cpu_count() or 4) // 2))
     opt = None
-    if not args.no_autotune:
-        g0, qu0, qv0 = max(reqs, key=lambda r: r[0].n)
-        s0 = P.Symbolic.of(g0, 0, qu0, qv0)
-        caps = P.autotune(ctx, s0, P.Numeric(ctx, s0), tuning_cache())["qcap"]
+    if qcap is not None:
         opt = P.Options()
-        opt.qcap[:] = caps
-    nq_total = sum((g.m if qu is None else qu.size) for g, qu, qv in reqs)
+        opt.qcap[:] = list(qcap)
+    # calibration: every request alone, device time of its factorization and sweep
+    ctx.set_timing(True)
+    gpu_s, host_s, nq_total = [], [], 0
+    for g, qu, qv in reqs:
+        t0 = time.perf_counter()
+        sym = P.Symbolic.of(g, 0, qu, qv, options=opt)
+        host_s.append(time.perf_counter() - t0)
+        num = P.Numeric(ctx, sym)
+        f_s = ctx.last_stats()["factor_s"]
+        P.query(ctx, sym, num)
+        gpu_s.append(f_s + ctx.last_stats()["sweep_s"])
+        nq_total += sym.nq
+        num.close()
+        sym.close()
+    ctx.set_timing(False)
+    mean_gpu = float(np.mean(gpu_s))
+    workers = max(2, min(8, (os.cpu_count() or 4) // 2))
     loads = []
-    for rho in [float(x) for x in args.rho.split(",")]:
-        arrivals = I.poisson_arrivals(len(reqs), rho / t_single, seed=4)
+    for rho in [float(x) for x in args.rho.split(",") if x]:
+        rate = rho / mean_gpu
+        arrivals = I.poisson_arrivals(len(reqs), rate, seed=4)
         arrivals -= arrivals[0]
         lat_b, st_b = _replay(P, reqs, arrivals, {"max_active": 64, "workers": workers,
                                                   "options": opt})
@@ -632,30 +699,52 @@ def run_serve(args):
                                                   "options": opt})
         lat_p, qps_p = _replay_plain(P, ctx, reqs, arrivals)
         loads.append({
-            "rho": rho, "arrival_rate_per_s": rho / t_single,
-            "continuous_batching": {"qps": st_b["qps"], "p50_s": float(np.percentile(lat_b, 50)),
-                                    "p99_s": float(np.percentile(lat_b, 99)),
-                                    "mean_s": float(lat_b.mean()), "steps": st_b["steps"],
-                                    "peak_bytes": st_b["peak_bytes"]},
-            "one_at_a_time_on_gpu": {"qps": st_1["qps"], "p50_s": float(np.percentile(lat_1, 50)),
-                                     "p99_s": float(np.percentile(lat_1, 99)),
-                                     "note": "same server, one admitted request at a time"},
-            "plain_api_fifo": {"qps": qps_p, "p50_s": float(np.percentile(lat_p, 50)),
-                               "p99_s": float(np.percentile(lat_p, 99)),
-                               "note": "analyse + factor + sweep per request, in order"},
+            "rho": rho, "arrival_rate_per_s": rate,
+            "continuous_batching": _lat(lat_b, st_b["qps"], {
+                "steps": st_b["steps"], "max_step_requests": st_b["max_step_requests"],
+                "request_steps": st_b["request_steps"], "peak_bytes": st_b["peak_bytes"]}),
+            "one_at_a_time_on_gpu": _lat(lat_1, st_1["qps"], {
+                "steps": st_1["steps"],
+                "note": "same server and workers, one admitted request at a time"}),
+            "plain_api_fifo": _lat(lat_p, qps_p, {
+                "note": "analyse + factor + sweep per request through the plain API, in "
+                        "arrival order"}),
         })
-    main_load = loads[0]
+    return {
+        "workload": workload_name("serve"), "requests": len(reqs), "queries": int(nq_total),
+        "gpu_service_s": {"mean": mean_gpu, "p50": float(np.median(gpu_s)),
+                          "max": float(np.max(gpu_s)), "sum": float(np.sum(gpu_s)),
+                          "what": "device seconds of peers_factor + peers_query per request, "
+                                  "one request at a time (CUDA events)"},
+        "host_analyze_s": {"mean": float(np.mean(host_s)), "max": float(np.max(host_s))},
+        "workers": workers, "t_generate_s": t_gen, "loads": loads,
+    }
+
+
+def run_serve(args):
+    import torch
+    from paper_2606_31535_b300 import peers as P
+    torch.cuda.set_device(0)
+    ctx = P.Context(0)
+    qcap = None
+    if not args.no_autotune:
+        from paper_2606_31535_b300 import inputs as I
+        g0, qu0, qv0 = max((I.serve_request(i) for i in range(min(8, args.requests))),
+                           key=lambda r: r[0].n)
+        s0 = P.Symbolic.of(g0, 0, qu0, qv0)
+        qcap = P.autotune(ctx, s0, P.Numeric(ctx, s0), tuning_cache())["qcap"]
+    res = measure_serve(args, ctx, qcap)
+    main_load = res["loads"][0]
     line = {
         "metric": "edge queries/s and p50/p99 request latency, served request stream (FP64)",
         "value": main_load["continuous_batching"]["qps"], "unit": UNIT, "n_gpus": 1,
         "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name("serve"), "requests": len(reqs),
-                   "queries": int(nq_total), "t_single_s": t_single, "workers": workers,
-                   "generation_s": t_gen},
+        "config": {"workload": res["workload"], "requests": res["requests"],
+                   "queries": res["queries"], "workers": res["workers"]},
         "latency": {"p50_s": main_load["continuous_batching"]["p50_s"],
                     "p99_s": main_load["continuous_batching"]["p99_s"]},
-        "loads": loads,
+        "serve": res,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -70,7 +70,12 @@ typedef struct peers_options {
   int32_t qcap[4];      /* sweep tile caps: at most qcap[c] queries per CTA for supernodes
                            whose front has N rows in class c = [0,128), [128,512), [512,2048),
                            [2048,inf); 0 = the largest tile that fits (up to 32) */
-  int64_t reserved[6];
+  int64_t front_smem;   /* shared-memory bytes a sweep CTA may give its query fronts (0 = the
+                           default: tiles sized for 200 KiB, fronts up to the 227 KiB per-CTA
+                           limit).  A supernode whose front does not fit even with one query
+                           keeps its fronts in global memory instead (results are unchanged
+                           bit for bit); a small value forces that path, e.g. for tests */
+  int64_t reserved[5];
 } peers_options;
 
 /* Statistics of an analysis (all counts exact). */
@@ -93,6 +98,8 @@ typedef struct peers_info {
   int64_t factor_fma;     /* FMAs of the numeric factorization (dense blocks) */
   int64_t device_bytes;   /* device memory of peers_factor + peers_query (footprint) */
   double t_order, t_symbolic, t_queries; /* host seconds of the analysis phases */
+  int64_t nsuper_spilled; /* supernodes whose sweep fronts live in global memory (fronts
+                             larger than a CTA's shared memory; see peers_options) */
 } peers_info;
 
 /* ---- context --------------------------------------------------------------------------- */
@@ -239,10 +246,12 @@ int peers_query(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *
  *     the plan's query order.  The call allocates and frees nothing.
  *   - Scratch: the fronts carried between levels and the running sums live in one static
  *     device array of 2 Mi doubles (16 MiB) compiled into the library; every GPU that loads
- *     the library holds it until the process exits.  A plan fits when
- *     carry_slots * (max n_b + 1) <= 2 Mi doubles: analyse with peers_options.carry_budget
- *     at most 16 MiB to bound its waves.  A plan that does not
- *     fit is rejected with PEERS_EINVAL and a message naming both sizes.
+ *     the library holds it until the process exits.  A plan fits when its largest wave's
+ *     query slots x (max n_b + 1) <= 2 Mi doubles.  peers_analyze counts exactly
+ *     8 (max n_b + 1) bytes per slot against peers_options.carry_budget, so any plan analysed
+ *     with carry_budget <= 16 MiB fits (its queries are split into more waves).  A plan that
+ *     does not fit is rejected with PEERS_EINVAL and a message naming both sizes.
+ *   - The call returns after the sweep has finished: it synchronises the context's stream.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *     and caches it; make that first call before any stream capture.
  *   - All calls share the one array, which keeps the last call's contents.  Nothing in it
@@ -285,9 +294,14 @@ int peers_query_batch(peers_ctx *ctx, int32_t count, const peers_symbolic *const
  * submit) is analysed and factored by one of `workers` host threads on its own CUDA stream,
  * admitted when its device footprint (peers_footprint_bytes) fits in `mem_budget_bytes`
  * next to the admitted requests and at most `max_active` are admitted, and then swept by
- * continuous batching: one persistent launch per step carries the next etree level of every
- * active request; requests join at the next step after their factor is ready and leave after
- * their last level.  Results equal peers_query's bit for bit, alone or in the mix.
+ * continuous batching: one persistent launch per step carries work of every active request;
+ * requests join at the next step after their factor is ready and leave after their last
+ * level.  Each step gives every active request a share of a fixed amount of work (a few
+ * milliseconds of the device) from its current etree level -- the whole level when it is
+ * smaller -- so a step's length does not depend on the largest request in the mix.  Device
+ * memory of the requests comes from a memory pool of the server with stream-ordered
+ * allocation and release, so requests joining and leaving never synchronise the device.
+ * Results equal peers_query's bit for bit, alone or in the mix.
  * mem_budget_bytes <= 0 selects 64 GiB; max_active <= 0 selects 64; workers <= 0 selects 4. */
 typedef struct peers_server peers_server;
 typedef struct peers_server_stats {
@@ -297,6 +311,10 @@ typedef struct peers_server_stats {
   double wall_s;                /* first submit to last completion */
   double qps;                   /* completed queries / wall_s */
   double p50_s, p99_s, mean_s;  /* request latency, submit to results ready */
+  int64_t max_step_requests;    /* most requests with work in one step */
+  int64_t request_steps;        /* sum over completed requests of the steps that carried their
+                                   work; above `steps` exactly when requests shared steps */
+  int64_t ready;                /* factored requests waiting to join the sweep */
 } peers_server_stats;
 /* `opt` (may be NULL) is applied to the analysis of every request (ordering, tile caps,
  * carry budget). */
@@ -314,6 +332,10 @@ int peers_server_poll(peers_server *sv, int64_t ticket);
 int peers_server_wait(peers_server *sv, int64_t ticket, double *R, int64_t cap,
                       double *latency_s);
 int peers_server_get_stats(peers_server *sv, peers_server_stats *out);
+/* hold != 0: factored requests wait (stats.ready counts them) instead of joining the sweep;
+ * hold == 0: they join at the next step.  Lets a caller start a known set of requests in the
+ * same step.  Destroying the server releases a hold. */
+int peers_server_hold(peers_server *sv, int hold);
 /* Finishes the admitted and queued requests, then stops the threads and frees everything. */
 void peers_server_destroy(peers_server *sv);
 
@@ -331,10 +353,14 @@ typedef struct peers_stats {
 int peers_set_timing(peers_ctx *ctx, int enable);
 int peers_last_stats(const peers_ctx *ctx, peers_stats *out);
 
-/* Device milliseconds of each sweep launch (one per etree level) of the last timed
- * peers_query, summed over waves, into ms[0 .. min(levels, cap)).  Returns the level count or
- * a negative status. */
-int peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap);
+/* Device milliseconds per step of the last timed call on the context, into
+ * ms[0 .. min(count, cap)), where the steps are: for peers_query, each sweep launch (one per
+ * etree level, leaves first, summed over waves); for peers_factor, each etree level (leaves
+ * first); for peers_query_selinv, phase 1 (T^{-1} and M) and then each tree depth (root
+ * first); for peers_query_blockinv, the diagonal inverses, M, each tree depth of Z blocks
+ * (root first) and the query pass.  Returns the step count or a negative status (PEERS_EINVAL for a null context, or a
+ * null ms with cap > 0). */
+int64_t peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap);
 
 /* Measures the FP64 throughput of the context's device with short register-only kernels
  * (about 0.2 s), in TFLOP/s with 2 flops per multiply-add, into the caller's array of 3:
@@ -345,6 +371,14 @@ int peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap);
  * tflops[0] is the sweep's roofline denominator: the sweep is bound by FP64 FMA throughput.
  * Returns PEERS_EINVAL for a null argument, PEERS_ECUDA if a launch fails. */
 int peers_fp64_peak(peers_ctx *ctx, double tflops[3]);
+
+/* Measures every shape of the FP64 tensor instruction mma.sync .f64 (register-only kernels,
+ * about 0.2 s), in TFLOP/s with 2 flops per multiply-add, into the caller's array of 4:
+ *   tflops[0] m8n8k4, tflops[1] m16n8k4, tflops[2] m16n8k8, tflops[3] m16n8k16.
+ * The sweep's dense multi-query solve would move from DFMA (peers_fp64_peak's tflops[0]) to
+ * the FP64 tensor path only if one of these shapes were faster.
+ * Returns PEERS_EINVAL for a null argument, PEERS_ECUDA if a launch fails. */
+int peers_fp64_mma_shapes(peers_ctx *ctx, double tflops[4]);
 
 /* ---- misc ------------------------------------------------------------------------------- */
 const char *peers_strerror(int status);

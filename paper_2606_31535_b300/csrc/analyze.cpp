@@ -320,9 +320,42 @@ void assembly_values(const Symbolic &S, const double *w, std::vector<double> &va
   }
 }
 
+int32_t sweep_tile(const Symbolic &S, int64_t N, int32_t cap) {
+  int64_t q = S.front_budget / (8 * (N + 2 * kBlock));
+  q = std::min<int64_t>(q, cap);
+  if (q >= 4) q -= q % 4;
+  return static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(kQMax, q)));
+}
+
+namespace {
+
+// Orders the items [b, end) of a wave's level l (sorted by cost) with the spilled ones first
+// and records the level's launch shapes: shared memory of the regular launch, and the count
+// and shared memory of the spilled items' launch.
+void finish_level(const Symbolic &S, SweepWave &W, int32_t l, size_t b) {
+  std::stable_partition(W.items.begin() + b, W.items.end(),
+                        [](const SweepItem &it) { return it.spill != 0; });
+  int64_t smem = 0, nspill = 0, spill_smem = 0;
+  for (size_t k = b; k < W.items.size(); ++k) {
+    const SweepItem &it = W.items[k];
+    if (it.spill) {
+      ++nspill;
+      spill_smem = std::max(spill_smem, int64_t(2) * kBlock * sweep_qstride(it.nq) * 8);
+    } else {
+      smem = std::max(smem, sweep_smem_bytes(sn_nc(S, it.s) + S.nb[it.s], it.nq));
+    }
+  }
+  W.level_smem[l] = smem;
+  W.level_nspill[l] = nspill;
+  W.level_spill_smem[l] = spill_smem;
+}
+
+}  // namespace
+
 // Tiles, waves and the two-branch walk of an analysed plan for the given per-size-class
 // tile caps (queries per CTA; 0 = the largest that fits).  Rebuilding it does not change the
-// arithmetic of any query: blocks stay aligned to kBlock whatever the tile.
+// arithmetic of any query: blocks stay aligned to kBlock whatever the tile, and a front kept
+// in global memory goes through exactly the same operations as one in shared memory.
 int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
   struct Two { int32_t lo, hi; int64_t idx; };
   const int32_t kInfCol = INT32_MAX;
@@ -332,21 +365,25 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
   for (int c = 0; c < kSizeClasses; ++c)
     S.qcap[c] = qcap && qcap[c] > 0 ? std::min<int32_t>(qcap[c], kQMax) : kQMax;
   S.qtile.assign(static_cast<size_t>(ns), 1);
+  S.spill.assign(static_cast<size_t>(ns), 0);
+  S.spill_stride = 0;
   for (int32_t s = 0; s < ns; ++s) {
     const int64_t N = sn_nc(S, s) + S.nb[s];
-    int64_t q = kSweepSmemBudget / (8 * (N + 2 * kBlock));
-    q = std::min<int64_t>(q, S.qcap[size_class(N)]);
-    if (q >= 4) q -= q % 4;
-    S.qtile[s] = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(kQMax, q)));
-    if (sweep_smem_bytes(N, S.qtile[s]) > kMaxSmem) {
-      err = "supernode front of " + std::to_string(N) + " rows exceeds one CTA's shared memory";
-      return PEERS_ENOMEM;
+    const int32_t cap = S.qcap[size_class(N)];
+    S.qtile[s] = sweep_tile(S, N, cap);
+    if (sweep_smem_bytes(N, S.qtile[s]) > S.front_limit) {
+      // the front does not fit one CTA's shared memory even for one query: keep the tile's
+      // fronts in the CTA's global scratch and take the class's full tile
+      S.qtile[s] = std::max<int32_t>(1, std::min<int32_t>(kQMax, cap));
+      S.spill[s] = 1;
+      S.spill_stride = std::max(S.spill_stride, N * sweep_qstride(S.qtile[s]));
     }
   }
 
-  // waves: bound the carry buffer (one slot of nbmax doubles per query in flight)
+  // waves: bound the carry buffer (per query in flight, one slot of nbmax doubles for its
+  // carried front plus one double for its running sum)
   const int64_t budget = S.carry_budget;
-  const int64_t slot_bytes = std::max<int64_t>(8, int64_t(8) * S.nbmax);
+  const int64_t slot_bytes = int64_t(8) * (int64_t(S.nbmax) + 1);
   int64_t per_wave = std::max<int64_t>(1, budget / slot_bytes);
   if (per_wave > INT32_MAX) per_wave = INT32_MAX;
   S.waves.clear();
@@ -373,6 +410,9 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
     if (W.q_end <= W.q_begin && S.nsorted > 0) break;
     S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
     W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+    W.level_smem.assign(static_cast<size_t>(S.nlevels), 0);
+    W.level_nspill.assign(static_cast<size_t>(S.nlevels), 0);
+    W.level_spill_smem.assign(static_cast<size_t>(S.nlevels), 0);
     std::vector<std::pair<int64_t, SweepItem>> lv;
     for (int32_t l = 0; l < S.nlevels; ++l) {
       lv.clear();
@@ -388,6 +428,7 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
             it.src = src;
             it.q0 = static_cast<int32_t>(q);
             it.nq = static_cast<int32_t>(std::min<int64_t>(tile, e - q));
+            it.spill = S.spill[p];
             int32_t j0;
             if (src >= 0) {
               j0 = S.rmap[S.rows_off[src]];
@@ -410,14 +451,10 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
       }
       std::stable_sort(lv.begin(), lv.end(),
                        [](const auto &x, const auto &y) { return x.first > y.first; });
-      int64_t smem = 0;
-      for (auto &x : lv) {
-        W.items.push_back(x.second);
-        const int32_t s = x.second.s;
-        smem = std::max(smem, sweep_smem_bytes(sn_nc(S, s) + S.nb[s], x.second.nq));
-      }
+      const size_t b = W.items.size();
+      for (auto &x : lv) W.items.push_back(x.second);
+      finish_level(S, W, l, b);
       W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
-      W.level_smem.push_back(smem);
     }
     S.waves.push_back(std::move(W));
     if (S.nsorted == 0) break;
@@ -489,6 +526,8 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
       S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
       W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
       W.level_smem.assign(static_cast<size_t>(S.nlevels), 0);
+      W.level_nspill.assign(static_cast<size_t>(S.nlevels), 0);
+      W.level_spill_smem.assign(static_cast<size_t>(S.nlevels), 0);
       auto first_row = [&](const SweepDesc &d) -> int32_t {
         int32_t r = kInf;
         if (d.src_a >= 0) r = S.rmap[S.rows_off[d.src_a]];
@@ -502,6 +541,7 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
       };
       size_t i = 0;
       for (int32_t l = 0; l < S.nlevels; ++l) {
+        const size_t lb = W.items.size();
         while (i < steps.size() && S.level[steps[i].first] == l) {
           const int32_t p = steps[i].first;
           size_t e = i;
@@ -512,6 +552,7 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
             it.s = p;
             it.src = -1;
             it.kind = 1;
+            it.spill = S.spill[p];
             it.q0 = static_cast<int32_t>(S.ldesc.size());
             it.nq = static_cast<int32_t>(ce - c);
             int32_t j0 = kInf;
@@ -524,11 +565,10 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
             it.j0 = (j0 / kBlock) * kBlock;
             S.walk_fma += it.nq * item_fma(p, it.j0);
             W.items.push_back(it);
-            W.level_smem[l] = std::max(W.level_smem[l],
-                                       sweep_smem_bytes(sn_nc(S, p) + S.nb[p], it.nq));
           }
           i = e;
         }
+        finish_level(S, W, l, lb);
         W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
       }
       S.waves.push_back(std::move(W));
@@ -977,6 +1017,7 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     S.two_idx[k] = twos[k].idx;
   }
   S.carry_budget = opt.carry_budget > 0 ? opt.carry_budget : (int64_t(48) << 30);
+  if (opt.front_smem > 0) S.front_budget = S.front_limit = std::min(opt.front_smem, kMaxSmem);
   int32_t caps[kSizeClasses];
   for (int c = 0; c < kSizeClasses; ++c) caps[c] = opt.qcap[c];
   st = build_sweep_plan(S, caps, err);

@@ -28,12 +28,6 @@ namespace {
 using peers::kBlock;
 using peers::SweepItem;
 
-int64_t tile_of(int64_t N, int32_t cap) {
-  int64_t q = peers::kSweepSmemBudget / (8 * (N + 2 * kBlock));
-  q = std::min<int64_t>(q, cap);
-  if (q >= 4) q -= q % 4;
-  return std::max<int64_t>(1, std::min<int64_t>(peers::kQMax, q));
-}
 
 int64_t items_fma(const Symbolic &S, int32_t s, int32_t j0) {
   const int64_t nc = peers::sn_nc(S, s), N = nc + S.nb[s];
@@ -54,7 +48,7 @@ std::vector<SweepItem> tile_items(const Symbolic &S, const std::vector<int32_t> 
   for (size_t i = 0; i < sns.size(); ++i) {
     const int32_t p = sns[i];
     const int64_t N = peers::sn_nc(S, p) + S.nb[p];
-    const int64_t tile = tile_of(N, cap);
+    const int64_t tile = peers::sweep_tile(S, N, cap);
     auto emit = [&](int32_t src, int64_t b, int64_t e) {
       b = std::max(b, W.q_begin);
       e = std::min(e, W.q_end);
@@ -104,7 +98,7 @@ void write_cache(const char *path, const std::map<std::string, int32_t> &m) {
 int tune(peers_ctx *ctx, peers_symbolic *sym, peers_numeric *num, const char *cache_path,
          int32_t caps[4], double gain[4], std::string &err) {
   Symbolic &S = sym->S;
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  DEVICE_SCOPE(ctx->device);
   cudaDeviceProp prop;
   CUDA_TRY(cudaGetDeviceProperties(&prop, ctx->device));
   auto cache = read_cache(cache_path);
@@ -123,7 +117,7 @@ int tune(peers_ctx *ctx, peers_symbolic *sym, peers_numeric *num, const char *ca
   for (int32_t p = 0; p < S.nsuper; ++p) {
     const int64_t q = std::min(S.qbeg[p + 1], S.waves[0].q_end) -
                       std::max(S.qbeg[S.fdesc[p]], S.waves[0].q_begin);
-    if (q <= 0) continue;
+    if (q <= 0 || S.spill[p]) continue;   // fronts in global memory keep the full tile
     const int64_t N = peers::sn_nc(S, p) + S.nb[p];
     by_class[peers::size_class(N)].push_back({q * items_fma(S, p, 0), p});
   }

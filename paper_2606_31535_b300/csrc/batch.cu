@@ -65,7 +65,7 @@ int64_t item_cost(const Symbolic &S, const SweepItem &it) {
 }
 
 int build(peers_ctx *ctx, peers_batch *b, std::string &err) {
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  DEVICE_SCOPE(ctx->device);
   b->device = ctx->device;
   // results and scratch: one carry region per graph (its waves run one after another)
   std::vector<int64_t> carry_off(b->count), racc_off(b->count);
@@ -187,7 +187,7 @@ int enqueue(peers_batch *b, cudaStream_t st, std::string &err) {
 }
 
 int query(peers_ctx *ctx, peers_batch *b, double *const *R, int flags, std::string &err) {
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  DEVICE_SCOPE(ctx->device);
   cudaStream_t st = ctx->stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ctx->timing) {
@@ -280,6 +280,12 @@ int peers_batch_create(peers_ctx *ctx, int32_t count, const peers_symbolic *cons
       return peers_fail(PEERS_EINVAL, "batch entry " + std::to_string(i) +
                                           ": missing handle, foreign factor or other device");
     }
+    if (syms[i]->S.spill_stride > 0) {
+      delete b;
+      return peers_fail(PEERS_EINVAL, "batch entry " + std::to_string(i) +
+                                          " keeps fronts larger than shared memory in global "
+                                          "memory; sweep it with peers_query");
+    }
     b->syms.push_back(syms[i]);
     b->nums.push_back(nums[i]);
   }
@@ -316,9 +322,11 @@ int peers_batch_info(const peers_batch *b, int64_t out[4]) {
 
 void peers_batch_free(peers_batch *b) {
   if (!b) return;
-  cudaSetDevice(b->device);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  for (void *p : b->allocs) cudaFree(p);
+  {
+    peers::DeviceGuard guard(b->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (void *p : b->allocs) cudaFree(p);
+  }
   delete b;
 }
 

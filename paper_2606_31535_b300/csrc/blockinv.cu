@@ -1262,7 +1262,7 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
              std::string &err) {
   const Symbolic &S = sym->S;
   cudaStream_t st = ctx->stream;
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  DEVICE_SCOPE(ctx->device);
   std::shared_ptr<const peers::BlockInvPlan> plan;
   int rc = peers::cached_blockinv_plan(sym, plan, err);
   if (rc != PEERS_OK) return rc;
@@ -1444,7 +1444,7 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
              std::string &err) {
   const Symbolic &S = sym->S;
   cudaStream_t st = ctx->stream;
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  DEVICE_SCOPE(ctx->device);
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   std::shared_ptr<const peers::SelInvPlan> plan;
@@ -1653,8 +1653,14 @@ int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_nu
                        double *R, int flags) {
   if (!ctx || !sym || !num || (!R && sym->S.nq > 0)) return peers_fail(PEERS_EINVAL, "null argument");
   if (num->sym != sym) return peers_fail(PEERS_EINVAL, "numeric handle belongs to another plan");
+  if (num->device != ctx->device) return peers_fail(PEERS_EINVAL, "context on another device");
   std::string err;
-  int rc = si_query(ctx, sym, const_cast<peers_numeric *>(num), R, flags, err);
+  int rc = PEERS_OK;
+  if ((flags & PEERS_OUT_DEVICE) && sym->S.nq > 0) {
+    peers::DeviceGuard guard(ctx->device);
+    rc = peers::check_device_result(ctx->device, R, err);
+  }
+  if (rc == PEERS_OK) rc = si_query(ctx, sym, const_cast<peers_numeric *>(num), R, flags, err);
   return rc == PEERS_OK ? rc : peers_fail(rc, err);
 }
 
@@ -1671,8 +1677,14 @@ int peers_query_blockinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_
                          double *R, int flags) {
   if (!ctx || !sym || !num || (!R && sym->S.nq > 0)) return peers_fail(PEERS_EINVAL, "null argument");
   if (num->sym != sym) return peers_fail(PEERS_EINVAL, "numeric handle belongs to another plan");
+  if (num->device != ctx->device) return peers_fail(PEERS_EINVAL, "context on another device");
   std::string err;
-  int rc = bi_query(ctx, sym, const_cast<peers_numeric *>(num), R, flags, err);
+  int rc = PEERS_OK;
+  if ((flags & PEERS_OUT_DEVICE) && sym->S.nq > 0) {
+    peers::DeviceGuard guard(ctx->device);
+    rc = peers::check_device_result(ctx->device, R, err);
+  }
+  if (rc == PEERS_OK) rc = bi_query(ctx, sym, const_cast<peers_numeric *>(num), R, flags, err);
   return rc == PEERS_OK ? rc : peers_fail(rc, err);
 }
 

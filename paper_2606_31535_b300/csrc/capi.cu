@@ -26,6 +26,24 @@ int fail(int status, const std::string &msg) {
 
 int peers_fail(int status, const std::string &msg) { return fail(status, msg); }
 
+int peers::check_device_result(int device, const void *p, std::string &err) {
+  if (!p) return PEERS_OK;
+  cudaPointerAttributes at{};
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    err = std::string("result pointer: ") + cudaGetErrorString(e);
+    return PEERS_EINVAL;
+  }
+  if (at.type == cudaMemoryTypeManaged) return PEERS_OK;
+  if (at.type != cudaMemoryTypeDevice || at.device != device) {
+    err = "the result pointer is not device memory of the context's device (flag "
+          "PEERS_OUT_DEVICE)";
+    return PEERS_EINVAL;
+  }
+  return PEERS_OK;
+}
+
 namespace {
 
 template <class T>
@@ -33,7 +51,9 @@ int dalloc(peers_numeric *num, T **p, int64_t count, std::string &err) {
   *p = nullptr;
   if (count <= 0) return PEERS_OK;
   void *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, sizeof(T) * static_cast<size_t>(count));
+  const size_t bytes = sizeof(T) * static_cast<size_t>(count);
+  cudaError_t e = num->pool ? cudaMallocFromPoolAsync(&q, bytes, num->pool, num->pool_stream)
+                            : cudaMalloc(&q, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     err = "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes: " + cudaGetErrorString(e);
@@ -56,7 +76,10 @@ int upload(peers_numeric *num, T **p, const std::vector<T> &v, cudaStream_t st, 
 void dfree(peers_numeric *num, void *p) {
   auto it = std::find(num->allocs.begin(), num->allocs.end(), p);
   if (it != num->allocs.end()) {
-    cudaFree(p);
+    if (num->pool)
+      cudaFreeAsync(p, num->pool_stream);
+    else
+      cudaFree(p);
     num->allocs.erase(it);
   }
 }
@@ -89,10 +112,14 @@ int upload_tiles(peers_numeric *num, const Symbolic &S, cudaStream_t st, std::st
   TRY(upload(num, &num->two_user, S.two_user, st, err));
   TRY(upload(num, &num->two_a, S.two_a, st, err));
   TRY(upload(num, &num->two_b, S.two_b, st, err));
-  // the carry buffer is sized by the plan's waves: drop it, the next query re-allocates
+  // the carry buffer and the front scratch are sized by the plan's waves and tiles: drop
+  // them, the next query re-allocates
   if (num->carry) dfree(num, num->carry);
   if (num->racc) dfree(num, num->racc);
-  num->carry = num->racc = nullptr;
+  if (num->spill) dfree(num, num->spill);
+  if (num->spill_counter) dfree(num, num->spill_counter);
+  num->carry = num->racc = num->spill = nullptr;
+  num->spill_counter = nullptr;
   return PEERS_OK;
 }
 
@@ -100,7 +127,7 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
                 std::string &err) {
   const Symbolic &S = sym->S;
   cudaStream_t st = ctx->stream;
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  DEVICE_SCOPE(ctx->device);
   num->device = ctx->device;
   num->sym = sym;
   // structure shared by the factorization and the sweep
@@ -139,13 +166,16 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
   D.ea_pairs = ea_pairs;
   D.trail_prefix = trail_prefix;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<cudaEvent_t> lev;
   if (ctx->timing) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    lev.resize(static_cast<size_t>(S.nlevels) + 1);
+    for (auto &e : lev) cudaEventCreate(&e);
     cudaEventRecord(e0, st);
   }
   int64_t launches = 0;
-  int rc = peers::run_factor(S, D, st, &launches, err);
+  int rc = peers::run_factor(S, D, st, &launches, err, ctx->timing ? lev.data() : nullptr);
   ctx->stats.factor_launches = launches;
   if (ctx->timing) {
     cudaEventRecord(e1, st);
@@ -153,6 +183,14 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     ctx->stats.factor_s = ms * 1e-3;
+    if (rc == PEERS_OK) {
+      ctx->level_ms.assign(static_cast<size_t>(S.nlevels), 0.0);
+      for (int32_t l = 0; l < S.nlevels; ++l) {
+        cudaEventElapsedTime(&ms, lev[l], lev[l + 1]);
+        ctx->level_ms[l] = ms;
+      }
+    }
+    for (auto e : lev) cudaEventDestroy(e);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
@@ -176,16 +214,39 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
 
 }  // namespace
 
+int factor_from_pool(peers_ctx *ctx, const peers_symbolic *sym, const double *w,
+                     cudaMemPool_t pool, peers_numeric **out, std::string &err) {
+  *out = nullptr;
+  auto *num = new (std::nothrow) peers_numeric;
+  if (!num) {
+    err = "host allocation";
+    return PEERS_ENOMEM;
+  }
+  num->pool = pool;
+  num->pool_stream = ctx->stream;
+  const int rc = factor_impl(ctx, sym, w, num, err);
+  if (rc != PEERS_OK) {
+    peers_free_numeric(num);
+    return rc;
+  }
+  *out = num;
+  return PEERS_OK;
+}
+
 int ensure_carry(peers_numeric *num, const Symbolic &S, std::string &err) {
   if (!num->carry && S.carry_slots > 0) {
     TRY(dalloc(num, &num->carry, std::max<int64_t>(1, S.carry_slots * S.nbmax), err));
     TRY(dalloc(num, &num->racc, S.carry_slots, err));
   }
+  if (!num->spill && S.spill_stride > 0) {
+    TRY(dalloc(num, &num->spill, int64_t(peers::kSpillGrid) * S.spill_stride, err));
+    TRY(dalloc(num, &num->spill_counter, std::max<int64_t>(1, S.nlevels), err));
+  }
   return PEERS_OK;
 }
 
 int refresh_tiles(peers_ctx *ctx, const Symbolic &S, peers_numeric *num, std::string &err) {
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  DEVICE_SCOPE(ctx->device);
   TRY(upload_tiles(num, S, ctx->stream, err));
   CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return PEERS_OK;
@@ -197,10 +258,11 @@ int query_impl(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, do
                int flags, std::string &err) {
   const Symbolic &S = sym->S;
   cudaStream_t st = ctx->stream;
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  DEVICE_SCOPE(ctx->device);
+  const bool host_out = !(flags & PEERS_OUT_DEVICE);
+  if (!host_out && S.nq > 0) TRY(peers::check_device_result(ctx->device, R, err));
   TRY(ensure_carry(num, S, err));
   double *Rout = R;
-  const bool host_out = !(flags & PEERS_OUT_DEVICE);
   if (host_out) {
     if (!num->Rdev && S.nq > 0) TRY(dalloc(num, &num->Rdev, S.nq, err));
     Rout = num->Rdev;
@@ -224,6 +286,9 @@ int query_impl(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, do
   a.racc = num->racc;
   a.R = Rout;
   a.nbmax = S.nbmax;
+  a.spill = num->spill;
+  a.spill_stride = S.spill_stride;
+  a.spill_counter = num->spill_counter;
   std::vector<cudaEvent_t> ev;
   if (ctx->timing) {
     ev.resize(2 * static_cast<size_t>(S.nlevels));
@@ -301,7 +366,8 @@ int peers_create(peers_ctx **out, int device, void *cuda_stream) {
   auto *ctx = new (std::nothrow) peers_ctx;
   if (!ctx) return fail(PEERS_ENOMEM, "host allocation");
   ctx->device = device;
-  e = cudaSetDevice(device);
+  peers::DeviceGuard guard(device);
+  e = guard.status();
   if (e == cudaSuccess) {
     if (cuda_stream) {
       ctx->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -376,6 +442,7 @@ int peers_symbolic_info(const peers_symbolic *sym, peers_info *info) {
   info->t_order = S.t_order;
   info->t_symbolic = S.t_symbolic;
   info->t_queries = S.t_queries;
+  for (char x : S.spill) info->nsuper_spilled += x ? 1 : 0;
   return PEERS_OK;
 }
 
@@ -389,6 +456,7 @@ int64_t peers_footprint_bytes(const peers_symbolic *sym) {
   // resident factor + sweep scratch + results, plus the factorization's transient update
   // matrices and assembly arrays (freed when peers_factor returns)
   return 8 * (S.panel_total + S.tinv_total + 2 * S.nr + S.carry_slots * (S.nbmax + 1) + S.nq) +
+         8 * int64_t(peers::kSpillGrid) * S.spill_stride + 4 * int64_t(S.nlevels) +
          8 * (S.u_total + 2 * static_cast<int64_t>(S.a_dest.size())) +
          4 * (3 * int64_t(S.nsuper) + static_cast<int64_t>(S.rmap.size()) + 2 * S.nsorted) +
          8 * (3 * int64_t(S.nsuper) + S.nsorted) + static_cast<int64_t>(sizeof(SweepItem)) * items;
@@ -433,7 +501,7 @@ int peers_numeric_diag(peers_ctx *ctx, const peers_numeric *num, double *d_host)
   if (!ctx || !num || !d_host) return fail(PEERS_EINVAL, "null argument");
   std::string err;
   auto run = [&]() -> int {
-    CUDA_TRY(cudaSetDevice(num->device));
+    DEVICE_SCOPE(num->device);
     CUDA_TRY(cudaMemcpyAsync(d_host, num->d, sizeof(double) * num->sym->S.nr,
                              cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -446,8 +514,13 @@ int peers_numeric_diag(peers_ctx *ctx, const peers_numeric *num, double *d_host)
 void peers_free_numeric(peers_numeric *num) {
   if (!num) return;
   if (!num->allocs.empty()) {
-    cudaSetDevice(num->device);
-    for (void *p : num->allocs) cudaFree(p);
+    peers::DeviceGuard guard(num->device);
+    for (void *p : num->allocs) {
+      if (num->pool)
+        cudaFreeAsync(p, num->pool_stream);
+      else
+        cudaFree(p);
+    }
   }
   delete num;
 }
@@ -512,18 +585,30 @@ int peers_fp64_peak(peers_ctx *ctx, double tflops[3]) {
   if (!ctx || !tflops) return fail(PEERS_EINVAL, "null argument");
   std::string err;
   auto run = [&]() -> int {
-    CUDA_TRY(cudaSetDevice(ctx->device));
+    DEVICE_SCOPE(ctx->device);
     return peers::fp64_peak(ctx->stream, tflops, err);
   };
   int rc = run();
   return rc == PEERS_OK ? rc : fail(rc, err);
 }
 
-int peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap) {
+int peers_fp64_mma_shapes(peers_ctx *ctx, double tflops[4]) {
+  if (!ctx || !tflops) return fail(PEERS_EINVAL, "null argument");
+  std::string err;
+  auto run = [&]() -> int {
+    DEVICE_SCOPE(ctx->device);
+    return peers::fp64_mma_shapes(ctx->stream, tflops, err);
+  };
+  int rc = run();
+  return rc == PEERS_OK ? rc : fail(rc, err);
+}
+
+int64_t peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap) {
   if (!ctx) return fail(PEERS_EINVAL, "null context");
+  if (cap > 0 && !ms) return fail(PEERS_EINVAL, "null output array with a positive capacity");
   const int64_t nl = static_cast<int64_t>(ctx->level_ms.size());
   for (int64_t i = 0; i < std::min(nl, cap); ++i) ms[i] = ctx->level_ms[i];
-  return static_cast<int>(nl);
+  return nl;
 }
 
 }  // extern "C"

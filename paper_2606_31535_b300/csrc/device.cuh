@@ -18,6 +18,36 @@
 
 namespace peers {
 
+// Makes `device` current for the guard's lifetime and then restores the calling thread's
+// previous device, so that no library call leaves its caller on another device.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int device) {
+    status_ = cudaGetDevice(&prev_);
+    if (status_ == cudaSuccess && prev_ != device) {
+      status_ = cudaSetDevice(device);
+      switched_ = status_ == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  DeviceGuard(const DeviceGuard &) = delete;
+  DeviceGuard &operator=(const DeviceGuard &) = delete;
+  cudaError_t status() const { return status_; }
+
+ private:
+  int prev_ = 0;
+  bool switched_ = false;
+  cudaError_t status_ = cudaSuccess;
+};
+
+// Declares a DeviceGuard for `dev` in the enclosing scope and returns PEERS_ECUDA (with `err`
+// set) if the device cannot be made current.
+#define DEVICE_SCOPE(dev)                 \
+  ::peers::DeviceGuard device_guard_(dev); \
+  CUDA_TRY(device_guard_.status())
+
 constexpr int kErrNotSpd = 1;
 
 // Records the first error code and where it happened; later errors are dropped.
@@ -57,11 +87,19 @@ struct SweepArgs {
   const int32_t *two_a, *two_b;
   int64_t nbmax;
   int64_t wave_base;
+  // fronts of supernodes that do not fit shared memory (items with spill == 1): CTA b of the
+  // spilled launch keeps its tile's fronts at spill + b * spill_stride; spill_counter holds
+  // one work counter per level (zeroed before each wave)
+  double *spill;
+  int64_t spill_stride;
+  int *spill_counter;
 };
 
 // Runs the whole factorization on `stream`; adds the number of kernels launched to *launches.
+// If `level_events` is non-null it must hold nlevels + 1 events: [0] is recorded before the
+// first level and [l + 1] after level l.
 int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, int64_t *launches,
-               std::string &err);
+               std::string &err, cudaEvent_t *level_events = nullptr);
 
 // Launches the sweep of one wave, level by level.  If `events` is non-null it must hold
 // 2 * nlevels events; launch l is bracketed by events[2l], events[2l+1].
@@ -97,8 +135,15 @@ int query_noalloc(cudaStream_t stream, int device, const Symbolic &S, const Swee
                   const int64_t *two_user, const int32_t *two_a, const int32_t *two_b,
                   double *R, int64_t *launches, std::string &err);
 
+// Checks that a caller's device result pointer is device (or managed) memory reachable from
+// `device` before any kernel writes through it; PEERS_EINVAL otherwise (capi.cu).
+int check_device_result(int device, const void *p, std::string &err);
+
 // FP64 throughput probes (TFLOP/s) on the current device: out[0] DFMA (CUDA cores),
 // out[1] mma.sync m8n8k4 f64 (the FP64 tensor path).
 int fp64_peak(cudaStream_t stream, double out[3], std::string &err);
+// Every f64 mma.sync shape (TFLOP/s): out[0] m8n8k4, out[1] m16n8k4, out[2] m16n8k8,
+// out[3] m16n8k16.
+int fp64_mma_shapes(cudaStream_t stream, double out[4], std::string &err);
 
 }  // namespace peers

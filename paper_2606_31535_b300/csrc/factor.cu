@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
 
 // Host driver: the full factorization on `stream`.  Returns a PEERS_* status.
 int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, int64_t *launches,
-               std::string &err) {
+               std::string &err, cudaEvent_t *level_events) {
   FactorArgs a = D.args;
   CUDA_TRY(cudaMemsetAsync(a.panel, 0, sizeof(double) * S.panel_total, stream));
   if (S.u_total > 0) CUDA_TRY(cudaMemsetAsync(a.U, 0, sizeof(double) * S.u_total, stream));
@@ -214,6 +214,7 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, in
     }
     CUDA_TRY(cudaGetLastError());
   }
+  if (level_events) CUDA_TRY(cudaEventRecord(level_events[0], stream));
   for (int32_t l = 0; l < S.nlevels; ++l) {
     const int32_t *sns = D.level_sn + S.level_ptr[l];
     // 1. extend-add of the children, one launch per child rank
@@ -256,6 +257,7 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, in
         CUDA_TRY(cudaGetLastError());
       }
     }
+    if (level_events) CUDA_TRY(cudaEventRecord(level_events[l + 1], stream));
   }
   int status[2] = {0, 0};
   CUDA_TRY(cudaMemcpyAsync(status, a.status, sizeof(status), cudaMemcpyDeviceToHost, stream));

@@ -44,6 +44,12 @@ struct peers_numeric {
   int device = 0;
   const peers_symbolic *sym = nullptr;   // not owned; must outlive this handle
   std::vector<void *> allocs;
+  // Stream-ordered allocation (the server's requests): when `pool` is set, every buffer of the
+  // handle comes from that memory pool on `pool_stream` and is returned to it on
+  // `pool_stream`, so that neither allocating nor freeing synchronises the device.  The owner
+  // may point pool_stream at another stream before freeing the handle.
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t pool_stream = nullptr;
   int64_t h2d_bytes = 0;   // bytes uploaded while building this handle
   // factor
   double *panel = nullptr, *tinv = nullptr, *d = nullptr, *dinv = nullptr;
@@ -58,6 +64,8 @@ struct peers_numeric {
   int32_t *two_a = nullptr, *two_b = nullptr;
   std::vector<int64_t> wave_item_off;
   double *carry = nullptr, *racc = nullptr, *Rdev = nullptr;
+  double *spill = nullptr;        // kSpillGrid x spill_stride front scratch (if the plan spills)
+  int *spill_counter = nullptr;   // one work counter per level
 };
 
 
@@ -81,11 +89,19 @@ inline peers::SweepArgs sweep_args_of(const peers_numeric *num, const Symbolic &
   a.two_a = num->two_a;
   a.two_b = num->two_b;
   a.nbmax = S.nbmax;
+  a.spill = num->spill;
+  a.spill_stride = S.spill_stride;
+  a.spill_counter = num->spill_counter;
   return a;
 }
 
 // Records a failure message for peers_last_error and returns the status.
 int peers_fail(int status, const std::string &msg);
+
+// peers_factor with every device buffer of the new handle taken from `pool` on the context's
+// stream (stream-ordered; see peers_numeric::pool).  Returns a PEERS_* status (capi.cu).
+int factor_from_pool(peers_ctx *ctx, const peers_symbolic *sym, const double *w,
+                     cudaMemPool_t pool, peers_numeric **out, std::string &err);
 
 // Allocates the sweep's carry buffer of a factored plan if it has none (capi.cu).
 int ensure_carry(peers_numeric *num, const Symbolic &S, std::string &err);

@@ -29,6 +29,9 @@ constexpr int64_t kSweepSmemBudget = 200 * 1024;
 
 // Largest dynamic shared memory of one CTA on sm_103a (bytes).
 constexpr int64_t kMaxSmem = 232448;
+// CTAs of a sweep launch over fronts kept in global memory (supernodes whose front does not
+// fit one CTA's shared memory): a persistent grid, each CTA with its own front scratch.
+constexpr int kSpillGrid = 296;
 
 // Row stride (in queries) of a sweep CTA's shared front: a multiple of 4, at least 4.
 PEERS_HD inline int64_t sweep_qstride(int64_t Q) { return Q < 4 ? 4 : (Q + 3) / 4 * 4; }
@@ -59,7 +62,7 @@ struct SweepItem {
   int32_t j0;   // first column block (block-aligned) with a non-zero right-hand side
   int32_t kind;
   int32_t g;
-  int32_t pad;
+  int32_t spill;   // 1: the tile's fronts live in the CTA's global scratch, not shared memory
 };
 
 // One query step of the two-branch walk (a listed pair whose endpoints' etree paths meet
@@ -78,6 +81,9 @@ struct SweepWave {
   int64_t two_begin = 0, two_end = 0;   // two-branch queries finished by this wave (combine)
   std::vector<int64_t> level_ptr;
   std::vector<int64_t> level_smem;   // dynamic shared memory of the level's launch
+  // the first level_nspill[l] items of level l have spill == 1 and run in their own launch
+  // (dynamic shared memory level_spill_smem[l])
+  std::vector<int64_t> level_nspill, level_spill_smem;
   std::vector<SweepItem> items;
 };
 
@@ -148,6 +154,12 @@ struct Symbolic {
   std::vector<int32_t> qtile;       // tile size (queries per CTA) per supernode
   int32_t qcap[kSizeClasses] = {kQMax, kQMax, kQMax, kQMax};   // tile caps in use
   int64_t carry_budget = 0;         // bytes of carried fronts per wave
+  // shared memory of a sweep CTA: the tile is sized for front_budget bytes of fronts, and a
+  // supernode whose smallest tile still needs more than front_limit bytes keeps its fronts in
+  // global memory (spill[s] = 1, kSpillGrid CTAs x spill_stride doubles of scratch)
+  int64_t front_budget = kSweepSmemBudget, front_limit = kMaxSmem;
+  std::vector<char> spill;
+  int64_t spill_stride = 0;
   std::vector<int32_t> two_lo, two_hi;   // two-branch queries (elimination positions)
   std::vector<int64_t> two_idx;          // and their user indices
   int32_t nbmax = 0;
@@ -166,6 +178,10 @@ struct Symbolic {
 int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indices,
             const double *w, int32_t ground, int64_t nq, const int32_t *qu, const int32_t *qv,
             const double *coords, int dim, const peers_options &opt, std::string &err);
+
+// Queries per sweep CTA for a front of N rows under the plan's shared-memory budget and the
+// size class's cap (analyze.cpp).
+int32_t sweep_tile(const Symbolic &S, int64_t N, int32_t cap);
 
 // (Re)builds the sweep's tiles and waves of an analysed plan (analyze.cpp).
 int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err);

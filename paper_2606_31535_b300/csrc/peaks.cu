@@ -2,7 +2,10 @@
 // denominator.  Three figures: DFMA on the CUDA cores, mma.sync m8n8k4 f64 (the FP64 tensor
 // path), and both issued at once by alternate warps of one kernel.  The third says whether
 // the two draw on separate hardware (it would then approach the sum of the first two) or on
-// one FP64 unit (it stays near the larger of the two).
+// one FP64 unit (it stays near the larger of the two).  A second probe times every shape of
+// the f64 mma.sync (m8n8k4, m16n8k4, m16n8k8, m16n8k16): the larger shapes carry more
+// multiply-adds per instruction, so they would show an FP64 tensor rate that the smallest
+// shape's issue rate hides.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,6 +55,56 @@ __global__ void __launch_bounds__(kPeakThreads) k_fp64_peak(double *out, int ite
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The larger f64 mma.sync shapes (sm_90 and later).  Fragments per thread: m16n8k4 A 2, B 1,
+// C/D 4; m16n8k8 A 4, B 2, C/D 4; m16n8k16 A 8, B 4, C/D 4 doubles.
+__device__ __forceinline__ void dmma_m16n8k4(double (&d)[4], double a, double b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+      "{%0,%1,%2,%3};\n"
+      : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+      : "d"(a), "d"(a), "d"(b));
+}
+__device__ __forceinline__ void dmma_m16n8k8(double (&d)[4], double a, double b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+      : "d"(a), "d"(a), "d"(a), "d"(a), "d"(b), "d"(b));
+}
+__device__ __forceinline__ void dmma_m16n8k16(double (&d)[4], double a, double b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
+      "{%4,%5,%6,%7,%8,%9,%10,%11}, {%12,%13,%14,%15}, {%0,%1,%2,%3};\n"
+      : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+      : "d"(a), "d"(a), "d"(a), "d"(a), "d"(a), "d"(a), "d"(a), "d"(a), "d"(b), "d"(b),
+        "d"(b), "d"(b));
+}
+
+// SHAPE 1: m16n8k4, 2: m16n8k8, 3: m16n8k16; kMmaChains independent accumulators per warp.
+template <int SHAPE>
+__global__ void __launch_bounds__(kPeakThreads) k_fp64_mma_shape(double *out, int iters,
+                                                                 double a, double b) {
+  double acc[kMmaChains][4];
+#pragma unroll
+  for (int j = 0; j < kMmaChains; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[j][i] = threadIdx.x + j + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < kMmaChains; ++j) {
+      if (SHAPE == 1) dmma_m16n8k4(acc[j], a, b);
+      else if (SHAPE == 2) dmma_m16n8k8(acc[j], a, b);
+      else dmma_m16n8k16(acc[j], a, b);
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < kMmaChains; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s += acc[j][i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // flops one warp does per iteration
 constexpr double kDfmaWarpFlops = 2.0 * 32 * kDfmaChains * kDfmaDepth;
 constexpr double kMmaWarpFlops = 2.0 * 8 * 8 * 4 * kMmaChains;
@@ -90,7 +143,54 @@ int time_mode(cudaStream_t stream, double *out, int blocks, int iters, double *t
   return PEERS_OK;
 }
 
+// Best-of-3 TFLOP/s of k_fp64_mma_shape<SHAPE> (after one untimed launch).
+template <int SHAPE>
+int time_shape(cudaStream_t stream, double *out, int blocks, int iters, double *tflops,
+               std::string &err) {
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = 0.0f;
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, stream);
+    k_fp64_mma_shape<SHAPE><<<blocks, kPeakThreads, 0, stream>>>(out, iters, 1.0, 1.0);
+    cudaEventRecord(e1, stream);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms > 0.0f) best = best == 0.0f ? ms : std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return PEERS_ECUDA;
+  }
+  const double k = SHAPE == 1 ? 4 : SHAPE == 2 ? 8 : 16;
+  const double warp_flops = 2.0 * 16 * 8 * k * kMmaChains;
+  const double warps = double(blocks) * (kPeakThreads / 32);
+  *tflops = best > 0.0f ? warps * warp_flops * iters / (double(best) * 1e9) : 0.0;
+  return PEERS_OK;
+}
+
 }  // namespace
+
+int fp64_mma_shapes(cudaStream_t stream, double out4[4], std::string &err) {
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 4;
+  double *out = nullptr;
+  CUDA_TRY(cudaMalloc(&out, sizeof(double) * blocks * kPeakThreads));
+  int rc = time_mode<1>(stream, out, blocks, 1024, &out4[0], err);
+  if (rc == PEERS_OK) rc = time_shape<1>(stream, out, blocks, 512, &out4[1], err);
+  if (rc == PEERS_OK) rc = time_shape<2>(stream, out, blocks, 256, &out4[2], err);
+  if (rc == PEERS_OK) rc = time_shape<3>(stream, out, blocks, 128, &out4[3], err);
+  cudaFree(out);
+  return rc;
+}
 
 int fp64_peak(cudaStream_t stream, double out3[3], std::string &err) {
   int dev = 0, sms = 0;

@@ -1,9 +1,23 @@
 // Serving loop: requests (graph + queries) arrive at any time; each is analysed and factored
 // by a worker thread, admitted by device-memory footprint, and then swept together with every
-// other admitted request by continuous batching: one persistent launch per step carries the
-// next etree level of every active request, requests join at the next step after their
-// factor is ready and leave after their last level.  A request's arithmetic is exactly that
-// of peers_query, so its result is the same alone and in the mix, bit for bit.
+// other admitted request by continuous batching: one persistent launch per step carries work
+// of every active request, requests join at the next step after their factor is ready and
+// leave after their last level.  A request's arithmetic is exactly that of peers_query, so its
+// result is the same alone and in the mix, bit for bit.
+//
+// Time slicing.  The items of one etree level of one request are independent of each other
+// (eq. 16-18 per query; a query's next level needs only its own previous level), so a level
+// may be spread over several steps.  Each step gives every active request a share of about
+// kStepQuantum / (active requests) multiply-adds of its current level (whole levels when they
+// are smaller, at least one item), so a step lasts about one quantum whatever the requests'
+// sizes: a small request is never held for the length of a large request's root level, and
+// a large one keeps the GPU busy between the small ones' levels.
+//
+// Device memory.  Every request's factor and sweep scratch come from one memory pool of the
+// server, allocated on the worker's stream and returned on the server's stream
+// (cudaMallocFromPoolAsync / cudaFreeAsync), so neither admitting nor retiring a request
+// synchronises the device under the running steps.  Results are copied to pinned staging
+// buffers, one per step in flight, so the copy does not block the step thread either.
 //
 // Threads: `workers` analysis/factor threads (each with its own CUDA stream, so factoring
 // overlaps the sweep on the device) and one device thread that runs the steps.  The device
@@ -33,6 +47,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Multiply-adds of one step (about 4 ms of the sweep kernel on a B300 at its FP64 rate).
+constexpr int64_t kStepQuantum = int64_t(2500) * 1000 * 1000;
+
 struct ReqStep {
   int32_t wave;           // argument block of the request: slot base + wave
   int64_t i0, i1;         // items of the wave's level (when combine == false)
@@ -61,8 +78,12 @@ struct Request {
   int64_t footprint = 0;
   double *d_scratch = nullptr, *d_R = nullptr;
   std::vector<ReqStep> steps;
-  size_t pos = 0;
+  size_t pos = 0;          // current entry of `steps`
+  int64_t next = 0;        // items of steps[pos] already issued
+  int64_t issue_end = 0;   // items of steps[pos] issued once the step being prepared runs
+  int64_t steps_in = 0;    // sweep steps that carried work of this request
   int32_t slot = -1;
+  int64_t staged = -1;     // offset of the results in the pinned staging buffer
   std::vector<double> R;
   Clock::time_point t_submit, t_done;
 };
@@ -77,6 +98,7 @@ struct peers_server {
   std::mutex mu;
   std::condition_variable cv;
   bool stop = false;
+  bool hold = false;                                // factored requests wait to join
   int64_t next_ticket = 1;
   std::map<int64_t, std::shared_ptr<Request>> reqs;
   std::deque<std::shared_ptr<Request>> pending;    // waiting for a worker
@@ -85,18 +107,24 @@ struct peers_server {
   int32_t admitted = 0;                             // factored + active
   std::vector<std::thread> workers;
   std::thread device_thread;
+  // device memory of the requests (stream-ordered)
+  cudaMemPool_t pool = nullptr;
   // device thread state
   cudaStream_t stream = nullptr;
   peers::SweepArgs *d_table = nullptr;
+  peers::SweepArgs *h_table = nullptr;              // pinned mirror of d_table
   std::vector<char> slot_used;
   SweepItem *d_items[2] = {nullptr, nullptr};
   SweepItem *h_items[2] = {nullptr, nullptr};
   int64_t items_cap[2] = {0, 0};
+  double *h_stage[2] = {nullptr, nullptr};          // pinned result staging per step in flight
+  int64_t stage_cap[2] = {0, 0};
   int *d_counter = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   // statistics
   std::vector<double> latencies;
   int64_t completed = 0, failed = 0, queries = 0, steps = 0, launches = 0;
+  int64_t max_step_requests = 0, request_steps = 0;
   Clock::time_point t_first, t_last;
   bool any_submit = false;
   std::string fatal;
@@ -106,11 +134,16 @@ namespace {
 
 constexpr int32_t kTableSlots = 16384;
 
-void release_device(Request &r) {
-  if (r.d_scratch) cudaFree(r.d_scratch);
-  if (r.d_R) cudaFree(r.d_R);
+// Returns a request's device memory to the server's pool, ordered after the work already
+// issued on `stream`.
+void release_device(Request &r, cudaStream_t stream) {
+  if (r.d_scratch) cudaFreeAsync(r.d_scratch, stream);
+  if (r.d_R) cudaFreeAsync(r.d_R, stream);
   r.d_scratch = r.d_R = nullptr;
-  if (r.num) peers_free_numeric(r.num);
+  if (r.num) {
+    r.num->pool_stream = stream;
+    peers_free_numeric(r.num);
+  }
   r.num = nullptr;
 }
 
@@ -136,6 +169,11 @@ void worker_main(peers_server *sv) {
                            r->coords.empty() ? nullptr : r->coords.data(), r->dim, &sv->opt,
                            &r->sym);
     bool reserved = false;
+    if (rc == PEERS_OK && r->sym->S.spill_stride > 0) {
+      rc = PEERS_EINVAL;
+      r->err = "the request has supernode fronts larger than shared memory, which the server's "
+               "batched sweep does not take: use peers_query";
+    }
     if (rc == PEERS_OK) {
       const Symbolic &S = r->sym->S;
       r->footprint = peers_footprint_bytes(r->sym);
@@ -162,22 +200,33 @@ void worker_main(peers_server *sv) {
       }
       lk.unlock();
       if (rc == PEERS_OK) {
-        rc = peers_factor(ctx, r->sym, nullptr, &r->num);
-        if (rc != PEERS_OK) r->err = peers_last_error();
+        std::string err;
+        rc = factor_from_pool(ctx, r->sym, nullptr, sv->pool, &r->num, err);
+        if (rc != PEERS_OK) r->err = err;
       }
       if (rc == PEERS_OK) {
         const int64_t sc = S.carry_slots * (int64_t(S.nbmax) + 1);
-        if (cudaMalloc(&r->d_scratch, sizeof(double) * std::max<int64_t>(1, sc)) != cudaSuccess ||
-            cudaMalloc(&r->d_R, sizeof(double) * std::max<int64_t>(1, S.nq)) != cudaSuccess) {
+        void *a = nullptr, *b = nullptr;
+        if (cudaMallocFromPoolAsync(&a, sizeof(double) * std::max<int64_t>(1, sc), sv->pool,
+                                    ctx->stream) != cudaSuccess ||
+            cudaMallocFromPoolAsync(&b, sizeof(double) * std::max<int64_t>(1, S.nq), sv->pool,
+                                    ctx->stream) != cudaSuccess) {
           cudaGetLastError();
           rc = PEERS_ENOMEM;
           r->err = "device allocation of the request's sweep scratch";
-        } else if (S.nq > 0 &&
-                   cudaMemsetAsync(r->d_R, 0, sizeof(double) * S.nq, ctx->stream) != cudaSuccess) {
+        }
+        r->d_scratch = static_cast<double *>(a);
+        r->d_R = static_cast<double *>(b);
+        if (rc == PEERS_OK && S.nq > 0 &&
+            cudaMemsetAsync(r->d_R, 0, sizeof(double) * S.nq, ctx->stream) != cudaSuccess) {
           rc = PEERS_ECUDA;
           r->err = "clearing the request's results";
         }
-        cudaStreamSynchronize(ctx->stream);
+        // the factor, the scratch and the cleared R are ready for the server's stream
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == PEERS_OK) {
+          rc = PEERS_ECUDA;
+          r->err = "factorization stream failed";
+        }
       }
       if (rc == PEERS_OK) {
         for (size_t wv = 0; wv < S.waves.size() && S.nsorted + S.nq_two > 0; ++wv) {
@@ -195,12 +244,15 @@ void worker_main(peers_server *sv) {
         sv->used_bytes -= r->footprint;
         sv->admitted--;
       }
-    } else {
+    } else if (r->err.empty()) {
       r->err = peers_last_error();
+    }
+    if (rc != PEERS_OK) {
+      release_device(*r, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
     }
     std::lock_guard<std::mutex> lk(sv->mu);
     if (rc != PEERS_OK) {
-      release_device(*r);
       r->status = rc;
       r->done = true;
       r->t_done = Clock::now();
@@ -213,48 +265,79 @@ void worker_main(peers_server *sv) {
   peers_destroy(ctx);
 }
 
+// Grows a pinned/device buffer pair of the step thread to hold at least n entries.  Only
+// called for buffer b while no step that reads it is in flight.
 int ensure_items(peers_server *sv, int b, int64_t n) {
   if (n <= sv->items_cap[b]) return PEERS_OK;
   const int64_t cap = std::max<int64_t>(n, 2 * sv->items_cap[b]);
-  if (sv->d_items[b]) cudaFree(sv->d_items[b]);
+  if (sv->d_items[b]) cudaFreeAsync(sv->d_items[b], sv->stream);
   if (sv->h_items[b]) cudaFreeHost(sv->h_items[b]);
   sv->d_items[b] = nullptr;
   sv->h_items[b] = nullptr;
   sv->items_cap[b] = 0;
-  if (cudaMalloc(&sv->d_items[b], sizeof(SweepItem) * cap) != cudaSuccess ||
+  void *d = nullptr;
+  if (cudaMallocFromPoolAsync(&d, sizeof(SweepItem) * cap, sv->pool, sv->stream) != cudaSuccess ||
       cudaMallocHost(&sv->h_items[b], sizeof(SweepItem) * cap) != cudaSuccess) {
+    cudaGetLastError();
+    if (d) cudaFreeAsync(d, sv->stream);
+    return PEERS_ENOMEM;
+  }
+  sv->d_items[b] = static_cast<SweepItem *>(d);
+  sv->items_cap[b] = cap;
+  return PEERS_OK;
+}
+
+int ensure_stage(peers_server *sv, int b, int64_t n) {
+  if (n <= sv->stage_cap[b]) return PEERS_OK;
+  const int64_t cap = std::max<int64_t>(n, 2 * sv->stage_cap[b]);
+  if (sv->h_stage[b]) cudaFreeHost(sv->h_stage[b]);
+  sv->h_stage[b] = nullptr;
+  sv->stage_cap[b] = 0;
+  if (cudaMallocHost(&sv->h_stage[b], sizeof(double) * cap) != cudaSuccess) {
     cudaGetLastError();
     return PEERS_ENOMEM;
   }
-  sv->items_cap[b] = cap;
+  sv->stage_cap[b] = cap;
   return PEERS_OK;
 }
 
 int64_t step_cost(const Symbolic &S, const SweepItem &it) {
   if (it.kind == 2) return it.nq;
   const int64_t nc = peers::sn_nc(S, it.s), N = nc + S.nb[it.s], cols = nc - it.j0;
-  return int64_t(it.nq) * cols * (N - it.j0 - cols / 2);
+  return std::max<int64_t>(1, int64_t(it.nq) * cols * (N - it.j0 - cols / 2));
 }
 
-// Fills buffer b with the next step of every active request; returns the item count and the
-// launch's shared memory.
+// Fills buffer b with the next step: a share of the current level of every active request
+// (see the time slicing note at the top).  Sets each request's issue_end; returns the item
+// count, the launch's shared memory and the number of requests in the step.
 int64_t prepare_step(peers_server *sv, int b, std::vector<std::shared_ptr<Request>> &active,
-                     int64_t *smem_out, std::string &err) {
+                     int64_t *smem_out, int64_t *nreq_out, std::string &err) {
   std::vector<std::pair<int64_t, SweepItem>> step;
-  int64_t smem = 1024;
+  int64_t smem = 1024, nreq = 0;
+  int64_t sweeping = 0;
+  for (auto &r : active)
+    if (r->pos < r->steps.size() && !r->steps[r->pos].combine) ++sweeping;
+  const int64_t share = std::max<int64_t>(1, kStepQuantum / std::max<int64_t>(1, sweeping));
   for (auto &r : active) {
+    r->issue_end = r->next;
     if (r->pos >= r->steps.size()) continue;
     const ReqStep &st = r->steps[r->pos];
     const Symbolic &S = r->sym->S;
     const int32_t g = r->slot + st.wave;
+    ++nreq;
     if (!st.combine) {
       const SweepItem *src = S.waves[st.wave].items.data();
-      for (int64_t k = st.i0; k < st.i1; ++k) {
+      int64_t k = st.i0 + r->next, spent = 0;
+      while (k < st.i1 && (spent < share || k == st.i0 + r->next)) {
         SweepItem it = src[k];
         it.g = g;
-        step.push_back({step_cost(S, it), it});
+        const int64_t c = step_cost(S, it);
+        spent += c;
+        step.push_back({c, it});
         smem = std::max(smem, peers::sweep_smem_bytes(peers::sn_nc(S, it.s) + S.nb[it.s], it.nq));
+        ++k;
       }
+      r->issue_end = k - st.i0;
     } else {
       for (int64_t k = st.k0; k < st.k1; k += 4096) {
         SweepItem it{};
@@ -264,14 +347,16 @@ int64_t prepare_step(peers_server *sv, int b, std::vector<std::shared_ptr<Reques
         it.g = g;
         step.push_back({it.nq, it});
       }
+      r->issue_end = 0;
     }
   }
   std::stable_sort(step.begin(), step.end(),
                    [](const auto &x, const auto &y) { return x.first > y.first; });
   const int64_t n = static_cast<int64_t>(step.size());
+  *nreq_out = nreq;
   if (n == 0) return 0;
   if (ensure_items(sv, b, n) != PEERS_OK) {
-    err = "device allocation of the step's work list";
+    err = "allocation of the step's work list";
     return -1;
   }
   for (int64_t i = 0; i < n; ++i) sv->h_items[b][i] = step[i].second;
@@ -279,11 +364,41 @@ int64_t prepare_step(peers_server *sv, int b, std::vector<std::shared_ptr<Reques
   return n;
 }
 
+// Records the completion of the requests of finishing[b] (their step has finished).
+void retire(peers_server *sv, std::vector<std::shared_ptr<Request>> &fin, int b, cudaError_t e) {
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (e != cudaSuccess) sv->fatal = cudaGetErrorString(e);
+  for (auto &r : fin) {
+    r->t_done = Clock::now();
+    const int64_t nq = r->sym->S.nq;
+    if (e == cudaSuccess && nq > 0 && r->staged >= 0)
+      std::memcpy(r->R.data(), sv->h_stage[b] + r->staged, sizeof(double) * nq);
+    for (int32_t k = 0; k < static_cast<int32_t>(r->sym->S.waves.size()); ++k)
+      sv->slot_used[r->slot + k] = 0;
+    release_device(*r, sv->stream);
+    sv->used_bytes -= r->footprint;
+    sv->admitted--;
+    r->done = true;
+    if (e != cudaSuccess) {
+      r->status = PEERS_ECUDA;
+      r->err = std::string("sweep step failed: ") + cudaGetErrorString(e);
+      sv->failed++;
+    } else {
+      sv->completed++;
+      sv->queries += nq;
+      sv->request_steps += r->steps_in;
+      sv->latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
+      sv->t_last = r->t_done;
+    }
+  }
+  fin.clear();
+  sv->cv.notify_all();
+}
+
 void device_main(peers_server *sv) {
   cudaSetDevice(sv->device);
   std::vector<std::shared_ptr<Request>> active;
   std::vector<std::shared_ptr<Request>> finishing[2];
-  int64_t pending_n[2] = {0, 0};
   bool in_flight[2] = {false, false};
   int cur = 0;
   std::string err;
@@ -305,7 +420,7 @@ void device_main(peers_server *sv) {
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       if (active.empty() && !in_flight[0] && !in_flight[1]) {
-        sv->cv.wait(lk, [&] { return sv->stop || !sv->factored.empty(); });
+        sv->cv.wait(lk, [&] { return sv->stop || (!sv->factored.empty() && !sv->hold); });
         if (sv->factored.empty() && sv->stop && sv->pending.empty() && sv->admitted == 0) break;
         if (sv->factored.empty() && sv->stop) {
           // stop requested while workers still hold requests: keep waiting for them
@@ -316,7 +431,7 @@ void device_main(peers_server *sv) {
           }
         }
       }
-      while (!sv->factored.empty()) {
+      while (!sv->factored.empty() && !sv->hold) {
         auto r = sv->factored.front();
         const int32_t need = static_cast<int32_t>(r->sym->S.waves.size());
         int32_t base = -1;
@@ -329,20 +444,19 @@ void device_main(peers_server *sv) {
         sv->factored.pop_front();
         for (int32_t k = 0; k < need; ++k) sv->slot_used[base + k] = 1;
         r->slot = base;
-        std::vector<peers::SweepArgs> blocks;
         const Symbolic &S = r->sym->S;
-        for (const auto &W : S.waves) {
+        for (int32_t k = 0; k < need; ++k) {
           peers::SweepArgs a = sweep_args_of(r->num, S);
           a.carry = r->d_scratch;
           a.racc = r->d_scratch + S.carry_slots * int64_t(S.nbmax);
           a.R = r->d_R;
-          a.wave_base = W.q_begin;
-          blocks.push_back(a);
+          a.wave_base = S.waves[k].q_begin;
+          sv->h_table[base + k] = a;   // slots of retired requests only: no copy reads them
         }
-        if (!blocks.empty())
-          cudaMemcpyAsync(sv->d_table + base, blocks.data(),
-                          sizeof(peers::SweepArgs) * blocks.size(), cudaMemcpyHostToDevice,
-                          sv->stream);
+        if (need > 0)
+          cudaMemcpyAsync(sv->d_table + base, sv->h_table + base, sizeof(peers::SweepArgs) * need,
+                          cudaMemcpyHostToDevice, sv->stream);
+        r->R.resize(static_cast<size_t>(S.nq));
         if (r->steps.empty()) {   // nothing to walk (no queries or only u == v)
           finishing[cur].push_back(r);
         } else {
@@ -351,8 +465,8 @@ void device_main(peers_server *sv) {
       }
     }
     // 2. prepare and launch step `cur`
-    int64_t smem = 0;
-    const int64_t n = prepare_step(sv, cur, active, &smem, err);
+    int64_t smem = 0, nreq = 0;
+    const int64_t n = prepare_step(sv, cur, active, &smem, &nreq, err);
     if (n < 0) {
       fail_all(err);
       continue;
@@ -369,85 +483,66 @@ void device_main(peers_server *sv) {
         fail_all("sweep step launch failed: " + err);
         continue;
       }
+      std::lock_guard<std::mutex> lk(sv->mu);
       sv->steps++;
       sv->launches++;
+      sv->max_step_requests = std::max(sv->max_step_requests, nreq);
     }
-    // requests whose last step this is retire when the step completes
+    // advance every request past what this step issued; the finished ones retire when the
+    // step completes
     std::vector<std::shared_ptr<Request>> still;
     for (auto &r : active) {
-      if (r->pos < r->steps.size()) r->pos++;
+      if (r->pos < r->steps.size()) {
+        r->steps_in++;
+        const ReqStep &st = r->steps[r->pos];
+        if (st.combine || r->issue_end >= st.i1 - st.i0) {
+          r->pos++;
+          r->next = 0;
+        } else {
+          r->next = r->issue_end;
+        }
+      }
       if (r->pos >= r->steps.size()) finishing[cur].push_back(r);
       else still.push_back(r);
     }
     active.swap(still);
-    for (auto &r : finishing[cur]) {
-      const int64_t nq = r->sym->S.nq;
-      r->R.resize(static_cast<size_t>(nq));
-      if (nq > 0)
-        cudaMemcpyAsync(r->R.data(), r->d_R, sizeof(double) * nq, cudaMemcpyDeviceToHost,
-                        sv->stream);
+    {
+      int64_t total = 0;
+      for (auto &r : finishing[cur]) total += r->sym->S.nq;
+      if (ensure_stage(sv, cur, total) != PEERS_OK) {
+        fail_all("pinned allocation of the result staging buffer");
+        continue;
+      }
+      int64_t off = 0;
+      for (auto &r : finishing[cur]) {
+        const int64_t nq = r->sym->S.nq;
+        r->staged = off;
+        if (nq > 0)
+          cudaMemcpyAsync(sv->h_stage[cur] + off, r->d_R, sizeof(double) * nq,
+                          cudaMemcpyDeviceToHost, sv->stream);
+        off += nq;
+      }
     }
     cudaEventRecord(sv->ev[cur], sv->stream);
     in_flight[cur] = true;
-    pending_n[cur] = n;
     // 3. retire the previous step's finished requests once it has completed
     const int prev = cur ^ 1;
     if (in_flight[prev]) {
       const cudaError_t e = cudaEventSynchronize(sv->ev[prev]);
       in_flight[prev] = false;
+      retire(sv, finishing[prev], prev, e);
       if (e != cudaSuccess) {
         fail_all(std::string("sweep step failed: ") + cudaGetErrorString(e));
         continue;
       }
-      std::lock_guard<std::mutex> lk(sv->mu);
-      for (auto &r : finishing[prev]) {
-        r->t_done = Clock::now();
-        for (int32_t k = 0; k < static_cast<int32_t>(r->sym->S.waves.size()); ++k)
-          sv->slot_used[r->slot + k] = 0;
-        release_device(*r);
-        sv->used_bytes -= r->footprint;
-        sv->admitted--;
-        r->done = true;
-        sv->completed++;
-        sv->queries += r->sym->S.nq;
-        sv->latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
-        sv->t_last = r->t_done;
-      }
-      finishing[prev].clear();
-      sv->cv.notify_all();
     }
-    (void)pending_n;
     cur ^= 1;
-    if (active.empty() && !in_flight[cur] && !in_flight[cur ^ 1] && finishing[0].empty() &&
-        finishing[1].empty())
-      continue;
     if (active.empty() && in_flight[cur ^ 1]) {
       // nothing new to launch: drain the last step before sleeping
       const int last = cur ^ 1;
       const cudaError_t e = cudaEventSynchronize(sv->ev[last]);
       in_flight[last] = false;
-      std::lock_guard<std::mutex> lk(sv->mu);
-      if (e != cudaSuccess) sv->fatal = cudaGetErrorString(e);
-      for (auto &r : finishing[last]) {
-        r->t_done = Clock::now();
-        for (int32_t k = 0; k < static_cast<int32_t>(r->sym->S.waves.size()); ++k)
-          sv->slot_used[r->slot + k] = 0;
-        release_device(*r);
-        sv->used_bytes -= r->footprint;
-        sv->admitted--;
-        r->done = true;
-        if (e != cudaSuccess) {
-          r->status = PEERS_ECUDA;
-          sv->failed++;
-        } else {
-          sv->completed++;
-          sv->queries += r->sym->S.nq;
-          sv->latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
-          sv->t_last = r->t_done;
-        }
-      }
-      finishing[last].clear();
-      sv->cv.notify_all();
+      retire(sv, finishing[last], last, e);
     }
   }
 }
@@ -481,17 +576,32 @@ int peers_server_create(int device, int64_t mem_budget_bytes, int32_t max_active
   sv->budget = mem_budget_bytes > 0 ? mem_budget_bytes : (int64_t(64) << 30);
   sv->max_active = max_active > 0 ? max_active : 64;
   if (workers <= 0) workers = 4;
-  cudaSetDevice(device);
+  peers::DeviceGuard guard(device);
   sv->slot_used.assign(kTableSlots, 0);
-  if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&sv->d_table, sizeof(peers::SweepArgs) * kTableSlots) != cudaSuccess ||
-      cudaMalloc(&sv->d_counter, sizeof(int) * 2) != cudaSuccess ||
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  // keep freed memory in the pool (no release to the driver at synchronisation points)
+  uint64_t keep = UINT64_MAX;
+  void *tbl = nullptr, *ctr = nullptr;
+  if (guard.status() != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMemPoolCreate(&sv->pool, &props) != cudaSuccess ||
+      cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+      cudaMalloc(&tbl, sizeof(peers::SweepArgs) * kTableSlots) != cudaSuccess ||
+      cudaMallocHost(&sv->h_table, sizeof(peers::SweepArgs) * kTableSlots) != cudaSuccess ||
+      cudaMalloc(&ctr, sizeof(int) * 2) != cudaSuccess ||
       cudaEventCreateWithFlags(&sv->ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&sv->ev[1], cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
+    sv->d_table = static_cast<peers::SweepArgs *>(tbl);
+    sv->d_counter = static_cast<int *>(ctr);
     peers_server_destroy(sv);
     return peers_fail(PEERS_ECUDA, "server device setup failed");
   }
+  sv->d_table = static_cast<peers::SweepArgs *>(tbl);
+  sv->d_counter = static_cast<int *>(ctr);
   for (int32_t i = 0; i < workers; ++i) sv->workers.emplace_back(worker_main, sv);
   sv->device_thread = std::thread(device_main, sv);
   *out = sv;
@@ -588,6 +698,17 @@ int peers_server_get_stats(peers_server *sv, peers_server_stats *out) {
                     ? std::chrono::duration<double>(sv->t_last - sv->t_first).count()
                     : 0.0;
   out->qps = out->wall_s > 0 ? sv->queries / out->wall_s : 0.0;
+  out->max_step_requests = sv->max_step_requests;
+  out->request_steps = sv->request_steps;
+  out->ready = static_cast<int64_t>(sv->factored.size());
+  return PEERS_OK;
+}
+
+int peers_server_hold(peers_server *sv, int hold) {
+  if (!sv) return peers_fail(PEERS_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->hold = hold != 0;
+  sv->cv.notify_all();
   return PEERS_OK;
 }
 
@@ -596,22 +717,27 @@ void peers_server_destroy(peers_server *sv) {
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stop = true;
+    sv->hold = false;
   }
   sv->cv.notify_all();
   for (auto &t : sv->workers)
     if (t.joinable()) t.join();
   sv->cv.notify_all();
   if (sv->device_thread.joinable()) sv->device_thread.join();
-  cudaSetDevice(sv->device);
+  peers::DeviceGuard guard(sv->device);
   for (auto &kv : sv->reqs) {
-    release_device(*kv.second);
+    if (sv->stream) release_device(*kv.second, sv->stream);
     if (kv.second->sym) peers_free_symbolic(kv.second->sym);
   }
   for (int b = 0; b < 2; ++b) {
-    if (sv->d_items[b]) cudaFree(sv->d_items[b]);
+    if (sv->d_items[b]) cudaFreeAsync(sv->d_items[b], sv->stream);
     if (sv->h_items[b]) cudaFreeHost(sv->h_items[b]);
+    if (sv->h_stage[b]) cudaFreeHost(sv->h_stage[b]);
     if (sv->ev[b]) cudaEventDestroy(sv->ev[b]);
   }
+  if (sv->stream) cudaStreamSynchronize(sv->stream);
+  if (sv->pool) cudaMemPoolDestroy(sv->pool);
+  if (sv->h_table) cudaFreeHost(sv->h_table);
   if (sv->d_table) cudaFree(sv->d_table);
   if (sv->d_counter) cudaFree(sv->d_counter);
   if (sv->stream) cudaStreamDestroy(sv->stream);

@@ -163,7 +163,7 @@ extern "C" int peers_sparsify(peers_ctx *ctx, int64_t m, const double *w, const 
     return peers_fail(PEERS_EINVAL, "null argument or empty edge set");
   std::string err;
   auto run = [&]() -> int {
-    CUDA_TRY(cudaSetDevice(ctx->device));
+    DEVICE_SCOPE(ctx->device);
     cudaStream_t st = ctx->stream;
     const int64_t nb = (m + peers::kScanBlock - 1) / peers::kScanBlock;
     long long *C = nullptr, *bsum = nullptr, *total = nullptr;

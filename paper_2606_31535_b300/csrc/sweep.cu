@@ -21,6 +21,7 @@
 // The path is FP64 arithmetic bound (about 2 flops per 8-byte panel entry per query).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "device.cuh"
@@ -30,7 +31,10 @@ namespace peers {
 
 constexpr int kSweepThreads = 256;
 
-// One work item (see SweepItem) by one CTA of kSweepThreads threads.
+// One work item (see SweepItem) by one CTA of kSweepThreads threads.  SPILL: the tile's
+// fronts X live in this CTA's slice of the global scratch a.spill (fronts too large for
+// shared memory); Y and T stay in shared memory.  The arithmetic is the same either way.
+template <bool SPILL>
 __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs &a,
                                            double *smem) {
   if (it.kind == 2) {   // combine two-branch sums (multi-graph launches)
@@ -45,8 +49,9 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
   const int QP = static_cast<int>(sweep_qstride(Q));
   const int nch = (Q + 3) / 4;
-  double *X = smem;                    // N x QP   the tile's fronts, row-major
-  double *Y = X + int64_t(N) * QP;     // kBlock x QP   y of the current block
+  double *X = SPILL ? a.spill + int64_t(blockIdx.x) * a.spill_stride
+                    : smem;            // N x QP   the tile's fronts, row-major
+  double *Y = SPILL ? smem : X + int64_t(N) * QP;   // kBlock x QP   y of the current block
   double *T = Y + kBlock * QP;         // kBlock x QP   y^2 / d of the current block
   const int tid = threadIdx.x;
   const int32_t j0 = it.j0;
@@ -199,7 +204,26 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepItem *__restrict__ items,
                                                          SweepArgs a) {
   extern __shared__ double smem[];
-  sweep_item(items[blockIdx.x], a, smem);
+  sweep_item<false>(items[blockIdx.x], a, smem);
+}
+
+// The items of a level whose fronts do not fit shared memory: a persistent grid of at most
+// kSpillGrid CTAs pulling items (largest first) through *counter, each CTA working on its own
+// front scratch.
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_spill(const SweepItem *__restrict__ items,
+                                                               int64_t nitems, SweepArgs a,
+                                                               int *counter) {
+  extern __shared__ double smem[];
+  __shared__ int next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int64_t i = next;
+    __syncthreads();
+    if (i >= nitems) break;
+    sweep_item<true>(items[i], a, smem);
+    __syncthreads();
+  }
 }
 
 // Persistent multi-graph launch: as many CTAs as fit on the GPU, each pulling items (sorted
@@ -218,7 +242,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_multi(const SweepItem *
     __syncthreads();
     if (i >= nitems) break;
     const SweepItem it = items[i];
-    sweep_item(it, table[it.g], smem);
+    sweep_item<false>(it, table[it.g], smem);
     __syncthreads();
   }
 }
@@ -283,12 +307,29 @@ int run_sweep_wave(const Symbolic &S, const SweepWave &W, const SweepItem *d_ite
   if (rc != PEERS_OK) return rc;
   SweepArgs a = args;
   a.wave_base = W.q_begin;
+  int64_t nspill_total = 0;
+  for (int64_t x : W.level_nspill) nspill_total += x;
+  if (nspill_total > 0) {
+    if (!a.spill || !a.spill_counter) {
+      err = "the plan keeps fronts in global memory but no front scratch was given";
+      return PEERS_EINVAL;
+    }
+    CUDA_TRY(cudaMemsetAsync(a.spill_counter, 0, sizeof(int) * S.nlevels, stream));
+  }
   for (int32_t l = 0; l < S.nlevels; ++l) {
     const int64_t i0 = W.level_ptr[l], i1 = W.level_ptr[l + 1];
+    const int64_t ns = W.level_nspill.empty() ? 0 : W.level_nspill[l];
     if (events) CUDA_TRY(cudaEventRecord(events[2 * l], stream));
-    if (i1 > i0) {
-      k_sweep<<<static_cast<unsigned>(i1 - i0), kSweepThreads, W.level_smem[l], stream>>>(
-          d_items + i0, a);
+    if (ns > 0) {
+      const unsigned grid = static_cast<unsigned>(std::min<int64_t>(ns, kSpillGrid));
+      k_sweep_spill<<<grid, kSweepThreads, W.level_spill_smem[l], stream>>>(
+          d_items + i0, ns, a, a.spill_counter + l);
+      ++*launches;
+      CUDA_TRY(cudaGetLastError());
+    }
+    if (i1 > i0 + ns) {
+      k_sweep<<<static_cast<unsigned>(i1 - i0 - ns), kSweepThreads, W.level_smem[l], stream>>>(
+          d_items + i0 + ns, a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
     }

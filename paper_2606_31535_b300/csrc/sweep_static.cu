@@ -55,15 +55,27 @@ int query_noalloc(cudaStream_t stream, int device, const Symbolic &S, const Swee
                   const SweepItem *items, const int64_t *wave_item_off,
                   const int64_t *two_user, const int32_t *two_a, const int32_t *two_b,
                   double *R, int64_t *launches, std::string &err) {
-  const int64_t need = S.carry_slots * (int64_t(S.nbmax) + 1);
-  if (need > kNoAllocScratchDoubles) {
-    err = "the plan needs " + std::to_string(need) + " doubles of sweep scratch but the "
-          "static buffer holds " + std::to_string(kNoAllocScratchDoubles) +
-          "; analyse with a smaller carry budget (peers_options.carry_budget <= " +
-          std::to_string(kNoAllocScratchDoubles * 8) + " bytes) or use peers_query";
+  if (S.spill_stride > 0) {
+    err = "the plan keeps supernode fronts in global memory (fronts larger than shared "
+          "memory), which needs scratch beyond the static buffer: use peers_query";
     return PEERS_EINVAL;
   }
-  CUDA_TRY(cudaSetDevice(device));
+  const int64_t need = S.carry_slots * (int64_t(S.nbmax) + 1);
+  if (need > kNoAllocScratchDoubles) {
+    // The analysis counts 8 (nbmax + 1) bytes per query slot against the carry budget, so a
+    // budget of at most the static buffer's size always yields a plan that fits.
+    err = "the plan needs " + std::to_string(need) + " doubles of sweep scratch (" +
+          std::to_string(S.carry_slots) + " query slots x (" + std::to_string(S.nbmax) +
+          " + 1)) but the static buffer holds " + std::to_string(kNoAllocScratchDoubles) +
+          "; analyse with peers_options.carry_budget <= " +
+          std::to_string(kNoAllocScratchDoubles * 8) + " bytes, or use peers_query";
+    return PEERS_EINVAL;
+  }
+  DEVICE_SCOPE(device);
+  if (S.nq > 0) {
+    const int rc0 = check_device_result(device, R, err);
+    if (rc0 != PEERS_OK) return rc0;
+  }
   double *scratch = nullptr;
   int rc = scratch_on_device(device, &scratch, err);
   if (rc != PEERS_OK) return rc;

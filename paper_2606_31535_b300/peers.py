@@ -32,7 +32,8 @@ class Options(ctypes.Structure):
     _fields_ = [("ordering", ctypes.c_int32), ("nd_leaf", ctypes.c_int32),
                 ("relax_small", ctypes.c_int32), ("relax_max", ctypes.c_int32),
                 ("relax_frac", ctypes.c_double), ("carry_budget", ctypes.c_int64),
-                ("qcap", ctypes.c_int32 * 4), ("reserved", ctypes.c_int64 * 6)]
+                ("qcap", ctypes.c_int32 * 4), ("front_smem", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -48,7 +49,8 @@ class Stats(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "queries",
                                                "steps", "launches", "peak_bytes")] + \
-               [(k, ctypes.c_double) for k in ("wall_s", "qps", "p50_s", "p99_s", "mean_s")]
+               [(k, ctypes.c_double) for k in ("wall_s", "qps", "p50_s", "p99_s", "mean_s")] + \
+               [(k, ctypes.c_int64) for k in ("max_step_requests", "request_steps", "ready")]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -59,7 +61,7 @@ class Info(ctypes.Structure):
         "n", "n_reduced", "nnz_a", "nnz_l", "nsuper", "levels", "max_nc", "max_nb", "nq",
         "nq_trivial", "nq_two_branch", "walk_entries", "walk_fma", "factor_fma",
         "device_bytes")] + [("t_order", ctypes.c_double), ("t_symbolic", ctypes.c_double),
-                            ("t_queries", ctypes.c_double)]
+                            ("t_queries", ctypes.c_double), ("nsuper_spilled", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +105,7 @@ def load(path: str | None = None):
         "peers_server_poll": (ctypes.c_int, [vp, i64]),
         "peers_server_wait": (ctypes.c_int, [vp, i64, vp, i64, P(dbl)]),
         "peers_server_get_stats": (ctypes.c_int, [vp, P(ServerStats)]),
+        "peers_server_hold": (ctypes.c_int, [vp, ctypes.c_int]),
         "peers_server_destroy": (None, [vp]),
         "peers_retile": (ctypes.c_int, [vp, vp, vp, vp]),
         "peers_query_blockinv": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
@@ -115,7 +118,8 @@ def load(path: str | None = None):
         "peers_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "peers_last_stats": (ctypes.c_int, [vp, P(Stats)]),
         "peers_fp64_peak": (ctypes.c_int, [vp, P(dbl)]),
-        "peers_last_level_times": (ctypes.c_int, [vp, P(dbl), i64]),
+        "peers_last_level_times": (i64, [vp, P(dbl), i64]),
+        "peers_fp64_mma_shapes": (ctypes.c_int, [vp, P(dbl)]),
         "peers_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "peers_last_error": (ctypes.c_char_p, []),
         "peers_version": (ctypes.c_char_p, []),
@@ -141,6 +145,32 @@ def _ptr(a):
     if isinstance(a, np.ndarray):
         return a.ctypes.data_as(ctypes.c_void_p)
     return ctypes.c_void_p(int(a.data_ptr()))   # torch tensor
+
+
+def _out_flags(ctx: "Context", out, n: int, where: str, device_only: bool = False) -> int:
+    """Checks a result buffer before its pointer reaches the library (whose kernels write n
+    doubles through it) and returns the matching flags: a writable, contiguous float64 numpy
+    array of at least n entries (host), or a contiguous float64 torch CUDA tensor of at least
+    n entries on the context's device."""
+    if isinstance(out, np.ndarray):
+        if device_only:
+            raise ValueError(f"{where}: the result must be a CUDA tensor, not a numpy array")
+        if out.dtype != np.float64 or not out.flags.c_contiguous or not out.flags.writeable \
+                or out.size < n:
+            raise ValueError(f"{where}: the host result must be a writable contiguous float64 "
+                             f"array of at least {n} entries")
+        return 0
+    import torch
+    if not isinstance(out, torch.Tensor):
+        raise ValueError(f"{where}: the result must be a numpy array or a torch tensor")
+    if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous() \
+            or out.numel() < n:
+        raise ValueError(f"{where}: the device result must be a contiguous float64 CUDA tensor "
+                         f"of at least {n} entries")
+    if out.device.index != ctx.device:
+        raise ValueError(f"{where}: the result is on cuda:{out.device.index}, the context on "
+                         f"cuda:{ctx.device}")
+    return OUT_DEVICE
 
 
 class Context:
@@ -181,6 +211,12 @@ class Context:
         out = (ctypes.c_double * 3)()
         _check(load().peers_fp64_peak(self._h, out), "peers_fp64_peak")
         return {"dfma": out[0], "dmma": out[1], "dfma_with_dmma": out[2]}
+
+    def fp64_mma_shapes(self) -> dict:
+        """Measured FP64 tensor throughput (TFLOP/s) of every mma.sync .f64 shape."""
+        out = (ctypes.c_double * 4)()
+        _check(load().peers_fp64_mma_shapes(self._h, out), "peers_fp64_mma_shapes")
+        return {"m8n8k4": out[0], "m16n8k4": out[1], "m16n8k8": out[2], "m16n8k16": out[3]}
 
     def last_level_times(self) -> np.ndarray:
         buf = (ctypes.c_double * 4096)()
@@ -279,7 +315,7 @@ def query_blockinv(ctx: Context, sym: Symbolic, num: Numeric, out=None):
     lib = load()
     if out is None:
         out = np.empty(sym.nq, dtype=np.float64)
-    flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
+    flags = _out_flags(ctx, out, sym.nq, "query_blockinv")
     _check(lib.peers_query_blockinv(ctx._h, sym._h, num._h, _ptr(out), flags),
            "peers_query_blockinv")
     return out
@@ -291,7 +327,7 @@ def query_selinv(ctx: Context, sym: Symbolic, num: Numeric, out=None):
     lib = load()
     if out is None:
         out = np.empty(sym.nq, dtype=np.float64)
-    flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
+    flags = _out_flags(ctx, out, sym.nq, "query_selinv")
     _check(lib.peers_query_selinv(ctx._h, sym._h, num._h, _ptr(out), flags), "peers_query_selinv")
     return out
 
@@ -336,7 +372,7 @@ def query(ctx: Context, sym: Symbolic, num: Numeric, out=None):
     lib = load()
     if out is None:
         out = np.empty(sym.nq, dtype=np.float64)
-    flags = 0 if isinstance(out, np.ndarray) else OUT_DEVICE
+    flags = _out_flags(ctx, out, sym.nq, "query")
     _check(lib.peers_query(ctx._h, sym._h, num._h, _ptr(out), flags), "peers_query")
     return out
 
@@ -377,7 +413,12 @@ class Batch:
         if outs is None:
             outs = [np.empty(s.nq, dtype=np.float64) for s in self._syms]
         n = len(outs)
-        flags = 0 if isinstance(outs[0], np.ndarray) else OUT_DEVICE
+        if n != len(self._syms):
+            raise ValueError("Batch.query: one result buffer per graph")
+        flags = {_out_flags(self._ctx, o, s.nq, "Batch.query") for o, s in zip(outs, self._syms)}
+        if len(flags) != 1:
+            raise ValueError("Batch.query: all results on the host or all on the device")
+        flags = flags.pop()
         ptrs = (ctypes.c_void_p * n)(*[_ptr(o).value for o in outs])
         _check(load().peers_batch_query(self._ctx._h, self._h, ptrs, flags), "peers_batch_query")
         return outs
@@ -440,6 +481,11 @@ class Server:
                "peers_server_wait")
         return R, lat.value
 
+    def hold(self, on: bool = True):
+        """While held, factored requests wait instead of joining the sweep (stats()["ready"]
+        counts them); releasing lets them all join at the next step."""
+        _check(load().peers_server_hold(self._h, int(on)), "peers_server_hold")
+
     def stats(self) -> dict:
         st = ServerStats()
         _check(load().peers_server_get_stats(self._h, ctypes.byref(st)), "peers_server_get_stats")
@@ -449,6 +495,7 @@ class Server:
 def query_noalloc(ctx: Context, sym: Symbolic, num: Numeric, out):
     """Resistances into the device tensor `out` (float64, sym.nq entries) with the library's
     static scratch array: the library allocates no device memory during the call."""
+    _out_flags(ctx, out, sym.nq, "query_noalloc", device_only=True)
     _check(load().peers_query_noalloc(ctx._h, sym._h, num._h, _ptr(out)), "peers_query_noalloc")
     return out
 

@@ -1,5 +1,8 @@
-"""Writes grid4096_sample.json: oracle resistances of 2000 seeded edges of the 4096 x 4096
-grid (log-uniform conductances 1e-3..1e3, seed 5, node 0 grounded).
+"""Writes grid4096_sample.json: oracle resistances of 3000 edges of the 4096 x 4096 grid
+(log-uniform conductances 1e-3..1e3, seed 5, node 0 grounded): 2000 drawn uniformly with a
+fixed seed, and the 1000 edges of largest conductance.  The latter have the smallest
+resistances, R_e <= 1/w_e, where y = z_lo - z_hi cancels the most, so they are the edges most
+exposed to rounding.
 
 The oracle has to factor the whole 16.7M-node Laplacian before it can answer any query, which
 takes tens of minutes on one core, so these values are computed once by this script (which
@@ -21,6 +24,7 @@ import oracle  # noqa: E402
 from paper_2606_31535_b300 import inputs as I  # noqa: E402
 
 SAMPLE = 2000
+HEAVY = 1000
 SEED = 4096
 
 
@@ -28,14 +32,19 @@ def main():
     t0 = time.time()
     g = I.grid4096()
     u, v = g.all_edges()
-    idx = np.sort(np.random.default_rng(SEED).choice(u.size, SAMPLE, replace=False))
+    uni = np.random.default_rng(SEED).choice(u.size, SAMPLE, replace=False)
+    heavy = np.argsort(-g.edge_weights(), kind="stable")
+    heavy = heavy[~np.isin(heavy, uni)][:HEAVY]
+    idx = np.sort(np.concatenate([uni, heavy]))
     F = oracle.Factor.of(g)
     t1 = time.time()
     R = F.resistance(u[idx], v[idx])
     t2 = time.time()
     out = {
-        "about": "oracle (oracle/oracle.c) effective resistances of a seeded sample of edges of "
-                 "the 4096x4096 grid, log-uniform conductances 1e-3..1e3, seed 5, ground 0",
+        "about": "oracle (oracle/oracle.c) effective resistances of edges of the 4096x4096 "
+                 "grid, log-uniform conductances 1e-3..1e3, seed 5, ground 0: a seeded uniform "
+                 "sample of 2000 edges and the 1000 other edges of largest conductance",
+        "selection": {"uniform": SAMPLE, "uniform_seed": SEED, "largest_conductance": HEAVY},
         "script": "tests/golden/make_grid4096_sample.py",
         "sample_seed": SEED,
         "edge_index": idx.tolist(),

@@ -210,3 +210,19 @@ def test_route_plan_costs_concurrent_and_cached(P):
     assert all(o[:2] == fresh[0] for o in out)
     assert len({o[2] for o in out}) == 1 and out[0][2] > 0
     assert fresh[0][0] > 0 and fresh[0][1] > 0
+
+
+def test_small_front_budget_moves_fronts_to_global_memory(P):
+    """A lowered shared-memory budget marks the supernodes whose fronts no longer fit (their
+    sweep fronts go to global memory) without changing the work of any query."""
+    g = I.grid2d(60, 61, seed=91)
+    base = P.Symbolic.of(g).info()
+    assert base["nsuper_spilled"] == 0
+    counts = []
+    for fs in (1, 4 << 10, 64 << 10):
+        opt = P.Options()
+        opt.front_smem = fs
+        info = P.Symbolic.of(g, options=opt).info()
+        assert info["walk_entries"] == base["walk_entries"]
+        counts.append(info["nsuper_spilled"])
+    assert counts[0] == base["nsuper"] and 0 < counts[1] < base["nsuper"] and counts[2] == 0

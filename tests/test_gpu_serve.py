@@ -107,3 +107,30 @@ def test_server_analysis_options_keep_results(P):
     st = sv.stats()
     assert st["completed"] == len(reqs) and st["failed"] == 0
     sv.close()
+
+
+def test_requests_share_steps(P):
+    """Continuous batching proper: requests held until all are factored, then released
+    together, are swept in shared launches (a step carries work of several requests, and the
+    steps run are fewer than the requests' own step counts added up), and every result is
+    still bit-identical to its solo sweep."""
+    import time
+    reqs = requests()
+    ctx = P.Context(0)
+    ref = [alone(P, ctx, *r)[0] for r in reqs]
+    sv = P.Server(0, workers=3)
+    sv.hold(True)
+    tickets = [sv.submit(g, qu, qv) for g, qu, qv in reqs]
+    t0 = time.time()
+    while sv.stats()["ready"] < len(reqs):
+        assert time.time() - t0 < 120, "requests were not factored in time"
+        time.sleep(0.01)
+    sv.hold(False)
+    for i, t in enumerate(tickets):
+        R, _ = sv.wait(t)
+        assert np.array_equal(R, ref[i]), i
+    st = sv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["max_step_requests"] >= 2
+    assert st["steps"] < st["request_steps"]
+    sv.close()

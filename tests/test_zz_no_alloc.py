@@ -53,6 +53,43 @@ def test_noalloc_matches_query_on_two_calls_in_a_row(P):
         assert np.all(got[~nz] == 0.0)
 
 
+def test_noalloc_fits_any_plan_under_a_16_mib_budget(P):
+    """A carry budget equal to the static buffer's 16 MiB must give a plan that fits it, here
+    with several waves (more queries than one wave of the budget holds)."""
+    import torch
+    g = I.grid2d(200, 200, seed=34)
+    opt = P.Options()
+    opt.carry_budget = 16 << 20
+    ctx = P.Context(0)
+    sym = P.Symbolic.of(g, options=opt)
+    info = sym.info()
+    slot_bytes = 8 * (info["max_nb"] + 1)
+    assert sym.nq > (16 << 20) // slot_bytes      # more than one wave
+    num = P.Numeric(ctx, sym)
+    ref = P.query(ctx, sym, num)
+    for _ in range(2):
+        out = torch.full((sym.nq,), float("nan"), dtype=torch.float64, device="cuda:0")
+        P.query_noalloc(ctx, sym, num, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.max(np.abs(got - ref) / np.abs(ref)) <= TOL
+
+
+def test_noalloc_rejects_bad_result_buffers(P):
+    """The binding refuses a result buffer the kernels could not write safely."""
+    import torch
+    g = I.grid2d(12, 13, seed=35)
+    ctx = P.Context(0)
+    sym = P.Symbolic.of(g)
+    num = P.Numeric(ctx, sym)
+    for bad in (np.empty(sym.nq),                                              # host array
+                torch.empty(sym.nq, dtype=torch.float32, device="cuda:0"),     # float32
+                torch.empty(sym.nq - 1, dtype=torch.float64, device="cuda:0"),  # too short
+                torch.empty(2 * sym.nq, dtype=torch.float64, device="cuda:0")[::2]):  # strided
+        with pytest.raises(ValueError):
+            P.query_noalloc(ctx, sym, num, bad)
+
+
 def test_noalloc_rejects_a_plan_larger_than_its_scratch(P):
     import torch
     g = I.grid2d(200, 200, seed=33)   # default plan: one wave of 79 600 queries

@@ -177,10 +177,13 @@ def k_sweep_source_sha(text):
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per k_sweep launch from the committed ncu capture of this workload, or None
-    when there is none or the kernel source has changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "k_sweep_dram_%s.json" % workload)
+def profiled_traffic(info, launches_per_step):
+    """DRAM bytes per k_sweep launch of this plan, scaled from the committed ncu capture of a
+    smaller sweep (the 512x512 grid) by the query-front bytes each sweep carries between
+    levels (the DRAM traffic of the walk is those fronts, written at one level and read at
+    the next; the panels are re-read from L2).  None when there is no capture or the kernel
+    source has changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "k_sweep_dram_grid512.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
@@ -188,7 +191,10 @@ def profiled_traffic(workload):
             sha = k_sweep_source_sha(fh.read())
     except (OSError, ValueError):
         return None
-    return rec["dram_bytes_per_launch"] if rec.get("k_sweep_source_sha256_16") == sha else None
+    if rec.get("k_sweep_source_sha256_16") != sha or not info.get("front_bytes"):
+        return None
+    per_front_byte = rec["dram_bytes_per_sweep"] / rec["front_bytes"]
+    return per_front_byte * info["front_bytes"] / max(1, launches_per_step)
 
 def tuning_cache():
     """Tile-autotuner cache file: $PEERS_TUNING_CACHE, else one in the system temp dir."""
@@ -409,8 +415,10 @@ def run_ours(args):
                          % (8e-9 * info["nnz_l"], 1e-9 * info["device_bytes"])},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak if fp64_peak else None,
-                     "traffic": profiled_traffic(args.workload),
-                     "traffic_note": "DRAM bytes per k_sweep launch (ncu, profiles/)",
+                     "traffic": profiled_traffic(info, launches // args.steps),
+                     "traffic_note": "DRAM bytes per k_sweep launch: the ncu capture of the "
+                                     "512x512 grid's sweep (profiles/), scaled by the query-"
+                                     "front bytes carried between levels",
                      "kernel": "k_sweep (FP64 DFMA; peak = DFMA throughput measured live; "
                                "mma.sync f64 m8n8k4 %.3f, m16n8k4 %.3f, m16n8k8 %.3f, "
                                "m16n8k16 %.3f TFLOP/s, DFMA and m8n8k4 at once %.3f)"

@@ -100,6 +100,8 @@ typedef struct peers_info {
   double t_order, t_symbolic, t_queries; /* host seconds of the analysis phases */
   int64_t nsuper_spilled; /* supernodes whose sweep fronts live in global memory (fronts
                              larger than a CTA's shared memory; see peers_options) */
+  int64_t front_bytes;    /* bytes of query fronts one sweep reads from and writes to the
+                             carry buffer between levels (single-path queries) */
 } peers_info;
 
 /* ---- context --------------------------------------------------------------------------- */
@@ -188,7 +190,8 @@ int64_t peers_blockinv_fma(const peers_symbolic *sym);
  * PEERS_EINVAL, PEERS_ENOMEM, PEERS_ECUDA. */
 int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
                        double *R, int flags);
-/* FMAs of the selected inversion for this plan. */
+/* Useful multiply-adds of the selected inversion for this plan: Sigma[B,C], the lower
+ * triangle of Sigma[C,C], and the phase that forms T^{-1} and M = P T^{-1}. */
 int64_t peers_selinv_fma(const peers_symbolic *sym);
 
 /* ---- spectral sparsification (PEERS §II-B, Alg. 1) ---------------------------------------- */
@@ -355,9 +358,10 @@ int peers_last_stats(const peers_ctx *ctx, peers_stats *out);
 
 /* Device milliseconds per step of the last timed call on the context, into
  * ms[0 .. min(count, cap)), where the steps are: for peers_query, each sweep launch (one per
- * etree level, leaves first, summed over waves); for peers_factor, each etree level (leaves
- * first); for peers_query_selinv, phase 1 (T^{-1} and M) and then each tree depth (root
- * first); for peers_query_blockinv, the diagonal inverses, M, each tree depth of Z blocks
+ * etree level, leaves first, summed over waves); for peers_query_selinv, phase 1 (T^{-1} and
+ * M) of the part above the concurrent subtrees, each tree depth of that part (root first), and
+ * then the concurrent subtrees, which run on several CUDA streams at once, as one step; for
+ * peers_query_blockinv, the diagonal inverses, M, each tree depth of Z blocks
  * (root first) and the query pass.  Returns the step count or a negative status (PEERS_EINVAL for a null context, or a
  * null ms with cap > 0). */
 int64_t peers_last_level_times(const peers_ctx *ctx, double *ms, int64_t cap);

@@ -390,6 +390,7 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
   S.carry_slots = 0;
   S.walk_entries = 0;
   S.walk_fma = 0;
+  S.front_bytes = 0;
   auto item_fma = [&](int32_t s, int32_t j0) -> int64_t {
     const int64_t nc = sn_nc(S, s), N = nc + S.nb[s];
     int64_t f = 0;
@@ -440,6 +441,8 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
             it.j0 = (j0 / kBlock) * kBlock;
             const int64_t f = it.nq * item_fma(p, it.j0);
             S.walk_fma += f;
+            // fronts carried between levels: read from the child's carry, written for the parent
+            S.front_bytes += int64_t(8) * it.nq * ((src >= 0 ? S.nb[src] : 0) + S.nb[p]);
             lv.push_back({f, it});
           }
         };
@@ -886,56 +889,140 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     }
   }
 
+  // ---- lanes: independent subtrees on separate CUDA streams ----
+  // The supernodes at the first depth that has at least 2 kLanes of them root disjoint
+  // subtrees; these are dealt to kLanes lanes, largest first (by N^2 n_c, the order of their
+  // dense work), to the least loaded lane.  The factorization and the selected inversion run
+  // each lane on its own stream, so that launches of different subtrees overlap and fill each
+  // other's partial last waves; the supernodes above the cut (lane -1) run on the context's
+  // stream.  A lane's arithmetic is that of the one-stream schedule, in the same order.
+  S.depth.assign(static_cast<size_t>(ns), 0);
+  for (int32_t s = ns - 1; s >= 0; --s) S.depth[s] = S.parent[s] == -1 ? 0 : S.depth[S.parent[s]] + 1;
+  S.lane_of.assign(static_cast<size_t>(ns), -1);
+  S.nlanes = 0;
+  {
+    int32_t maxd = 0;
+    for (int32_t s = 0; s < ns; ++s) maxd = std::max(maxd, S.depth[s]);
+    std::vector<int32_t> per_depth(static_cast<size_t>(maxd) + 1, 0);
+    for (int32_t s = 0; s < ns; ++s) per_depth[S.depth[s]]++;
+    int32_t cut = -1;
+    for (int32_t d = 0; d <= maxd && cut < 0; ++d)
+      if (per_depth[d] >= 2 * kLanes) cut = d;
+    if (cut > 0) {
+      std::vector<double> work(static_cast<size_t>(ns), 0.0);
+      for (int32_t s = 0; s < ns; ++s) {
+        const double nc = sn_nc(S, s), N = nc + S.nb[s];
+        work[s] += N * N * nc;
+        if (S.parent[s] != -1) work[S.parent[s]] += work[s];   // children precede parents
+      }
+      std::vector<int32_t> roots;
+      for (int32_t s = 0; s < ns; ++s)
+        if (S.depth[s] == cut) roots.push_back(s);
+      std::stable_sort(roots.begin(), roots.end(),
+                       [&](int32_t x, int32_t y) { return work[x] > work[y]; });
+      std::vector<double> load(kLanes, 0.0);
+      std::vector<int32_t> lane_root(static_cast<size_t>(ns), -1);
+      for (int32_t r : roots) {
+        const int32_t L = static_cast<int32_t>(std::min_element(load.begin(), load.end()) -
+                                               load.begin());
+        load[L] += work[r];
+        lane_root[r] = L;
+      }
+      // every supernode below the cut follows its depth-`cut` ancestor (parents come later
+      // in postorder, so walk from the top down)
+      for (int32_t s = ns - 1; s >= 0; --s) {
+        if (S.depth[s] == cut) S.lane_of[s] = lane_root[s];
+        else if (S.depth[s] > cut) S.lane_of[s] = S.lane_of[S.parent[s]];
+      }
+      S.nlanes = kLanes;
+    }
+  }
+
   // ---- factorization schedule ----
-  S.level_nblocks.assign(static_cast<size_t>(S.nlevels), 0);
-  S.trail_base.assign(static_cast<size_t>(S.nlevels) + 1, 0);
+  // Groups of supernodes of one level and one lane, in issue order: every level of every lane
+  // (lanes interleaved level by level), then the levels of the top part.  In a group, small
+  // one-block supernodes are factored whole by one CTA each; the rest by the blocked kernels,
+  // column block by column block, widest first.
+  S.fgroups.clear();
+  S.fuse_sn.clear();
+  S.fac_sn.clear();
   S.trail_off.clear();
   S.trail_na.clear();
+  S.trail_ts.clear();
   S.trail_prefix.clear();
-  for (int32_t l = 0; l < S.nlevels; ++l) {
-    const int32_t *ls = S.level_sn.data() + S.level_ptr[l];
-    const int32_t cnt = S.level_ptr[l + 1] - S.level_ptr[l];
-    const int32_t nblk = (sn_nc(S, ls[0]) + kBlock - 1) / kBlock;
-    S.level_nblocks[l] = nblk;
-    S.trail_base[l + 1] = S.trail_base[l] + nblk;
-    for (int32_t J = 0; J < nblk; ++J) {
+  S.ea_off.clear();
+  S.ea_pairs.clear();
+  auto add_group = [&](int32_t lane, int32_t l) {
+    FactorGroup G{};
+    G.lane = lane;
+    G.level = l;
+    G.fuse_b = static_cast<int32_t>(S.fuse_sn.size());
+    G.fac_b = static_cast<int32_t>(S.fac_sn.size());
+    for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
+      const int32_t s = S.level_sn[i];
+      if (S.lane_of[s] != lane) continue;
+      if (sn_nc(S, s) <= kBlock && sn_nc(S, s) + S.nb[s] <= kFactorFuseN)
+        S.fuse_sn.push_back(s);
+      else
+        S.fac_sn.push_back(s);
+    }
+    G.fuse_e = static_cast<int32_t>(S.fuse_sn.size());
+    G.fac_e = static_cast<int32_t>(S.fac_sn.size());
+    if (G.fuse_e == G.fuse_b && G.fac_e == G.fac_b) return;
+    const int32_t *ls = S.fac_sn.data() + G.fac_b;
+    const int32_t cnt = G.fac_e - G.fac_b;
+    G.nblocks = cnt > 0 ? (sn_nc(S, ls[0]) + kBlock - 1) / kBlock : 0;
+    G.trail_base = static_cast<int64_t>(S.trail_na.size());
+    for (int32_t J = 0; J < G.nblocks; ++J) {
       int32_t na = 0;
       while (na < cnt && sn_nc(S, ls[na]) > J * kBlock) ++na;
+      // tiles of 64, or of 32 when 64-tiles would not give every SM a few of them
+      auto tiles = [&](int64_t ts) {
+        int64_t acc = 0;
+        for (int32_t i = 0; i < na; ++i) {
+          const int64_t nc = sn_nc(S, ls[i]), N = nc + S.nb[ls[i]];
+          const int64_t T = (N - std::min<int64_t>(nc, (J + 1) * kBlock) + ts - 1) / ts;
+          acc += T * (T + 1) / 2;
+        }
+        return acc;
+      };
+      const int64_t ts = tiles(kTile) < kTrailFewTiles ? kTile / 2 : kTile;
       S.trail_off.push_back(static_cast<int64_t>(S.trail_prefix.size()));
       S.trail_na.push_back(na);
+      S.trail_ts.push_back(static_cast<int32_t>(ts));
       int64_t acc = 0;
       S.trail_prefix.push_back(0);
       for (int32_t i = 0; i < na; ++i) {
         const int32_t s = ls[i];
         const int64_t nc = sn_nc(S, s), N = nc + S.nb[s];
         const int64_t t0 = std::min<int64_t>(nc, (J + 1) * kBlock);
-        const int64_t T = (N - t0 + kTile - 1) / kTile;
+        const int64_t T = (N - t0 + ts - 1) / ts;
         acc += T * (T + 1) / 2;
         S.trail_prefix.push_back(acc);
       }
     }
-  }
-  S.ea_base.assign(static_cast<size_t>(S.nlevels) + 1, 0);
-  S.ea_off.clear();
-  S.ea_pairs.clear();
-  for (int32_t l = 0; l < S.nlevels; ++l) {
+    // extend-add of the blocked supernodes' children, one launch per child rank (the
+    // supernodes factored whole add their children's update matrices themselves)
     int32_t maxc = 0;
-    for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
-      const int32_t s = S.level_sn[i];
-      maxc = std::max(maxc, S.child_ptr[s + 1] - S.child_ptr[s]);
-    }
-    S.ea_base[l + 1] = S.ea_base[l] + maxc;
+    for (int32_t i = 0; i < cnt; ++i)
+      maxc = std::max(maxc, S.child_ptr[ls[i] + 1] - S.child_ptr[ls[i]]);
+    G.ea_b = static_cast<int64_t>(S.ea_off.size());
     for (int32_t r = 0; r < maxc; ++r) {
       S.ea_off.push_back(static_cast<int64_t>(S.ea_pairs.size() / 2));
-      for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
-        const int32_t s = S.level_sn[i];
+      for (int32_t i = 0; i < cnt; ++i) {
+        const int32_t s = ls[i];
         if (S.child_ptr[s] + r < S.child_ptr[s + 1]) {
           S.ea_pairs.push_back(s);
           S.ea_pairs.push_back(S.child_list[S.child_ptr[s] + r]);
         }
       }
     }
-  }
+    G.ea_e = static_cast<int64_t>(S.ea_off.size());
+    S.fgroups.push_back(G);
+  };
+  for (int32_t l = 0; l < S.nlevels; ++l)
+    for (int32_t L = 0; L < S.nlanes; ++L) add_group(L, l);
+  for (int32_t l = 0; l < S.nlevels; ++l) add_group(-1, l);
   S.ea_off.push_back(static_cast<int64_t>(S.ea_pairs.size() / 2));
   S.t_symbolic = since(t1);
   auto t2 = Clock::now();

@@ -605,9 +605,8 @@ struct SiArgs {
   const int64_t *doff;
   const double *M;        // n_b x n_c row-major per supernode
   const int64_t *moff;
-  const int64_t *foff;    // offset of F(s) in its depth's buffer
-  const double *Fprev;    // inverse fronts of the previous depth
-  double *Fcur;           // inverse fronts of this depth
+  const int64_t *foff;    // offset of F(s) in F (each lane's region alternates by depth)
+  double *F;              // inverse fronts
 };
 
 // Sigma[B,B] of each supernode of this depth from its parent's front.  grid = (supernode,
@@ -620,8 +619,8 @@ __global__ void __launch_bounds__(256) k_si_gather(const int32_t *__restrict__ s
   const int32_t j0 = blockIdx.y * 8;
   if (j0 >= nbv) return;
   const int32_t *rm = a.rmap + a.rows_off[s];
-  const double *Fp = a.Fprev + a.foff[p];
-  double *F = a.Fcur + a.foff[s];
+  const double *Fp = a.F + a.foff[p];
+  double *F = a.F + a.foff[s];
   for (int32_t j = j0; j < min(nbv, j0 + 8); ++j) {
     const int32_t rj = rm[j];
     for (int32_t i = threadIdx.x; i < nbv; i += blockDim.x) {
@@ -640,7 +639,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) k_si_bc(const Tile *__restric
   const Tile tl = tiles[blockIdx.x];
   const int32_t s = tl.t;
   const int32_t nc = a.first[s + 1] - a.first[s], nbv = a.nb[s], N = nc + nbv;
-  double *F = a.Fcur + a.foff[s];
+  double *F = a.F + a.foff[s];
   RowsGemm g;
   g.A = F + int64_t(nc) * N + nc;
   g.lda = N;
@@ -666,7 +665,7 @@ __device__ __forceinline__ void si_cc_tile(const Tile &tl, const SiArgs &a, doub
   constexpr int U = TS / 16;
   const int32_t s = tl.t;
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
-  double *F = a.Fcur + a.foff[s];
+  double *F = a.F + a.foff[s];
   const double *Zd = a.Zd + a.doff[s];
   const double *M = a.M + a.moff[s];
   const int R0 = tl.r * TS, C0 = tl.c * TS;
@@ -762,7 +761,7 @@ __global__ void __launch_bounds__(256) k_si_small(const int32_t *__restrict__ sn
   if (p >= 0) {
     const int32_t Np = a.first[p + 1] - a.first[p] + a.nb[p];
     const int32_t *rm = a.rmap + a.rows_off[s];
-    const double *Fp = a.Fprev + a.foff[p];
+    const double *Fp = a.F + a.foff[p];
     for (int e = tid; e < nbv * nbv; e += blockDim.x) {
       const int i = e % nbv, j = e / nbv;
       const int32_t ri = rm[i], rj = rm[j];
@@ -797,7 +796,7 @@ __global__ void __launch_bounds__(256) k_si_small(const int32_t *__restrict__ sn
     F[j * N + i] = acc;
   }
   __syncthreads();
-  double *Fg = a.Fcur + a.foff[s];
+  double *Fg = a.F + a.foff[s];
   for (int e = tid; e < N * N; e += blockDim.x) Fg[e] = F[e];
   for (int64_t q = b.qbeg[s] + tid; q < b.qbeg[s + 1]; q += blockDim.x) {
     const int32_t qa = b.qa[q], qb = b.qb[q];
@@ -812,7 +811,7 @@ __global__ void k_si_query(const SiQuery *__restrict__ qs, int64_t nq, SiArgs ar
   if (k >= nq) return;
   const SiQuery q = qs[k];
   const int32_t N = args.first[q.s + 1] - args.first[q.s] + args.nb[q.s];
-  const double *F = args.Fcur + args.foff[q.s];
+  const double *F = args.F + args.foff[q.s];
   double r = F[int64_t(q.a) * N + q.a];
   if (q.b >= 0) r += F[int64_t(q.b) * N + q.b] - 2.0 * F[int64_t(min(q.a, q.b)) * N + max(q.a, q.b)];
   R[q.out] = r;
@@ -1047,33 +1046,47 @@ int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, T
 
 // ---------------------------------------------------------------- selected inversion plan
 
+// One group of the selected inversion: the supernodes of one tree depth in one lane (lane -1:
+// the part above the lanes' subtrees, on the context's stream), with the ranges of its
+// launches in the plan's lists.
+struct SiGroup {
+  int32_t lane = -1, depth = 0;
+  int64_t fused_b = 0, fused_e = 0, fused_smem = 0;   // whole small supernodes
+  int64_t gather_b = 0, gather_e = 0;
+  int32_t gather_ych = 0;                              // column chunks of the largest B
+  int64_t bc_ptr[4] = {0, 0, 0, 0};                    // Sigma[B,C] tiles, three width groups
+  int32_t bc_rows = 0;                                 // rows per Sigma[B,C] CTA
+  int64_t cc_b = 0, cc_e = 0;
+  int64_t q_b = 0, q_e = 0;
+};
+
+// Phase 1 (T^{-1} and M) of one lane's supernodes (index lane + 1).
+struct SiPhase1 {
+  int64_t small_b = 0, small_e = 0, diag_b = 0, diag_e = 0;
+  std::vector<int64_t> m_ptr;   // 4 entries into m_tiles
+};
+
 struct SelInvPlan {
   std::vector<int32_t> ncs;                        // n_c per supernode (ld of Zd)
   std::vector<int64_t> doff, moff;
   int64_t dtotal = 0, mtotal = 0;
-  std::vector<int64_t> foff;                       // offset of F(s) in its depth's buffer
-  int64_t fbuf = 0;                                // largest depth buffer (doubles)
-  std::vector<std::vector<int32_t>> depth_sn;      // supernodes by depth
-  std::vector<int32_t> gather_sn;                  // per depth, consecutive
-  std::vector<int64_t> gather_ptr;
-  std::vector<int32_t> gather_ych;                 // max column chunks per depth
+  std::vector<int64_t> foff;                       // offset of F(s) in the fronts buffer
+  int64_t fbuf = 0;                                // doubles of the fronts buffer
+  int32_t nlanes = 0;
+  std::vector<SiGroup> groups;                     // top part by depth, then lanes by depth
+  std::vector<SiPhase1> phase1;                    // per lane + 1
+  std::vector<int32_t> gather_sn;
   std::vector<Tile> bc, cc;
-  std::vector<int64_t> bc_ptr, cc_ptr;             // bc_ptr: 3 width groups per depth
-  std::vector<int32_t> bc_rows;                    // rows per Sigma[B,C] CTA, per depth
   std::vector<SiQuery> queries;
-  std::vector<int64_t> q_ptr;
-  std::vector<int32_t> fused_sn;                   // whole small supernodes, by depth
-  std::vector<int64_t> fused_ptr;
-  std::vector<int64_t> fused_smem;                 // dynamic shared memory per depth
+  std::vector<int32_t> fused_sn;                   // whole small supernodes
   std::vector<int32_t> small_sn, small_chunk, diag_sn, diag_blk;
   std::vector<Tile> m_tiles;
-  std::vector<int64_t> m_ptr;
   int64_t fma = 0;
 };
 
-// sms: the device's multiprocessor count (sizes the Sigma[B,C] launches).
+// sms: the device's multiprocessor count (sizes the launches).  The groups of the lanes run
+// concurrently on the lanes' streams, so each is sized for its share of the device.
 int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
-  const int64_t target_ctas = int64_t(std::max(sms, 1)) * 16;
   if (S.nq_two > 0) {
     err = "the selected inverse covers pairs inside the pattern of L (every graph edge and "
           "every pair touching the ground); this plan lists " + std::to_string(S.nq_two) +
@@ -1081,144 +1094,180 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
     return PEERS_EINVAL;
   }
   const int32_t ns = S.nsuper;
-  std::vector<int32_t> depth(ns, 0);
+  const int32_t nl = S.nlanes;
+  P.nlanes = nl;
   int32_t maxd = 0;
-  for (int32_t t = ns - 1; t >= 0; --t) {
-    depth[t] = S.parent[t] >= 0 ? depth[S.parent[t]] + 1 : 0;
-    maxd = std::max(maxd, depth[t]);
-  }
+  for (int32_t t = 0; t < ns; ++t) maxd = std::max(maxd, S.depth[t]);
   P.ncs.resize(ns);
   P.doff.assign(ns + 1, 0);
   P.moff.assign(ns + 1, 0);
   P.foff.assign(ns, 0);
-  P.depth_sn.assign(maxd + 1, {});
-  std::vector<int64_t> fsize(maxd + 1, 0);
   P.fma = 0;
+  // members of each (lane, depth) group; fronts of a lane alternate between two regions by
+  // depth parity (a depth reads only its parents' fronts, one depth up)
+  std::vector<std::vector<std::vector<int32_t>>> members(
+      nl + 1, std::vector<std::vector<int32_t>>(maxd + 1));
+  std::vector<std::vector<int64_t>> fsize(nl + 1, std::vector<int64_t>(maxd + 1, 0));
   for (int32_t t = 0; t < ns; ++t) {
     const int64_t nc = sn_nc(S, t), nbv = S.nb[t], N = nc + nbv;
     P.ncs[t] = static_cast<int32_t>(nc);
     P.doff[t + 1] = P.doff[t] + nc * nc;
     P.moff[t + 1] = P.moff[t] + nbv * nc;
-    P.depth_sn[depth[t]].push_back(t);
-    P.foff[t] = fsize[depth[t]];
-    fsize[depth[t]] += N * N;
-    P.fma += nbv * nbv * nc + nc * nc * (nc + nbv) / 2;
+    const int32_t L = S.lane_of[t] + 1, d = S.depth[t];
+    members[L][d].push_back(t);
+    P.foff[t] = fsize[L][d];
+    fsize[L][d] += N * N;
+    // useful multiply-adds: Sigma[B,C] (n_b^2 n_c), the lower triangle of Sigma[C,C] (the
+    // T^{-T} D^{-1} T^{-1} part over k >= max(i, j), and M^T Sigma[B,C]), M = P T^{-1} over
+    // k >= c, and T^{-1} itself where it is formed here (n_c > kBlock)
+    P.fma += nbv * nbv * nc + nc * (nc + 1) * (nc + 2) / 6 + nbv * nc * (nc + 1) / 2 +
+             nbv * nc * (nc + 1) / 2 + (nc > kBlock ? nc * (nc - 1) * (nc - 2) / 6 : 0);
   }
+  // region bases: (lane, parity) -> offset
+  std::vector<int64_t> base(2 * (nl + 1), 0);
+  P.fbuf = 0;
+  for (int32_t L = 0; L <= nl; ++L)
+    for (int par = 0; par < 2; ++par) {
+      int64_t mx = 0;
+      for (int32_t d = par; d <= maxd; d += 2) mx = std::max(mx, fsize[L][d]);
+      base[2 * L + par] = P.fbuf;
+      P.fbuf += mx;
+    }
+  for (int32_t t = 0; t < ns; ++t)
+    P.foff[t] += base[2 * (S.lane_of[t] + 1) + (S.depth[t] & 1)];
   P.dtotal = P.doff[ns];
   P.mtotal = P.moff[ns];
-  P.fbuf = 0;
-  for (int64_t x : fsize) P.fbuf = std::max(P.fbuf, x);
   auto fused = [&](int32_t t) {
     return sn_nc(S, t) <= kBlock && sn_nc(S, t) + S.nb[t] <= kSiSmallN;
   };
-  // phase 1 (T^{-1} and M) as in the block inverse, for the supernodes not fused
-  std::vector<int32_t> wide;
-  for (int32_t t = 0; t < ns; ++t) {
-    const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
-    if (fused(t)) continue;
-    if (nc <= kBlock) {
-      for (int32_t ch = 0; ch == 0 || ch * 256 < nbv; ++ch) {
-        P.small_sn.push_back(t);
-        P.small_chunk.push_back(ch);
-      }
-      continue;
-    }
-    for (int32_t J = 0; J * kBlock < nc; ++J)
-      for (int32_t sl = 0; sl < kDiagSlices && J * kBlock + sl * kDiagSlice < nc; ++sl) {
-        P.diag_sn.push_back(t);
-        P.diag_blk.push_back(J * kDiagSlices + sl);
-      }
-    wide.push_back(t);
-  }
-  m_tiles_of(S, wide, P.m_tiles, P.m_ptr);
-  // per depth: gathers, tiles, queries
-  P.gather_ptr.assign(1, 0);
-  P.bc_ptr.assign(1, 0);
-  P.cc_ptr.assign(1, 0);
-  P.q_ptr.assign(1, 0);
-  std::vector<std::vector<SiQuery>> qd(maxd + 1);
-  for (int32_t s0 = 0; s0 < ns; ++s0) {
-    if (fused(s0)) continue;   // answered inside the fused kernel
-    for (int64_t q = S.qbeg[s0]; q < S.qbeg[s0 + 1]; ++q)
-      qd[depth[s0]].push_back({s0, S.qa[q], S.qb[q], 0, S.qorig[q]});
-  }
-  P.fused_sn.clear();
-  P.fused_ptr.assign(1, 0);
-  for (int32_t d = 0; d <= maxd; ++d) {
-    int32_t ych = 0;
-    int64_t fsm = 0;
-    std::vector<Tile> bcg[3];
-    for (int32_t t : P.depth_sn[d]) {
-      if (fused(t)) {
-        P.fused_sn.push_back(t);
-        const int64_t nc = sn_nc(S, t), nbv = S.nb[t], N = nc + nbv;
-        fsm = std::max(fsm, 8 * (N * N + nc * nc + nbv * nc + nc));
+  // phase 1 (T^{-1} and M) as in the block inverse, per lane, for the supernodes not fused
+  P.phase1.assign(nl + 1, SiPhase1{});
+  for (int32_t L = 0; L <= nl; ++L) {
+    SiPhase1 &ph = P.phase1[L];
+    std::vector<int32_t> wide;
+    ph.small_b = static_cast<int64_t>(P.small_sn.size());
+    ph.diag_b = static_cast<int64_t>(P.diag_sn.size());
+    for (int32_t t = 0; t < ns; ++t) {
+      if (S.lane_of[t] + 1 != L || fused(t)) continue;
+      const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+      if (nc <= kBlock) {
+        for (int32_t ch = 0; ch == 0 || ch * 256 < nbv; ++ch) {
+          P.small_sn.push_back(t);
+          P.small_chunk.push_back(ch);
+        }
         continue;
       }
-      const int32_t nbv = S.nb[t];
-      if (nbv > 0) {
-        P.gather_sn.push_back(t);
-        ych = std::max(ych, (nbv + 7) / 8);
-      }
-    }
-    // Sigma[C,C] tiles: the largest tile (64, 32, 16; never wider than n_c needs) that still
-    // gives the launch many CTAs, as for Sigma[B,C]
-    int cc_cap = kT;
-    for (; cc_cap > 16; cc_cap /= 2) {
-      int64_t ctas = 0;
-      for (int32_t t : P.depth_sn[d]) {
-        if (fused(t)) continue;
-        const int64_t nt = (sn_nc(S, t) + std::min(cc_cap, cc_tile(sn_nc(S, t))) - 1) /
-                           std::min(cc_cap, cc_tile(sn_nc(S, t)));
-        ctas += nt * (nt + 1) / 2;
-      }
-      if (ctas >= target_ctas) break;
-    }
-    for (int32_t t : P.depth_sn[d]) {
-      if (fused(t)) continue;
-      const int32_t nc = sn_nc(S, t);
-      const int ts = std::min(cc_cap, cc_tile(nc));
-      for (int32_t r = 0; r * ts < nc; ++r)
-        for (int32_t c = 0; c <= r; ++c) P.cc.push_back({t, r, c, ts});
-    }
-    P.gather_ptr.push_back(static_cast<int64_t>(P.gather_sn.size()));
-    P.gather_ych.push_back(ych);
-    // Sigma[B,C] chunks: the widest chunks and tallest CTAs that still give the launch many
-    // waves of CTAs (at least 16 per SM).  FP64 issue is so slow that one warp with W
-    // independent multiply-adds keeps an SM sub-partition's unit busy, so small CTAs lose
-    // little; a launch of few large CTAs loses up to half its time to the last, partial wave.
-    constexpr int kOpts[][2] = {{128, 64}, {64, 64}, {64, 32}, {32, 32}, {32, 16}, {32, 8}};
-    constexpr int kNOpts = sizeof(kOpts) / sizeof(kOpts[0]);
-    int opt = 0;
-    for (; opt < kNOpts - 1; ++opt) {
-      const int rows = kOpts[opt][0], wcap = kOpts[opt][1];
-      int64_t ctas = 0;
-      for (int32_t t : P.depth_sn[d]) {
-        if (fused(t) || S.nb[t] == 0) continue;
-        ctas += int64_t((S.nb[t] + rows - 1) / rows) * ((sn_nc(S, t) + wcap - 1) / wcap);
-      }
-      if (ctas >= target_ctas) break;
-    }
-    const int rows = kOpts[opt][0], wcap = kOpts[opt][1];
-    for (int32_t t : P.depth_sn[d]) {
-      if (fused(t) || S.nb[t] == 0) continue;
-      const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
-      for (int32_t r = 0; r * rows < nbv; ++r)
-        for (int32_t c0 = 0; c0 < nc; c0 += wcap) {
-          const int w = rows_width(std::min(wcap, nc - c0));
-          bcg[rows_group(w)].push_back({t, r, c0, w});
+      for (int32_t J = 0; J * kBlock < nc; ++J)
+        for (int32_t sl = 0; sl < kDiagSlices && J * kBlock + sl * kDiagSlice < nc; ++sl) {
+          P.diag_sn.push_back(t);
+          P.diag_blk.push_back(J * kDiagSlices + sl);
         }
+      wide.push_back(t);
     }
-    P.bc_rows.push_back(rows);
-    for (int g = 0; g < 3; ++g) {
-      P.bc.insert(P.bc.end(), bcg[g].begin(), bcg[g].end());
-      P.bc_ptr.push_back(static_cast<int64_t>(P.bc.size()));
+    ph.small_e = static_cast<int64_t>(P.small_sn.size());
+    ph.diag_e = static_cast<int64_t>(P.diag_sn.size());
+    std::vector<Tile> mt;
+    std::vector<int64_t> mp;
+    m_tiles_of(S, wide, mt, mp);
+    const int64_t off = static_cast<int64_t>(P.m_tiles.size());
+    P.m_tiles.insert(P.m_tiles.end(), mt.begin(), mt.end());
+    for (int64_t x : mp) ph.m_ptr.push_back(off + x);
+  }
+  // groups: the top part depth by depth, then the lanes, depth by depth
+  for (int32_t L = 0; L <= nl; ++L) {
+    const int64_t target_ctas = int64_t(std::max(sms, 1)) * 16 / (L == 0 ? 1 : std::max(nl, 1));
+    for (int32_t d = 0; d <= maxd; ++d) {
+      const std::vector<int32_t> &mem = members[L][d];
+      if (mem.empty()) continue;
+      SiGroup G;
+      G.lane = L - 1;
+      G.depth = d;
+      G.fused_b = static_cast<int64_t>(P.fused_sn.size());
+      G.gather_b = static_cast<int64_t>(P.gather_sn.size());
+      int32_t ych = 0;
+      int64_t fsm = 0;
+      for (int32_t t : mem) {
+        if (fused(t)) {
+          P.fused_sn.push_back(t);
+          const int64_t nc = sn_nc(S, t), nbv = S.nb[t], N = nc + nbv;
+          fsm = std::max(fsm, 8 * (N * N + nc * nc + nbv * nc + nc));
+          continue;
+        }
+        const int32_t nbv = S.nb[t];
+        if (nbv > 0) {
+          P.gather_sn.push_back(t);
+          ych = std::max(ych, (nbv + 7) / 8);
+        }
+      }
+      G.fused_e = static_cast<int64_t>(P.fused_sn.size());
+      G.fused_smem = fsm;
+      G.gather_e = static_cast<int64_t>(P.gather_sn.size());
+      G.gather_ych = ych;
+      // Sigma[C,C] tiles: the largest tile (64, 32, 16; never wider than n_c needs) that still
+      // gives the launch many CTAs, as for Sigma[B,C]
+      int cc_cap = kT;
+      for (; cc_cap > 16; cc_cap /= 2) {
+        int64_t ctas = 0;
+        for (int32_t t : mem) {
+          if (fused(t)) continue;
+          const int64_t nt = (sn_nc(S, t) + std::min(cc_cap, cc_tile(sn_nc(S, t))) - 1) /
+                             std::min(cc_cap, cc_tile(sn_nc(S, t)));
+          ctas += nt * (nt + 1) / 2;
+        }
+        if (ctas >= target_ctas) break;
+      }
+      G.cc_b = static_cast<int64_t>(P.cc.size());
+      for (int32_t t : mem) {
+        if (fused(t)) continue;
+        const int32_t nc = sn_nc(S, t);
+        const int ts = std::min(cc_cap, cc_tile(nc));
+        for (int32_t r = 0; r * ts < nc; ++r)
+          for (int32_t c = 0; c <= r; ++c) P.cc.push_back({t, r, c, ts});
+      }
+      G.cc_e = static_cast<int64_t>(P.cc.size());
+      // Sigma[B,C] chunks: the widest chunks and tallest CTAs that still give the launch many
+      // CTAs (at least 16 per SM of the group's share).  FP64 issue is so slow that a few
+      // warps with W independent multiply-adds keep an SM sub-partition's unit busy, so small
+      // CTAs lose little; a launch of few large CTAs loses up to half its time to the last,
+      // partial wave.
+      constexpr int kOpts[][2] = {{128, 64}, {64, 64}, {64, 32}, {32, 32}, {32, 16}, {32, 8}};
+      constexpr int kNOpts = sizeof(kOpts) / sizeof(kOpts[0]);
+      int opt = 0;
+      for (; opt < kNOpts - 1; ++opt) {
+        const int rows = kOpts[opt][0], wcap = kOpts[opt][1];
+        int64_t ctas = 0;
+        for (int32_t t : mem) {
+          if (fused(t) || S.nb[t] == 0) continue;
+          ctas += int64_t((S.nb[t] + rows - 1) / rows) * ((sn_nc(S, t) + wcap - 1) / wcap);
+        }
+        if (ctas >= target_ctas) break;
+      }
+      const int rows = kOpts[opt][0], wcap = kOpts[opt][1];
+      std::vector<Tile> bcg[3];
+      for (int32_t t : mem) {
+        if (fused(t) || S.nb[t] == 0) continue;
+        const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
+        for (int32_t r = 0; r * rows < nbv; ++r)
+          for (int32_t c0 = 0; c0 < nc; c0 += wcap) {
+            const int w = rows_width(std::min(wcap, nc - c0));
+            bcg[rows_group(w)].push_back({t, r, c0, w});
+          }
+      }
+      G.bc_rows = rows;
+      G.bc_ptr[0] = static_cast<int64_t>(P.bc.size());
+      for (int g = 0; g < 3; ++g) {
+        P.bc.insert(P.bc.end(), bcg[g].begin(), bcg[g].end());
+        G.bc_ptr[g + 1] = static_cast<int64_t>(P.bc.size());
+      }
+      G.q_b = static_cast<int64_t>(P.queries.size());
+      for (int32_t t : mem) {
+        if (fused(t)) continue;   // answered inside the fused kernel
+        for (int64_t q = S.qbeg[t]; q < S.qbeg[t + 1]; ++q)
+          P.queries.push_back({t, S.qa[q], S.qb[q], 0, S.qorig[q]});
+      }
+      G.q_e = static_cast<int64_t>(P.queries.size());
+      P.groups.push_back(G);
     }
-    P.cc_ptr.push_back(static_cast<int64_t>(P.cc.size()));
-    P.queries.insert(P.queries.end(), qd[d].begin(), qd[d].end());
-    P.q_ptr.push_back(static_cast<int64_t>(P.queries.size()));
-    P.fused_ptr.push_back(static_cast<int64_t>(P.fused_sn.size()));
-    P.fused_smem.push_back(fsm);
   }
   return PEERS_OK;
 }
@@ -1450,16 +1499,16 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   std::shared_ptr<const peers::SelInvPlan> plan;
   RC_TRY(peers::cached_selinv_plan(sym, sms, plan, err));
   const peers::SelInvPlan &P = *plan;
+  const peers::Lanes *lanes = P.nlanes > 0 ? ctx_lanes(ctx) : nullptr;
   DevMem mem(&err);
-  double *Zd, *M, *F0, *F1, *Rdev = R;
+  double *Zd, *M, *F, *Rdev = R;
   int32_t *ncs, *gsn, *ssn, *sch, *dsn, *dblk;
   int64_t *doff, *moff, *foff;
   peers::Tile *bc, *cc, *mt;
   peers::SiQuery *qs;
   RC_TRY(mem.alloc(&Zd, P.dtotal));
   RC_TRY(mem.alloc(&M, P.mtotal));
-  RC_TRY(mem.alloc(&F0, P.fbuf));
-  RC_TRY(mem.alloc(&F1, P.fbuf));
+  RC_TRY(mem.alloc(&F, P.fbuf));
   RC_TRY(mem.upload(&ncs, P.ncs, st));
   RC_TRY(mem.upload(&doff, P.doff, st));
   RC_TRY(mem.upload(&moff, P.moff, st));
@@ -1477,9 +1526,28 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   int64_t *qbeg;
   RC_TRY(mem.upload(&fsn, P.fused_sn, st));
   RC_TRY(mem.upload(&qbeg, S.qbeg, st));
+  std::vector<int32_t> parent_host(S.parent);
+  int32_t *par;
+  RC_TRY(mem.upload(&par, parent_host, st));
   const bool host_out = !(flags & PEERS_OUT_DEVICE);
   if (host_out) RC_TRY(mem.alloc(&Rdev, S.nq));
+  {
+    int64_t need = 0;
+    for (const peers::SiGroup &G : P.groups) need = std::max(need, G.fused_smem);
+    static int si_small_smem[64] = {};   // limit set so far, per device
+    RC_TRY(peers::raise_smem_limit(reinterpret_cast<const void *>(peers::k_si_small),
+                                   si_small_smem, need, err));
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&]() {
+    if (ctx->timing) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      cudaEventRecord(e, st);
+      ev.push_back(e);
+    }
+  };
   if (ctx->timing) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1488,7 +1556,13 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   int64_t launches = 0;
   if (S.nq > 0) CUDA_TRY(cudaMemsetAsync(Rdev, 0, sizeof(double) * S.nq, st));
   CUDA_TRY(cudaMemsetAsync(Zd, 0, sizeof(double) * std::max<int64_t>(1, P.dtotal), st));
-  // phase 1: T^{-1} (into Zd, ld = n_c) and M, by the block inverse's kernels
+  // the lanes start here (their phase 1 needs nothing of the top part)
+  const int nl = lanes ? P.nlanes : 0;
+  if (nl > 0) {
+    CUDA_TRY(cudaEventRecord(lanes->start, st));
+    for (int L = 0; L < nl; ++L) CUDA_TRY(cudaStreamWaitEvent(lanes->stream[L], lanes->start, 0));
+  }
+  auto stream_of = [&](int32_t lane) { return (lane >= 0 && nl > 0) ? lanes->stream[lane] : st; };
   peers::BiArgs b{};
   b.panel = num->panel;
   b.tinv = num->tinv;
@@ -1503,28 +1577,27 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   b.plen = ncs;
   b.Z = Zd;
   b.M = M;
-  if (!P.small_sn.empty()) {
-    peers::k_bi_small<<<static_cast<unsigned>(P.small_sn.size()), 256, 0, st>>>(ssn, sch, b);
-    ++launches;
-  }
-  if (!P.diag_sn.empty()) {
-    peers::k_bi_diag<<<static_cast<unsigned>(P.diag_sn.size()), peers::kBlock * peers::kDiagSlice, 0, st>>>(
-        dsn, dblk, b);
-    ++launches;
-  }
-  RC_TRY(peers::launch_m_all(mt, P.m_ptr, b, st, &launches, err));
-  CUDA_TRY(cudaGetLastError());
-  std::vector<cudaEvent_t> ev;
-  auto mark = [&]() {
-    if (ctx->timing) {
-      cudaEvent_t e;
-      cudaEventCreate(&e);
-      cudaEventRecord(e, st);
-      ev.push_back(e);
+  // phase 1: T^{-1} (into Zd, ld = n_c) and M, by the block inverse's kernels, lane by lane
+  // (P.phase1[0] is the top part)
+  for (int32_t L = 0; L <= P.nlanes; ++L) {
+    const peers::SiPhase1 &ph = P.phase1[L];
+    const cudaStream_t ls = stream_of(L - 1);
+    if (ph.small_e > ph.small_b) {
+      peers::k_bi_small<<<static_cast<unsigned>(ph.small_e - ph.small_b), 256, 0, ls>>>(
+          ssn + ph.small_b, sch + ph.small_b, b);
+      ++launches;
     }
-  };
+    if (ph.diag_e > ph.diag_b) {
+      peers::k_bi_diag<<<static_cast<unsigned>(ph.diag_e - ph.diag_b),
+                         peers::kBlock * peers::kDiagSlice, 0, ls>>>(dsn + ph.diag_b,
+                                                                     dblk + ph.diag_b, b);
+      ++launches;
+    }
+    RC_TRY(peers::launch_m_all(mt, ph.m_ptr, b, ls, &launches, err));
+    CUDA_TRY(cudaGetLastError());
+  }
   mark();
-  // phase 2: top-down by depth
+  // phase 2: top-down by depth, the top part first, then every lane on its own stream
   peers::SiArgs a{};
   a.dinv = num->dinv;
   a.first = num->first;
@@ -1536,17 +1609,8 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   a.M = M;
   a.moff = moff;
   a.foff = foff;
-  std::vector<int32_t> parent_host(S.parent);
-  int32_t *par;
-  RC_TRY(mem.upload(&par, parent_host, st));
   a.parent = par;
-  {
-    int64_t need = 0;
-    for (int64_t x : P.fused_smem) need = std::max(need, x);
-    static int si_small_smem[64] = {};   // limit set so far, per device
-    RC_TRY(peers::raise_smem_limit(reinterpret_cast<const void *>(peers::k_si_small),
-                                   si_small_smem, need, err));
-  }
+  a.F = F;
   peers::SiSmallArgs sb{};
   sb.panel = num->panel;
   sb.tinv = num->tinv;
@@ -1557,44 +1621,60 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   sb.qa = num->qa;
   sb.qb = num->qb;
   sb.R = Rdev;
-  const size_t D = P.depth_sn.size();
-  for (size_t d = 0; d < D; ++d) {
-    a.Fcur = (d % 2) ? F1 : F0;
-    a.Fprev = (d % 2) ? F0 : F1;
-    const int64_t f0 = P.fused_ptr[d], f1 = P.fused_ptr[d + 1];
-    if (f1 > f0) {
-      peers::k_si_small<<<static_cast<unsigned>(f1 - f0), 256, P.fused_smem[d], st>>>(fsn + f0,
-                                                                                     a, sb);
+  bool top_done = nl == 0;
+  for (const peers::SiGroup &G : P.groups) {
+    if (G.lane >= 0 && !top_done) {
+      // the lanes' first depth reads the top part's last fronts
+      CUDA_TRY(cudaEventRecord(lanes->top_done, st));
+      for (int L = 0; L < nl; ++L)
+        CUDA_TRY(cudaStreamWaitEvent(lanes->stream[L], lanes->top_done, 0));
+      top_done = true;
+    }
+    const cudaStream_t gs = stream_of(G.lane);
+    if (G.fused_e > G.fused_b) {
+      peers::k_si_small<<<static_cast<unsigned>(G.fused_e - G.fused_b), 256, G.fused_smem, gs>>>(
+          fsn + G.fused_b, a, sb);
       ++launches;
     }
-    const int64_t g0 = P.gather_ptr[d], g1 = P.gather_ptr[d + 1];
-    if (g1 > g0) {
-      dim3 grid(static_cast<unsigned>(g1 - g0), static_cast<unsigned>(P.gather_ych[d]));
-      peers::k_si_gather<<<grid, 256, 0, st>>>(gsn + g0, a);
+    if (G.gather_e > G.gather_b) {
+      dim3 grid(static_cast<unsigned>(G.gather_e - G.gather_b),
+                static_cast<unsigned>(G.gather_ych));
+      peers::k_si_gather<<<grid, 256, 0, gs>>>(gsn + G.gather_b, a);
       ++launches;
     }
     for (int g = 0; g < 3; ++g) {
-      const int64_t b0 = P.bc_ptr[3 * d + g], b1 = P.bc_ptr[3 * d + g + 1];
+      const int64_t b0 = G.bc_ptr[g], b1 = G.bc_ptr[g + 1];
       if (b1 <= b0) continue;
-      const unsigned nb = static_cast<unsigned>(b1 - b0);
-      const int rows = P.bc_rows[d];
-      if (g == 0) peers::k_si_bc<0><<<nb, rows, 0, st>>>(bc + b0, a, rows);
-      if (g == 1) peers::k_si_bc<1><<<nb, rows, 0, st>>>(bc + b0, a, rows);
-      if (g == 2) peers::k_si_bc<2><<<nb, rows, 0, st>>>(bc + b0, a, rows);
+      const unsigned n = static_cast<unsigned>(b1 - b0);
+      const int rows = G.bc_rows;
+      if (g == 0) peers::k_si_bc<0><<<n, rows, 0, gs>>>(bc + b0, a, rows);
+      if (g == 1) peers::k_si_bc<1><<<n, rows, 0, gs>>>(bc + b0, a, rows);
+      if (g == 2) peers::k_si_bc<2><<<n, rows, 0, gs>>>(bc + b0, a, rows);
       ++launches;
     }
-    const int64_t c0 = P.cc_ptr[d], c1 = P.cc_ptr[d + 1];
-    if (c1 > c0) {
-      peers::k_si_cc<<<static_cast<unsigned>(c1 - c0), peers::kGemmThreads, 0, st>>>(cc + c0, a);
+    if (G.cc_e > G.cc_b) {
+      peers::k_si_cc<<<static_cast<unsigned>(G.cc_e - G.cc_b), peers::kGemmThreads, 0, gs>>>(
+          cc + G.cc_b, a);
       ++launches;
     }
-    const int64_t q0 = P.q_ptr[d], q1 = P.q_ptr[d + 1];
-    if (q1 > q0) {
-      peers::k_si_query<<<static_cast<unsigned>((q1 - q0 + 255) / 256), 256, 0, st>>>(
-          qs + q0, q1 - q0, a, Rdev);
+    if (G.q_e > G.q_b) {
+      peers::k_si_query<<<static_cast<unsigned>((G.q_e - G.q_b + 255) / 256), 256, 0, gs>>>(
+          qs + G.q_b, G.q_e - G.q_b, a, Rdev);
       ++launches;
     }
     CUDA_TRY(cudaGetLastError());
+    if (G.lane < 0) mark();
+  }
+  if (nl > 0) {
+    if (!top_done) {
+      CUDA_TRY(cudaEventRecord(lanes->top_done, st));
+      for (int L = 0; L < nl; ++L)
+        CUDA_TRY(cudaStreamWaitEvent(lanes->stream[L], lanes->top_done, 0));
+    }
+    for (int L = 0; L < nl; ++L) {
+      CUDA_TRY(cudaEventRecord(lanes->done[L], lanes->stream[L]));
+      CUDA_TRY(cudaStreamWaitEvent(st, lanes->done[L], 0));
+    }
     mark();
   }
   if (ctx->timing) {
@@ -1603,7 +1683,8 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     ctx->stats.sweep_s = ms * 1e-3;
-    // phase 1 (T^{-1} and M), then one entry per depth
+    // phase 1 (the top part's; the lanes' runs beside it), each depth of the top part, and
+    // the lanes' subtrees (concurrent streams) as one entry
     ctx->level_ms.clear();
     cudaEventElapsedTime(&ms, e0, ev[0]);
     ctx->level_ms.push_back(ms);

@@ -146,14 +146,18 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
   peers::assembly_values(S, w ? w : S.w0.data(), vals);
   peers::FactorDevice D{};
   int64_t *u_off = nullptr, *a_dest = nullptr, *trail_prefix = nullptr;
-  int32_t *level_sn = nullptr, *ea_pairs = nullptr;
+  int32_t *fac_sn = nullptr, *fuse_sn = nullptr, *child_ptr = nullptr, *child_list = nullptr;
+  int32_t *ea_pairs = nullptr;
   double *a_val = nullptr, *U = nullptr;
   int *status = nullptr;
   TRY(upload(num, &u_off, S.u_off, st, err));
   TRY(upload(num, &a_dest, S.a_dest, st, err));
   TRY(upload(num, &a_val, vals, st, err));
   TRY(upload(num, &trail_prefix, S.trail_prefix, st, err));
-  TRY(upload(num, &level_sn, S.level_sn, st, err));
+  TRY(upload(num, &fac_sn, S.fac_sn, st, err));
+  TRY(upload(num, &fuse_sn, S.fuse_sn, st, err));
+  TRY(upload(num, &child_ptr, S.child_ptr, st, err));
+  TRY(upload(num, &child_list, S.child_list, st, err));
   TRY(upload(num, &ea_pairs, S.ea_pairs, st, err));
   TRY(dalloc(num, &U, std::max<int64_t>(S.u_total, 1), err));
   TRY(dalloc(num, &status, 2, err));
@@ -162,20 +166,20 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
                              status};
   D.a_dest = a_dest;
   D.a_val = a_val;
-  D.level_sn = level_sn;
+  D.fac_sn = fac_sn;
+  D.fuse_sn = fuse_sn;
+  D.child_ptr = child_ptr;
+  D.child_list = child_list;
   D.ea_pairs = ea_pairs;
   D.trail_prefix = trail_prefix;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  std::vector<cudaEvent_t> lev;
   if (ctx->timing) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    lev.resize(static_cast<size_t>(S.nlevels) + 1);
-    for (auto &e : lev) cudaEventCreate(&e);
     cudaEventRecord(e0, st);
   }
   int64_t launches = 0;
-  int rc = peers::run_factor(S, D, st, &launches, err, ctx->timing ? lev.data() : nullptr);
+  int rc = peers::run_factor(S, D, st, ctx_lanes(ctx), &launches, err);
   ctx->stats.factor_launches = launches;
   if (ctx->timing) {
     cudaEventRecord(e1, st);
@@ -183,21 +187,15 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     ctx->stats.factor_s = ms * 1e-3;
-    if (rc == PEERS_OK) {
-      ctx->level_ms.assign(static_cast<size_t>(S.nlevels), 0.0);
-      for (int32_t l = 0; l < S.nlevels; ++l) {
-        cudaEventElapsedTime(&ms, lev[l], lev[l + 1]);
-        ctx->level_ms[l] = ms;
-      }
-    }
-    for (auto e : lev) cudaEventDestroy(e);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
   CUDA_TRY(cudaStreamSynchronize(st));
   for (void *p : {static_cast<void *>(u_off), static_cast<void *>(a_dest),
                   static_cast<void *>(a_val), static_cast<void *>(trail_prefix),
-                  static_cast<void *>(level_sn), static_cast<void *>(ea_pairs),
+                  static_cast<void *>(fac_sn), static_cast<void *>(fuse_sn),
+                  static_cast<void *>(child_ptr), static_cast<void *>(child_list),
+                  static_cast<void *>(ea_pairs),
                   static_cast<void *>(U), static_cast<void *>(status)})
     dfree(num, p);
   if (rc != PEERS_OK) return rc;
@@ -231,6 +229,23 @@ int factor_from_pool(peers_ctx *ctx, const peers_symbolic *sym, const double *w,
   }
   *out = num;
   return PEERS_OK;
+}
+
+const peers::Lanes *ctx_lanes(peers_ctx *ctx) {
+  if (ctx->lanes_ready) return &ctx->lanes;
+  peers::Lanes L{};
+  bool ok = cudaEventCreateWithFlags(&L.start, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&L.top_done, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < peers::kLanes && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&L.stream[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&L.done[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ctx->lanes = L;
+  ctx->lanes_ready = true;
+  return &ctx->lanes;
 }
 
 int ensure_carry(peers_numeric *num, const Symbolic &S, std::string &err) {
@@ -387,7 +402,18 @@ int peers_create(peers_ctx **out, int device, void *cuda_stream) {
 
 void peers_destroy(peers_ctx *ctx) {
   if (!ctx) return;
-  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  {
+    peers::DeviceGuard guard(ctx->device);
+    if (ctx->lanes_ready) {
+      for (int i = 0; i < peers::kLanes; ++i) {
+        cudaStreamDestroy(ctx->lanes.stream[i]);
+        cudaEventDestroy(ctx->lanes.done[i]);
+      }
+      cudaEventDestroy(ctx->lanes.start);
+      cudaEventDestroy(ctx->lanes.top_done);
+    }
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  }
   delete ctx;
 }
 
@@ -443,6 +469,7 @@ int peers_symbolic_info(const peers_symbolic *sym, peers_info *info) {
   info->t_symbolic = S.t_symbolic;
   info->t_queries = S.t_queries;
   for (char x : S.spill) info->nsuper_spilled += x ? 1 : 0;
+  info->front_bytes = S.front_bytes;
   return PEERS_OK;
 }
 

@@ -67,7 +67,9 @@ struct FactorDevice {
   FactorArgs args;
   const int64_t *a_dest;
   const double *a_val;
-  const int32_t *level_sn;
+  const int32_t *fac_sn;     // blocked supernodes by level (Symbolic::fac_sn)
+  const int32_t *fuse_sn;    // supernodes factored whole by one CTA (Symbolic::fuse_sn)
+  const int32_t *child_ptr, *child_list;
   const int32_t *ea_pairs;
   const int64_t *trail_prefix;
 };
@@ -95,11 +97,19 @@ struct SweepArgs {
   int *spill_counter;
 };
 
-// Runs the whole factorization on `stream`; adds the number of kernels launched to *launches.
-// If `level_events` is non-null it must hold nlevels + 1 events: [0] is recorded before the
-// first level and [l + 1] after level l.
-int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, int64_t *launches,
-               std::string &err, cudaEvent_t *level_events = nullptr);
+// CUDA streams over which a call spreads the lanes' independent subtrees (see kLanes), and
+// the events that order them against the context's stream.
+struct Lanes {
+  cudaStream_t stream[kLanes];
+  cudaEvent_t done[kLanes];   // recorded on a lane's stream when its work is issued
+  cudaEvent_t start;          // recorded on the context's stream where the lanes may begin
+  cudaEvent_t top_done;       // recorded on the context's stream when the top part is issued
+};
+
+// Runs the whole factorization on `stream` (and the lanes' subtrees on `lanes`' streams when
+// it is non-null); adds the number of kernels launched to *launches.
+int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, const Lanes *lanes,
+               int64_t *launches, std::string &err);
 
 // Launches the sweep of one wave, level by level.  If `events` is non-null it must hold
 // 2 * nlevels events; launch l is bracketed by events[2l], events[2l+1].

@@ -16,6 +16,8 @@
 // FP64 throughout (DFMA; on this part the FP64 mma.sync path is not faster than DFMA).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -140,11 +142,16 @@ __global__ void __launch_bounds__(128) k_panel_rows(const int32_t *__restrict__ 
 
 // Trailing update of block J: F[i, j] -= sum_k L[i, c0+k] d_k L[j, c0+k] for t0 <= j <= i < N,
 // t0 = c0 + bw.  Column j < nc lives in the panel, j >= nc in the update matrix U_s.
+// TS x TS tiles (TS = 64, or 32 for launches with few tiles, so that their work spreads over
+// more SMs); 16 x 16 threads, (TS/16)^2 outputs each.  Every output sums over k in the same
+// order whatever TS is.
+template <int TS>
 __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sns, int32_t J,
                                                   const int64_t *__restrict__ prefix, int32_t na,
                                                   FactorArgs a) {
-  __shared__ double Li[kBlock][kTile];
-  __shared__ double Lj[kBlock][kTile];
+  constexpr int U = TS / 16;
+  __shared__ double Li[kBlock][TS];
+  __shared__ double Lj[kBlock][TS];
   // locate the supernode of this tile
   const int64_t t = blockIdx.x;
   int32_t lo = 0, hi = na;   // prefix[lo] <= t < prefix[hi]
@@ -160,34 +167,34 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
   const int64_t tj = lt - ti * (ti + 1) / 2;
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
   const int32_t c0 = J * kBlock, bw = min(kBlock, nc - c0), t0 = c0 + bw;
-  const int32_t R0 = t0 + int32_t(ti) * kTile, C0 = t0 + int32_t(tj) * kTile;
+  const int32_t R0 = t0 + int32_t(ti) * TS, C0 = t0 + int32_t(tj) * TS;
   const double *P = a.panel + a.panel_off[s];
-  for (int idx = threadIdx.x; idx < kBlock * kTile; idx += blockDim.x) {
-    const int k = idx / kTile, r = idx % kTile;
+  for (int idx = threadIdx.x; idx < kBlock * TS; idx += blockDim.x) {
+    const int k = idx / TS, r = idx % TS;
     const bool kin = k < bw;
     Li[k][r] = (kin && R0 + r < N) ? P[int64_t(c0 + k) * N + R0 + r] : 0.0;
     Lj[k][r] = (kin && C0 + r < N) ? P[int64_t(c0 + k) * N + C0 + r] * a.d[f + c0 + k] : 0.0;
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
+  double acc[U][U] = {};
   for (int k = 0; k < bw; ++k) {
-    double li[4], lj[4];
+    double li[U], lj[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) { li[u] = Li[k][tx + 16 * u]; lj[u] = Lj[k][ty + 16 * u]; }
+    for (int u = 0; u < U; ++u) { li[u] = Li[k][tx + 16 * u]; lj[u] = Lj[k][ty + 16 * u]; }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = fma(li[u], lj[v], acc[u][v]);
+      for (int v = 0; v < U; ++v) acc[u][v] = fma(li[u], lj[v], acc[u][v]);
   }
   double *Pw = a.panel + a.panel_off[s];
   double *Uw = a.U + a.u_off[s];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < U; ++v) {
     const int32_t j = C0 + ty + 16 * v;
     if (j >= N) continue;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int32_t i = R0 + tx + 16 * u;
       if (i >= N || i < j) continue;
       if (j < nc)
@@ -198,9 +205,108 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
   }
 }
 
-// Host driver: the full factorization on `stream`.  Returns a PEERS_* status.
-int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, int64_t *launches,
-               std::string &err, cudaEvent_t *level_events) {
+// A whole supernode of one column block (n_c <= kBlock) whose front has at most kFactorFuseN
+// rows, by one CTA in shared memory.  The front F (N x N, column-major, ld = N) is filled from
+// the panel's assembled entries and the children's update matrices, added child by child in
+// child order (the order of the per-rank k_extend_add launches); then the operations of
+// k_diag_block, k_panel_rows and k_trailing run in their order on F, and the panel, d, 1/d,
+// the diagonal-block inverse and the update matrix are written back.  The results are those
+// of the blocked kernels bit for bit; the small supernodes of the lower levels just need one
+// launch per level instead of four or more.
+__global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict__ sns,
+                                                      const int32_t *__restrict__ child_ptr,
+                                                      const int32_t *__restrict__ child_list,
+                                                      FactorArgs a) {
+  extern __shared__ double sm_fac[];
+  __shared__ double X[kBlock][kBlock + 1];
+  __shared__ double dk[kBlock];
+  const int32_t s = sns[blockIdx.x];
+  const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
+  const int bw = nc;   // one column block
+  double *F = sm_fac;
+  double *P = a.panel + a.panel_off[s];
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  for (int idx = tid; idx < N * N; idx += blockDim.x) {
+    const int j = idx / N, i = idx - j * N;
+    F[idx] = j < nc ? P[idx] : 0.0;
+  }
+  __syncthreads();
+  for (int32_t c = child_ptr[s]; c < child_ptr[s + 1]; ++c) {
+    const int32_t ch = child_list[c];
+    const int32_t nbc = a.nb[ch];
+    const int32_t *rm = a.rmap + a.rows_off[ch];
+    const double *Uc = a.U + a.u_off[ch];
+    for (int idx = tid; idx < nbc * nbc; idx += blockDim.x) {
+      const int j = idx / nbc, i = idx - j * nbc;
+      if (i >= j) F[rm[j] * N + rm[i]] += Uc[idx];
+    }
+    __syncthreads();
+  }
+  // diagonal block: L_JJ D_J L_JJ^T (k_diag_block)
+  if (warp == 0) {
+    for (int k = 0; k < bw; ++k) {
+      const double d = F[k * N + k];
+      if (lane == 0 && !(d > 0.0 && d < INFINITY)) flag_error(a.status, kErrNotSpd, f + k);
+      if (lane > k && lane < bw) F[k * N + lane] = F[k * N + lane] / d;
+      __syncwarp();
+      if (lane > k && lane < bw) {
+        const double lk = F[k * N + lane] * d;
+        for (int j = k + 1; j <= lane; ++j) F[j * N + lane] = fma(-lk, F[k * N + j], F[j * N + lane]);
+      }
+      __syncwarp();
+    }
+    if (lane < bw) {
+      const double d = F[lane * N + lane];
+      dk[lane] = d;
+      P[int64_t(lane) * N + lane] = d;
+      for (int j = 0; j < lane; ++j) P[int64_t(j) * N + lane] = F[j * N + lane];
+      a.d[f + lane] = d;
+      a.dinv[f + lane] = 1.0 / d;
+      // inverse of the unit-lower L_JJ, column `lane`
+      X[lane][lane] = 1.0;
+      for (int i = lane + 1; i < bw; ++i) {
+        double t = 0.0;
+        for (int k = lane; k < i; ++k) t = fma(F[k * N + i], X[k][lane], t);
+        X[i][lane] = -t;
+      }
+    }
+    __syncwarp();
+    double *T = a.tinv + a.tinv_off[s];
+    for (int i = 0; i < bw; ++i)
+      if (lane < bw) T[i * bw + lane] = lane <= i ? X[i][lane] : 0.0;
+  }
+  __syncthreads();
+  // rows below the block: L[i, k] = w_k / d_k, w L_JJ^T = F[i, J] (k_panel_rows)
+  // (w is formed in place in row i of F: w_k overwrites F[i, k] once its sum is complete)
+  for (int i = bw + tid; i < N; i += blockDim.x) {
+    for (int k = 0; k < bw; ++k) {
+      double t = F[k * N + i];
+      for (int j = 0; j < k; ++j) t = fma(-F[j * N + i], F[j * N + k], t);
+      F[k * N + i] = t;
+    }
+    for (int k = 0; k < bw; ++k) {
+      const double l = F[k * N + i] / dk[k];
+      F[k * N + i] = l;
+      P[int64_t(k) * N + i] = l;
+    }
+  }
+  __syncthreads();
+  // trailing update of the update matrix: F[i, j] -= sum_k L[i, k] (L[j, k] d_k) (k_trailing)
+  double *Uw = a.U + a.u_off[s];
+  for (int idx = tid; idx < nbv * nbv; idx += blockDim.x) {
+    const int jj = idx / nbv, ii = idx - jj * nbv;
+    if (ii < jj) continue;
+    const int i = nc + ii, j = nc + jj;
+    double acc = 0.0;
+    for (int k = 0; k < bw; ++k) acc = fma(F[k * N + i], F[k * N + j] * dk[k], acc);
+    Uw[idx] = F[j * N + i] - acc;
+  }
+}
+
+// Host driver: the full factorization on `stream`, with the lanes' subtrees on the lane
+// streams when `lanes` is given (see kLanes).  Returns a PEERS_* status.
+int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, const Lanes *lanes,
+               int64_t *launches, std::string &err) {
   FactorArgs a = D.args;
   CUDA_TRY(cudaMemsetAsync(a.panel, 0, sizeof(double) * S.panel_total, stream));
   if (S.u_total > 0) CUDA_TRY(cudaMemsetAsync(a.U, 0, sizeof(double) * S.u_total, stream));
@@ -214,50 +320,99 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, in
     }
     CUDA_TRY(cudaGetLastError());
   }
-  if (level_events) CUDA_TRY(cudaEventRecord(level_events[0], stream));
-  for (int32_t l = 0; l < S.nlevels; ++l) {
-    const int32_t *sns = D.level_sn + S.level_ptr[l];
-    // 1. extend-add of the children, one launch per child rank
-    for (int64_t r = S.ea_base[l]; r < S.ea_base[l + 1]; ++r) {
+  {
+    int64_t smem = 0;
+    for (int32_t s : S.fuse_sn) {
+      const int64_t N = sn_nc(S, s) + S.nb[s];
+      smem = std::max(smem, 8 * N * N);
+    }
+    static int fuse_smem[64] = {};   // limit set so far, per device
+    const int rc = raise_smem_limit(reinterpret_cast<const void *>(k_factor_small), fuse_smem,
+                                    smem, err);
+    if (rc != PEERS_OK) return rc;
+  }
+  // the lanes start once the panels are assembled; the top part starts once they are done
+  const bool forked = lanes && S.nlanes > 0;
+  if (forked) {
+    CUDA_TRY(cudaEventRecord(lanes->start, stream));
+    for (int L = 0; L < S.nlanes; ++L) CUDA_TRY(cudaStreamWaitEvent(lanes->stream[L], lanes->start, 0));
+  }
+  bool joined = !forked;
+  auto join = [&]() -> int {
+    for (int L = 0; L < S.nlanes; ++L) {
+      CUDA_TRY(cudaEventRecord(lanes->done[L], lanes->stream[L]));
+      CUDA_TRY(cudaStreamWaitEvent(stream, lanes->done[L], 0));
+    }
+    joined = true;
+    return PEERS_OK;
+  };
+  for (const FactorGroup &G : S.fgroups) {
+    if (G.lane < 0 && !joined) {
+      const int rc = join();
+      if (rc != PEERS_OK) return rc;
+    }
+    const cudaStream_t st = (G.lane >= 0 && forked) ? lanes->stream[G.lane] : stream;
+    const int32_t *sns = D.fac_sn + G.fac_b;
+    // 0. supernodes factored whole, one CTA each
+    if (G.fuse_e > G.fuse_b) {
+      int64_t smem = 0;
+      for (int32_t i = G.fuse_b; i < G.fuse_e; ++i) {
+        const int64_t N = sn_nc(S, S.fuse_sn[i]) + S.nb[S.fuse_sn[i]];
+        smem = std::max(smem, 8 * N * N);
+      }
+      k_factor_small<<<static_cast<unsigned>(G.fuse_e - G.fuse_b), 256, smem, st>>>(
+          D.fuse_sn + G.fuse_b, D.child_ptr, D.child_list, a);
+      ++*launches;
+      CUDA_TRY(cudaGetLastError());
+    }
+    // 1. extend-add of the blocked supernodes' children, one launch per child rank
+    for (int64_t r = G.ea_b; r < G.ea_e; ++r) {
       const int64_t p0 = S.ea_off[r], p1 = S.ea_off[r + 1];
       if (p1 <= p0) continue;
       int32_t maxnb = 0;
       for (int64_t q = p0; q < p1; ++q) maxnb = std::max(maxnb, S.nb[S.ea_pairs[2 * q + 1]]);
       if (maxnb == 0) continue;
       dim3 grid(static_cast<unsigned>(p1 - p0), static_cast<unsigned>((maxnb + 7) / 8));
-      k_extend_add<<<grid, 256, 0, stream>>>(D.ea_pairs + 2 * p0, a);
+      k_extend_add<<<grid, 256, 0, st>>>(D.ea_pairs + 2 * p0, a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
     }
     // 2. right-looking column blocks
-    for (int32_t J = 0; J < S.level_nblocks[l]; ++J) {
-      const int64_t tp = S.trail_base[l] + J;
+    for (int32_t J = 0; J < G.nblocks; ++J) {
+      const int64_t tp = G.trail_base + J;
       const int32_t na = static_cast<int32_t>(S.trail_na[tp]);
       if (na == 0) continue;
-      k_diag_block<<<na, 32, 0, stream>>>(sns, J, a);
+      k_diag_block<<<na, 32, 0, st>>>(sns, J, a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
       int32_t maxrows = 0;
       for (int32_t i = 0; i < na; ++i) {
-        const int32_t s = S.level_sn[S.level_ptr[l] + i];
+        const int32_t s = S.fac_sn[G.fac_b + i];
         const int32_t nc = sn_nc(S, s), N = nc + S.nb[s];
         maxrows = std::max(maxrows, N - std::min(nc, (J + 1) * kBlock));
       }
       if (maxrows > 0) {
         dim3 grid(static_cast<unsigned>(na), static_cast<unsigned>((maxrows + 127) / 128));
-        k_panel_rows<<<grid, 128, 0, stream>>>(sns, J, a);
+        k_panel_rows<<<grid, 128, 0, st>>>(sns, J, a);
         ++*launches;
         CUDA_TRY(cudaGetLastError());
       }
       const int64_t ntiles = S.trail_prefix[S.trail_off[tp] + na];
       if (ntiles > 0) {
-        k_trailing<<<static_cast<unsigned>(ntiles), 256, 0, stream>>>(
-            sns, J, D.trail_prefix + S.trail_off[tp], na, a);
+        if (S.trail_ts[tp] == 32)
+          k_trailing<32><<<static_cast<unsigned>(ntiles), 256, 0, st>>>(
+              sns, J, D.trail_prefix + S.trail_off[tp], na, a);
+        else
+          k_trailing<64><<<static_cast<unsigned>(ntiles), 256, 0, st>>>(
+              sns, J, D.trail_prefix + S.trail_off[tp], na, a);
         ++*launches;
         CUDA_TRY(cudaGetLastError());
       }
     }
-    if (level_events) CUDA_TRY(cudaEventRecord(level_events[l + 1], stream));
+  }
+  if (!joined) {
+    const int rc = join();
+    if (rc != PEERS_OK) return rc;
   }
   int status[2] = {0, 0};
   CUDA_TRY(cudaMemcpyAsync(status, a.status, sizeof(status), cudaMemcpyDeviceToHost, stream));

@@ -18,6 +18,9 @@ struct peers_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // lane streams and events (created on first use, see ctx_lanes)
+  peers::Lanes lanes{};
+  bool lanes_ready = false;
   bool timing = false;
   peers_stats stats{};
   std::vector<double> level_ms;
@@ -94,6 +97,11 @@ inline peers::SweepArgs sweep_args_of(const peers_numeric *num, const Symbolic &
   a.spill_counter = num->spill_counter;
   return a;
 }
+
+// The context's lane streams (created on the first call that needs them, on the context's
+// device, which must be current); nullptr if they cannot be created, in which case callers
+// run everything on the context's stream (capi.cu).
+const peers::Lanes *ctx_lanes(peers_ctx *ctx);
 
 // Records a failure message for peers_last_error and returns the status.
 int peers_fail(int status, const std::string &msg);

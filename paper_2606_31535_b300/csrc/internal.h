@@ -20,8 +20,28 @@ namespace peers {
 // inverses and the sweep's update steps all use it, so every query's arithmetic is blocked
 // identically whatever tile it lands in.
 constexpr int kBlock = 32;
-// Rows x columns of one trailing-update tile of the factorization.
+// Rows x columns of one trailing-update tile of the factorization (halved for launches that
+// would have fewer than kTrailFewTiles tiles).
 constexpr int kTile = 64;
+constexpr int64_t kTrailFewTiles = 148 * 4;
+// Supernodes of one column block whose front has at most this many rows are factored whole
+// by one CTA in shared memory (assembly, children's update matrices, L D L^T, write-back).
+constexpr int kFactorFuseN = 96;
+// CUDA streams over which independent subtrees are spread (factorization, selected inversion).
+constexpr int kLanes = 4;
+
+// One group of the factorization: the supernodes of one level in one lane (lane -1: the part
+// above the lanes' subtrees, on the context's stream).  fuse_sn[fuse_b, fuse_e) are factored
+// whole, fac_sn[fac_b, fac_e) (widest first) by the blocked kernels over nblocks column
+// blocks, with trailing-update tiles trail_*[trail_base + J] and extend-add ranks
+// ea_off[ea_b .. ea_e].
+struct FactorGroup {
+  int32_t lane, level;
+  int32_t fuse_b, fuse_e, fac_b, fac_e;
+  int32_t nblocks;
+  int64_t trail_base;
+  int64_t ea_b, ea_e;
+};
 // Largest number of queries one sweep tile (one CTA) carries.
 constexpr int kQMax = 32;
 // Shared-memory budget of one sweep CTA for its query fronts (bytes).
@@ -129,16 +149,21 @@ struct Symbolic {
   // diagonal of the reduced node r = sum of the conductances of CSR row g(r)
   std::vector<int64_t> csr_indptr;  // copy of the input indptr (to rebuild degrees)
   std::vector<double> w0;           // conductances given to analyze
-  // factorization schedule per level: number of column blocks of the widest supernode
-  std::vector<int32_t> level_nblocks;
-  // trailing-update tiles: for (level l, block J) the active supernodes are the first
-  // na = trail_na[tp] of level l's list; trail_prefix[trail_off[tp] + i] is the tile prefix
-  // of the i-th active supernode (na + 1 entries).  tp = trail_base[l] + J.
-  std::vector<int64_t> trail_base, trail_off, trail_na;
+  // lanes (see kLanes): per supernode its depth below its root and its lane (-1: top part)
+  std::vector<int32_t> depth, lane_of;
+  int32_t nlanes = 0;
+  // factorization schedule: groups in issue order, over the supernode lists fuse_sn (factored
+  // whole in one CTA, see kFactorFuseN) and fac_sn (blocked kernels)
+  std::vector<FactorGroup> fgroups;
+  std::vector<int32_t> fuse_sn, fac_sn;
+  // trailing-update tiles: for (group g, block J) the active supernodes are the first
+  // na = trail_na[tp] of the group's blocked supernodes; trail_prefix[trail_off[tp] + i] is the
+  // tile prefix of the i-th active supernode (na + 1 entries).  tp = fgroups[g].trail_base + J.
+  std::vector<int64_t> trail_off, trail_na;
+  std::vector<int32_t> trail_ts;    // tile size of each (group, block): kTile or kTile / 2
   std::vector<int64_t> trail_prefix;
-  // extend-add schedule: for level l and child rank r, pairs (parent, child) in
-  // ea_pairs[ea_off[ea_base[l] + r] .. ea_off[ea_base[l] + r + 1])
-  std::vector<int64_t> ea_base;     // nlevels + 1 (index into ea_off)
+  // extend-add schedule: for group g and child rank r (ea_b <= r < ea_e), pairs
+  // (parent, child) in ea_pairs[2 ea_off[r] .. 2 ea_off[r + 1])
   std::vector<int64_t> ea_off;
   std::vector<int32_t> ea_pairs;    // (parent, child) interleaved
   int64_t factor_fma = 0;
@@ -171,6 +196,7 @@ struct Symbolic {
   std::vector<int32_t> two_a, two_b;
   int64_t carry_slots = 0;          // slots of the carry buffer (largest wave)
   int64_t walk_entries = 0, walk_fma = 0;
+  int64_t front_bytes = 0;   // query-front bytes one sweep reads and writes between levels
   double t_order = 0, t_symbolic = 0, t_queries = 0;
 };
 

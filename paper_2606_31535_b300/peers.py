@@ -61,7 +61,8 @@ class Info(ctypes.Structure):
         "n", "n_reduced", "nnz_a", "nnz_l", "nsuper", "levels", "max_nc", "max_nb", "nq",
         "nq_trivial", "nq_two_branch", "walk_entries", "walk_fma", "factor_fma",
         "device_bytes")] + [("t_order", ctypes.c_double), ("t_symbolic", ctypes.c_double),
-                            ("t_queries", ctypes.c_double), ("nsuper_spilled", ctypes.c_int64)]
+                            ("t_queries", ctypes.c_double), ("nsuper_spilled", ctypes.c_int64),
+                            ("front_bytes", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -358,9 +358,10 @@ int peers_last_stats(const peers_ctx *ctx, peers_stats *out);
 
 /* Device milliseconds per step of the last timed call on the context, into
  * ms[0 .. min(count, cap)), where the steps are: for peers_query, each sweep launch (one per
- * etree level, leaves first, summed over waves); for peers_query_selinv, phase 1 (T^{-1} and
- * M) of the part above the concurrent subtrees, each tree depth of that part (root first), and
- * then the concurrent subtrees, which run on several CUDA streams at once, as one step; for
+ * etree level, leaves first, summed over waves); for peers_query_selinv, each tree depth of
+ * the part above the concurrent subtrees (root first; a step includes the wait for that
+ * depth's T^{-1} and M, which are formed beside the depths above it), then the concurrent
+ * subtrees, which run on several CUDA streams at once, as one step; for
  * peers_query_blockinv, the diagonal inverses, M, each tree depth of Z blocks
  * (root first) and the query pass.  Returns the step count or a negative status (PEERS_EINVAL for a null context, or a
  * null ms with cap > 0). */

@@ -47,6 +47,8 @@ struct BiArgs {
   const int32_t *gstart;           // per B_t entry: first row of its column within P_parent
   const int64_t *gsrc;             // per B_t entry: offset of its column in Z
   double *Z, *M;
+  int *status;                     // error flag (bounds-checked build)
+  int64_t ztotal, nq;              // extents of Z and of the results
 };
 
 // ---------------------------------------------------------------- phase 1a: T_t^{-1}
@@ -70,6 +72,11 @@ __global__ void __launch_bounds__(kBlock * kDiagSlice) k_bi_diag(const int32_t *
   const int32_t ld = a.plen[t];
   const double *P = a.panel + a.panel_off[t];
   double *Zt = a.Z + a.zoff[t];
+  // the supernode's panel, block inverses and block of Z hold what this CTA touches
+  if (!PEERS_IN(int64_t(nc) * N - 1, a.panel_off[t + 1] - a.panel_off[t], a.status) ||
+      !PEERS_IN(int64_t(nc - 1) * ld + nc - 1, a.zoff[t + 1] - a.zoff[t], a.status) ||
+      !PEERS_IN(a.tinv_off[t + 1] - a.tinv_off[t] - 1, a.tinv_off[t + 1] - a.tinv_off[t], a.status))
+    return;
   const int c0 = J * kBlock;                        // the block's first column
   const int s0 = c0 + sl * kDiagSlice;              // this slice's first column
   const int sw = min(kDiagSlice, nc - s0);          // columns in the slice
@@ -121,6 +128,11 @@ __global__ void __launch_bounds__(256) k_bi_small(const int32_t *__restrict__ sn
   const int32_t t = sns[blockIdx.x], ch = chunk[blockIdx.x];
   const int32_t nc = a.first[t + 1] - a.first[t], nbv = a.nb[t], N = nc + nbv;
   const double *TI = a.tinv + a.tinv_off[t];
+  if (!PEERS_IN(int64_t(nc) * nc - 1, a.tinv_off[t + 1] - a.tinv_off[t], a.status) ||
+      !PEERS_IN(int64_t(nc) * N - 1, a.panel_off[t + 1] - a.panel_off[t], a.status) ||
+      !PEERS_IN(int64_t(nc - 1) * a.plen[t] + nc - 1, a.zoff[t + 1] - a.zoff[t], a.status) ||
+      !(nbv == 0 || PEERS_IN(int64_t(nbv) * nc - 1, a.moff[t + 1] - a.moff[t], a.status)))
+    return;
   for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
     const int i = e / kBlock, j = e % kBlock;
     Ti[i][j] = (i < nc && j < nc) ? TI[i * nc + j] : 0.0;
@@ -181,12 +193,23 @@ struct RowsGemm {
   int64_t oi, oc;         // out(i, c) = out[i * oi + c * oc]
   int32_t nrows, kb, ke, ncols;
   bool negate;
+  // extents of A, B and out from their pointers, and the error flag (bounds-checked build)
+  int64_t a_ext, b_ext, o_ext;
+  int *status;
 };
 
 template <int W>
 __device__ __forceinline__ void rows_gemm(const RowsGemm &g, int r, int c0, int rows, double *Ms) {
   const int wn = min(W, g.ncols - c0);
   const int i = r * rows + threadIdx.x;
+#if defined(PEERS_BOUNDS) && PEERS_BOUNDS
+  // the largest index of each operand this tile reads or writes lies inside its extent
+  if (g.ke > g.kb && g.nrows > 0 &&
+      (!PEERS_IN(int64_t(g.ke - 1) * g.lda + g.nrows - 1, g.a_ext, g.status) ||
+       !PEERS_IN(int64_t(g.ke - 1) * g.bk + int64_t(g.ncols - 1) * g.bc, g.b_ext, g.status) ||
+       !PEERS_IN(int64_t(g.nrows - 1) * g.oi + int64_t(g.ncols - 1) * g.oc, g.o_ext, g.status)))
+    return;
+#endif
   double acc[W];
 #pragma unroll
   for (int c = 0; c < W; ++c) acc[c] = 0.0;
@@ -271,6 +294,10 @@ __device__ __forceinline__ void rows_gemm_dispatch(const RowsGemm &g, const Tile
 // product.  Z[C_t, C_t] = T_t^{-1} is lower triangular, so a column chunk starting at c0 only
 // needs k >= c0 (the entries above the diagonal are stored zeros).
 constexpr int kMRows = 64;
+// Column chunk of M's tiles: 32 rather than the widest 64, so that a tile (64 x 32 over up to
+// n_c terms) holds its SM for a short time; the tiles of a low-priority stream then do not
+// keep the critical path's launches waiting for long.
+constexpr int kMWidth = 32;
 template <int G>
 __global__ void __launch_bounds__(kRowsMaxThreads) k_bi_m(const Tile *__restrict__ tiles, BiArgs a) {
   __shared__ double Ms[kRowsK * rows_group_width(G)];
@@ -291,6 +318,10 @@ __global__ void __launch_bounds__(kRowsMaxThreads) k_bi_m(const Tile *__restrict
   g.ke = nc;
   g.ncols = nc;
   g.negate = false;
+  g.a_ext = a.panel_off[t + 1] - a.panel_off[t] - nc;
+  g.b_ext = a.zoff[t + 1] - a.zoff[t];
+  g.o_ext = a.moff[t + 1] - a.moff[t];
+  g.status = a.status;
   rows_gemm_dispatch<G>(g, tl, kMRows, Ms);
 }
 
@@ -302,8 +333,8 @@ inline void m_tiles_of(const Symbolic &S, const std::vector<int32_t> &wide,
   for (int32_t t : wide) {
     const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
     for (int32_t r = 0; r * kMRows < nbv; ++r)
-      for (int32_t c0 = 0; c0 < nc; c0 += kRowsMaxW) {
-        const int w = rows_width(std::min(kRowsMaxW, nc - c0));
+      for (int32_t c0 = 0; c0 < nc; c0 += kMWidth) {
+        const int w = rows_width(std::min(kMWidth, nc - c0));
         grp[rows_group(w)].push_back({t, r, c0, w});
       }
   }
@@ -334,6 +365,149 @@ int launch_m_all(const Tile *d_tiles, const std::vector<int64_t> &ptr, const BiA
   if (rc == PEERS_OK) rc = launch_m<1>(d_tiles, ptr, a, st, launches, err);
   if (rc == PEERS_OK) rc = launch_m<2>(d_tiles, ptr, a, st, launches, err);
   return rc;
+}
+
+// ---------------------------------------------------------------- T^{-1} by doubling
+//
+// For a wide supernode (n_c > kBlock) the inverse X = T^{-1} of its unit-lower diagonal block
+// is built from the factor's 32 x 32 diagonal-block inverses by doubling.  At level l (blocks
+// of s = 32 * 2^l columns) each pair of adjacent inverted diagonal blocks A = T[a, a] and
+// C = T[c, c] (c = a + s) with coupling B = T[c, a] gives the inverse of the 2s block:
+//     X[c, a] = -C^{-1} (B A^{-1}),
+// formed by two row-per-thread products, W = B A^{-1} (A^{-1} lower triangular: only
+// k >= col contributes) and then X[c, a] = -C^{-1} W (C^{-1} lower triangular: k <= row).
+// The pairs of one level, over every wide supernode of a list, share one launch per product,
+// so the critical path is log2(n_c / 32) levels of well-filled launches rather than one
+// CTA's block substitution down all n_c rows.  W is kept in a buffer laid out like X.
+struct TinvTile {
+  int32_t t;          // supernode
+  int32_t a0, c0;     // first columns of A and of C
+  int32_t ha, hc;     // their widths
+  int32_t r;          // row chunk of the product (rows of C, kTinvRows each)
+  int32_t col0, w;    // first column (of A) of the tile and its width (rows_width)
+};
+constexpr int kTinvRows = 64;
+// Supernodes at least this wide form T^{-1} by doubling; narrower ones by k_bi_diag's block
+// substitution, whose single launch beats the doubling's launch chain there.
+constexpr int32_t kTinvDoubling = 1024;
+
+// X's 32 x 32 diagonal blocks from the factor's block inverses.  grid = (supernode, block).
+__global__ void __launch_bounds__(256) k_tinv_base(const int32_t *__restrict__ sns,
+                                                   const int32_t *__restrict__ blk, BiArgs a) {
+  const int32_t t = sns[blockIdx.x], J = blk[blockIdx.x];
+  const int32_t nc = a.first[t + 1] - a.first[t], ld = a.plen[t];
+  const int32_t c0 = J * kBlock, bw = min(kBlock, nc - c0);
+  if (!PEERS_IN(int64_t(J) * kBlock * kBlock + bw * bw - 1, a.tinv_off[t + 1] - a.tinv_off[t],
+                a.status) ||
+      !PEERS_IN(int64_t(c0 + bw - 1) * ld + c0 + bw - 1, a.zoff[t + 1] - a.zoff[t], a.status))
+    return;
+  const double *TI = a.tinv + a.tinv_off[t] + int64_t(J) * kBlock * kBlock;
+  double *X = a.Z + a.zoff[t];
+  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
+    const int i = e % bw, j = e / bw;
+    X[int64_t(c0 + j) * ld + c0 + i] = i >= j ? TI[i * bw + j] : 0.0;
+  }
+}
+
+// One product of a doubling level: PHASE 0 forms W = B A^{-1}, PHASE 1 forms
+// X[c, a] = -C^{-1} W (see above), for the tile's rows and columns.
+template <int G, int PHASE>
+__global__ void __launch_bounds__(kRowsMaxThreads) k_tinv_gemm(const TinvTile *__restrict__ tiles,
+                                                               BiArgs a, double *Wd) {
+  __shared__ double Ms[kRowsK * rows_group_width(G)];
+  const TinvTile tl = tiles[blockIdx.x];
+  const int32_t t = tl.t;
+  const int32_t nc = a.first[t + 1] - a.first[t], N = nc + a.nb[t];
+  const int32_t ld = a.plen[t];
+  double *X = a.Z + a.zoff[t];
+  double *Wt = Wd + a.zoff[t];
+  const int64_t xext = a.zoff[t + 1] - a.zoff[t];
+  RowsGemm g;
+  if (PHASE == 0) {
+    g.A = a.panel + a.panel_off[t] + int64_t(tl.a0) * N + tl.c0;
+    g.lda = N;
+    g.B = X + int64_t(tl.a0) * ld + tl.a0;
+    g.kb = tl.col0;
+    g.ke = tl.ha;
+    g.negate = false;
+    g.a_ext = a.panel_off[t + 1] - a.panel_off[t] - (int64_t(tl.a0) * N + tl.c0);
+  } else {
+    g.A = X + int64_t(tl.c0) * ld + tl.c0;
+    g.lda = ld;
+    g.B = Wt + int64_t(tl.a0) * ld + tl.c0;
+    g.kb = 0;
+    g.ke = min(tl.hc, (tl.r + 1) * kTinvRows);
+    g.negate = true;
+    g.a_ext = xext - (int64_t(tl.c0) * ld + tl.c0);
+  }
+  g.bk = 1;
+  g.bc = ld;
+  g.out = (PHASE == 0 ? Wt : X) + int64_t(tl.a0) * ld + tl.c0;
+  g.oi = 1;
+  g.oc = ld;
+  g.nrows = tl.hc;
+  g.ncols = tl.ha;
+  g.b_ext = xext - (int64_t(tl.a0) * ld + (PHASE == 0 ? tl.a0 : tl.c0));
+  g.o_ext = xext - (int64_t(tl.a0) * ld + tl.c0);
+  g.status = a.status;
+  rows_gemm_dispatch<G>(g, Tile{t, tl.r, tl.col0, tl.w}, kTinvRows, Ms);
+}
+
+// The doubling plan of a list of wide supernodes: base blocks, then per level the tiles of
+// both products, grouped by width group (ptr: per level, 3 groups + 1 entries).
+struct TinvPlan {
+  std::vector<int32_t> base_sn, base_blk;
+  std::vector<TinvTile> tiles;
+  std::vector<std::vector<int64_t>> level_ptr;   // per level: 4 offsets into tiles
+};
+
+inline void tinv_plan_of(const Symbolic &S, const std::vector<int32_t> &wide, TinvPlan &T,
+                         std::vector<TinvTile> &all) {
+  for (int32_t t : wide)
+    for (int32_t J = 0; J * kBlock < sn_nc(S, t); ++J) {
+      T.base_sn.push_back(t);
+      T.base_blk.push_back(J);
+    }
+  for (int32_t s = kBlock;; s *= 2) {
+    std::vector<TinvTile> grp[3];
+    bool any = false;
+    for (int32_t t : wide) {
+      const int32_t nc = sn_nc(S, t);
+      for (int32_t a0 = 0; a0 + s < nc; a0 += 2 * s) {
+        any = true;
+        const int32_t c0 = a0 + s, ha = s, hc = std::min(s, nc - c0);
+        for (int32_t r = 0; r * kTinvRows < hc; ++r)
+          for (int32_t col0 = 0; col0 < ha; col0 += 32) {
+            const int w = rows_width(std::min(32, ha - col0));
+            grp[rows_group(w)].push_back({t, a0, c0, ha, hc, r, col0, w});
+          }
+      }
+    }
+    if (!any) break;
+    std::vector<int64_t> ptr;
+    ptr.push_back(static_cast<int64_t>(all.size()));
+    for (auto &g : grp) {
+      all.insert(all.end(), g.begin(), g.end());
+      ptr.push_back(static_cast<int64_t>(all.size()));
+    }
+    T.level_ptr.push_back(ptr);
+  }
+}
+
+template <int PHASE>
+int launch_tinv_level(const TinvTile *d_tiles, const std::vector<int64_t> &ptr, const BiArgs &a,
+                      double *Wd, cudaStream_t st, int64_t *launches, std::string &err) {
+  for (int g = 0; g < 2; ++g) {   // widths never exceed 32: groups 0 and 1
+    const int64_t n = ptr[g + 1] - ptr[g];
+    if (n <= 0) continue;
+    if (g == 0)
+      k_tinv_gemm<0, PHASE><<<static_cast<unsigned>(n), kTinvRows, 0, st>>>(d_tiles + ptr[g], a, Wd);
+    else
+      k_tinv_gemm<1, PHASE><<<static_cast<unsigned>(n), kTinvRows, 0, st>>>(d_tiles + ptr[g], a, Wd);
+    ++*launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  return PEERS_OK;
 }
 
 // Phase 2: Z[P_par, C_t] = -Z[P_par, B_t] * M_t for the supernodes of one depth, in tiles of
@@ -378,7 +552,8 @@ __device__ __forceinline__ void bi_z_tile(const Tile &tl, const BiArgs &a, doubl
       if (kk < kend) {
         const int row = R0 + r;
         const int32_t st = sst[k];
-        if (row < lp && row >= st) g = a.Z[ssrc[k] + (row - st)];
+        if (row < lp && row >= st && PEERS_IN(ssrc[k] + (row - st), a.ztotal, a.status))
+          g = a.Z[ssrc[k] + (row - st)];
         if (C0 + r < nc) m = Mt[int64_t(kk) * nc + C0 + r];
       }
       As[k * TS + r] = g;
@@ -405,7 +580,8 @@ __device__ __forceinline__ void bi_z_tile(const Tile &tl, const BiArgs &a, doubl
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = R0 + tx + 16 * u;
-      if (i < lp) Zt[int64_t(j) * ldt + nc + i] = -acc[u][v];
+      if (i < lp && PEERS_IN(int64_t(j) * ldt + nc + i, a.zoff[t + 1] - a.zoff[t], a.status))
+        Zt[int64_t(j) * ldt + nc + i] = -acc[u][v];
     }
   }
 }
@@ -471,6 +647,7 @@ __device__ __forceinline__ void bi_z_narrow(const Tile &tl, const BiArgs &a, dou
       for (int kk = 0; kk < kn; ++kk) {
         const int32_t st = gss[kk];
         if (i < st) break;   // staircase: later columns start further down
+        if (!PEERS_IN(gsr[kk] + (i - st), a.ztotal, a.status)) break;
         const double g = a.Z[gsr[kk] + (i - st)];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = fma(g, Ms[kk * NC + c], acc[c]);
@@ -482,7 +659,8 @@ __device__ __forceinline__ void bi_z_narrow(const Tile &tl, const BiArgs &a, dou
     double *Zt = a.Z + a.zoff[t];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
-      if (c < nc) Zt[int64_t(c) * ldt + nc + i] = -acc[c];
+      if (c < nc && PEERS_IN(int64_t(c) * ldt + nc + i, a.zoff[t + 1] - a.zoff[t], a.status))
+        Zt[int64_t(c) * ldt + nc + i] = -acc[c];
   }
 }
 
@@ -582,7 +760,7 @@ __global__ void k_bi_query(const BiQuery *__restrict__ qs, int64_t nq, BiArgs a,
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) R[q.out] = acc;
+  if (lane == 0 && PEERS_IN(q.out, a.nq, a.status)) R[q.out] = acc;
 }
 
 // ================================================================ selected inversion
@@ -607,6 +785,8 @@ struct SiArgs {
   const int64_t *moff;
   const int64_t *foff;    // offset of F(s) in F (each lane's region alternates by depth)
   double *F;              // inverse fronts
+  int *status;            // error flag (bounds-checked build)
+  int64_t fbuf, nq;       // extents of F and of the results
 };
 
 // Sigma[B,B] of each supernode of this depth from its parent's front.  grid = (supernode,
@@ -621,11 +801,15 @@ __global__ void __launch_bounds__(256) k_si_gather(const int32_t *__restrict__ s
   const int32_t *rm = a.rmap + a.rows_off[s];
   const double *Fp = a.F + a.foff[p];
   double *F = a.F + a.foff[s];
+  if (!PEERS_IN(a.foff[s] + int64_t(N) * N - 1, a.fbuf, a.status) ||
+      !PEERS_IN(a.foff[p] + int64_t(Np) * Np - 1, a.fbuf, a.status))
+    return;
   for (int32_t j = j0; j < min(nbv, j0 + 8); ++j) {
     const int32_t rj = rm[j];
     for (int32_t i = threadIdx.x; i < nbv; i += blockDim.x) {
       const int32_t ri = rm[i];
-      F[int64_t(nc + j) * N + nc + i] = Fp[int64_t(min(ri, rj)) * Np + max(ri, rj)];
+      if (PEERS_IN(max(ri, rj), Np, a.status))
+        F[int64_t(nc + j) * N + nc + i] = Fp[int64_t(min(ri, rj)) * Np + max(ri, rj)];
     }
   }
 }
@@ -654,6 +838,10 @@ __global__ void __launch_bounds__(kRowsMaxThreads) k_si_bc(const Tile *__restric
   g.ke = nbv;
   g.ncols = nc;
   g.negate = true;
+  g.a_ext = a.fbuf - (a.foff[s] + int64_t(nc) * N + nc);
+  g.b_ext = a.moff[s + 1] - a.moff[s];
+  g.o_ext = a.fbuf - (a.foff[s] + nc);
+  g.status = a.status;
   rows_gemm_dispatch<G>(g, tl, rows, Ms);
 }
 
@@ -669,6 +857,10 @@ __device__ __forceinline__ void si_cc_tile(const Tile &tl, const SiArgs &a, doub
   const double *Zd = a.Zd + a.doff[s];
   const double *M = a.M + a.moff[s];
   const int R0 = tl.r * TS, C0 = tl.c * TS;
+  if (!PEERS_IN(a.foff[s] + int64_t(N) * N - 1, a.fbuf, a.status) ||
+      !PEERS_IN(int64_t(nc) * nc - 1, a.doff[s + 1] - a.doff[s], a.status) ||
+      !(nbv == 0 || PEERS_IN(int64_t(nbv) * nc - 1, a.moff[s + 1] - a.moff[s], a.status)))
+    return;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   double acc[U][U] = {};
   // Zd^T D^{-1} Zd: Zd[k, i] Zd[k, j] is non-zero only for k >= max(i, j)
@@ -756,6 +948,11 @@ __global__ void __launch_bounds__(256) k_si_small(const int32_t *__restrict__ sn
   const int32_t p = a.parent[s];
   const int tid = threadIdx.x;
   const double *TI = b.tinv + b.tinv_off[s];
+  if (!PEERS_IN(int64_t(N) * N + nc * nc + nbv * nc + nc - 1, dynamic_smem_doubles(), a.status) ||
+      !PEERS_IN(a.foff[s] + int64_t(N) * N - 1, a.fbuf, a.status) ||
+      !PEERS_IN(int64_t(nc) * nc - 1, b.tinv_off[s + 1] - b.tinv_off[s], a.status) ||
+      !PEERS_IN(int64_t(nc) * N - 1, b.panel_off[s + 1] - b.panel_off[s], a.status))
+    return;
   for (int e = tid; e < nc * nc; e += blockDim.x) Ti[e] = TI[e];
   for (int e = tid; e < nc; e += blockDim.x) dv[e] = a.dinv[f + e];
   if (p >= 0) {
@@ -765,7 +962,9 @@ __global__ void __launch_bounds__(256) k_si_small(const int32_t *__restrict__ sn
     for (int e = tid; e < nbv * nbv; e += blockDim.x) {
       const int i = e % nbv, j = e / nbv;
       const int32_t ri = rm[i], rj = rm[j];
-      F[(nc + j) * N + nc + i] = Fp[int64_t(min(ri, rj)) * Np + max(ri, rj)];
+      if (PEERS_IN(max(ri, rj), Np, a.status) &&
+          PEERS_IN(a.foff[p] + int64_t(Np) * Np - 1, a.fbuf, a.status))
+        F[(nc + j) * N + nc + i] = Fp[int64_t(min(ri, rj)) * Np + max(ri, rj)];
     }
   }
   __syncthreads();
@@ -800,6 +999,9 @@ __global__ void __launch_bounds__(256) k_si_small(const int32_t *__restrict__ sn
   for (int e = tid; e < N * N; e += blockDim.x) Fg[e] = F[e];
   for (int64_t q = b.qbeg[s] + tid; q < b.qbeg[s + 1]; q += blockDim.x) {
     const int32_t qa = b.qa[q], qb = b.qb[q];
+    if (!PEERS_IN(qa, N, a.status) || (qb >= 0 && !PEERS_IN(qb, N, a.status)) ||
+        !PEERS_IN(b.qorig[q], a.nq, a.status))
+      continue;
     double r = F[qa * N + qa];
     if (qb >= 0) r += F[qb * N + qb] - 2.0 * F[min(qa, qb) * N + max(qa, qb)];
     b.R[b.qorig[q]] = r;
@@ -812,6 +1014,10 @@ __global__ void k_si_query(const SiQuery *__restrict__ qs, int64_t nq, SiArgs ar
   const SiQuery q = qs[k];
   const int32_t N = args.first[q.s + 1] - args.first[q.s] + args.nb[q.s];
   const double *F = args.F + args.foff[q.s];
+  if (!PEERS_IN(q.a, N, args.status) || (q.b >= 0 && !PEERS_IN(q.b, N, args.status)) ||
+      !PEERS_IN(q.out, args.nq, args.status) ||
+      !PEERS_IN(args.foff[q.s] + int64_t(N) * N - 1, args.fbuf, args.status))
+    return;
   double r = F[int64_t(q.a) * N + q.a];
   if (q.b >= 0) r += F[int64_t(q.b) * N + q.b] - 2.0 * F[int64_t(min(q.a, q.b)) * N + max(q.a, q.b)];
   R[q.out] = r;
@@ -1060,10 +1266,15 @@ struct SiGroup {
   int64_t q_b = 0, q_e = 0;
 };
 
-// Phase 1 (T^{-1} and M) of one lane's supernodes (index lane + 1).
+// Phase 1 (T^{-1} and M) of one lane's supernodes, or of one depth of the top part
+// (lane -1), whose groups wait for it.
 struct SiPhase1 {
-  int64_t small_b = 0, small_e = 0, diag_b = 0, diag_e = 0;
-  std::vector<int64_t> m_ptr;   // 4 entries into m_tiles
+  int32_t lane = -1, depth = 0;
+  int64_t small_b = 0, small_e = 0;             // narrow supernodes (k_bi_small)
+  int64_t diag_b = 0, diag_e = 0;               // wide: T^{-1} by substitution (k_bi_diag)
+  int64_t base_b = 0, base_e = 0;               // wide: X's diagonal blocks (k_tinv_base)
+  std::vector<std::vector<int64_t>> tlevels;    // wide: doubling levels, into tinv_tiles
+  std::vector<int64_t> m_ptr;                   // 4 entries into m_tiles
 };
 
 struct SelInvPlan {
@@ -1074,18 +1285,18 @@ struct SelInvPlan {
   int64_t fbuf = 0;                                // doubles of the fronts buffer
   int32_t nlanes = 0;
   std::vector<SiGroup> groups;                     // top part by depth, then lanes by depth
-  std::vector<SiPhase1> phase1;                    // per lane + 1
+  std::vector<SiPhase1> phase1;                    // top part by depth, then per lane
   std::vector<int32_t> gather_sn;
   std::vector<Tile> bc, cc;
   std::vector<SiQuery> queries;
   std::vector<int32_t> fused_sn;                   // whole small supernodes
-  std::vector<int32_t> small_sn, small_chunk, diag_sn, diag_blk;
+  std::vector<int32_t> small_sn, small_chunk, diag_sn, diag_blk, tbase_sn, tbase_blk;
+  std::vector<TinvTile> tinv_tiles;
   std::vector<Tile> m_tiles;
   int64_t fma = 0;
 };
 
-// sms: the device's multiprocessor count (sizes the launches).  The groups of the lanes run
-// concurrently on the lanes' streams, so each is sized for its share of the device.
+// sms: the device's multiprocessor count (sizes the launches).
 int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
   if (S.nq_two > 0) {
     err = "the selected inverse covers pairs inside the pattern of L (every graph edge and "
@@ -1140,15 +1351,24 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
   auto fused = [&](int32_t t) {
     return sn_nc(S, t) <= kBlock && sn_nc(S, t) + S.nb[t] <= kSiSmallN;
   };
-  // phase 1 (T^{-1} and M) as in the block inverse, per lane, for the supernodes not fused
-  P.phase1.assign(nl + 1, SiPhase1{});
-  for (int32_t L = 0; L <= nl; ++L) {
-    SiPhase1 &ph = P.phase1[L];
-    std::vector<int32_t> wide;
+  // phase 1 (T^{-1} and M) as in the block inverse, for the supernodes not fused: the top
+  // part depth by depth (each depth's groups wait only for their own phase 1, so the deeper
+  // ones overlap the top of the tree), then each lane's supernodes
+  P.phase1.clear();
+  std::vector<std::pair<int32_t, int32_t>> p1keys;   // (lane, depth or -1 for all)
+  for (int32_t d = 0; d <= maxd; ++d)
+    if (!members[0][d].empty()) p1keys.push_back({-1, d});
+  for (int32_t L = 0; L < nl; ++L) p1keys.push_back({L, -1});
+  for (const auto &key : p1keys) {
+    SiPhase1 ph;
+    ph.lane = key.first;
+    ph.depth = key.second;
+    std::vector<int32_t> wide, doubling;
     ph.small_b = static_cast<int64_t>(P.small_sn.size());
     ph.diag_b = static_cast<int64_t>(P.diag_sn.size());
     for (int32_t t = 0; t < ns; ++t) {
-      if (S.lane_of[t] + 1 != L || fused(t)) continue;
+      if (S.lane_of[t] != key.first || (key.second >= 0 && S.depth[t] != key.second) || fused(t))
+        continue;
       const int32_t nc = sn_nc(S, t), nbv = S.nb[t];
       if (nc <= kBlock) {
         for (int32_t ch = 0; ch == 0 || ch * 256 < nbv; ++ch) {
@@ -1157,25 +1377,42 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
         }
         continue;
       }
+      wide.push_back(t);
+      if (nc >= kTinvDoubling) {
+        doubling.push_back(t);
+        continue;
+      }
       for (int32_t J = 0; J * kBlock < nc; ++J)
         for (int32_t sl = 0; sl < kDiagSlices && J * kBlock + sl * kDiagSlice < nc; ++sl) {
           P.diag_sn.push_back(t);
           P.diag_blk.push_back(J * kDiagSlices + sl);
         }
-      wide.push_back(t);
     }
     ph.small_e = static_cast<int64_t>(P.small_sn.size());
     ph.diag_e = static_cast<int64_t>(P.diag_sn.size());
+    {
+      TinvPlan T;
+      tinv_plan_of(S, doubling, T, P.tinv_tiles);
+      ph.base_b = static_cast<int64_t>(P.tbase_sn.size());
+      P.tbase_sn.insert(P.tbase_sn.end(), T.base_sn.begin(), T.base_sn.end());
+      P.tbase_blk.insert(P.tbase_blk.end(), T.base_blk.begin(), T.base_blk.end());
+      ph.base_e = static_cast<int64_t>(P.tbase_sn.size());
+      ph.tlevels = std::move(T.level_ptr);
+    }
     std::vector<Tile> mt;
     std::vector<int64_t> mp;
     m_tiles_of(S, wide, mt, mp);
     const int64_t off = static_cast<int64_t>(P.m_tiles.size());
     P.m_tiles.insert(P.m_tiles.end(), mt.begin(), mt.end());
     for (int64_t x : mp) ph.m_ptr.push_back(off + x);
+    P.phase1.push_back(std::move(ph));
   }
   // groups: the top part depth by depth, then the lanes, depth by depth
   for (int32_t L = 0; L <= nl; ++L) {
-    const int64_t target_ctas = int64_t(std::max(sms, 1)) * 16 / (L == 0 ? 1 : std::max(nl, 1));
+    // every launch is sized as if alone: the lanes overlap, but a launch of few one-warp CTAs
+    // leaves the FP64 units of its SMs half idle (two to three warps per SM sub-partition
+    // keep them busy)
+    const int64_t target_ctas = int64_t(std::max(sms, 1)) * 16;
     for (int32_t d = 0; d <= maxd; ++d) {
       const std::vector<int32_t> &mem = members[L][d];
       if (mem.empty()) continue;
@@ -1387,6 +1624,9 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   a.parent = static_cast<int32_t *>(dpar);
   a.gstart = static_cast<int32_t *>(dgs);
   a.gsrc = static_cast<int64_t *>(dgsrc);
+  a.status = num->status;
+  a.ztotal = B.ztotal;
+  a.nq = S.nq;
   double *Rdev = R;
   const bool host_out = !(flags & PEERS_OUT_DEVICE);
   if (host_out) {
@@ -1444,6 +1684,7 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
     rc = PEERS_ECUDA;
     err = cudaGetErrorString(e);
   }
+  if (rc == PEERS_OK) rc = check_bounds_flag(num->status, st, "peers_query_blockinv", err);
   cleanup();
   return rc;
 }
@@ -1501,12 +1742,14 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   const peers::SelInvPlan &P = *plan;
   const peers::Lanes *lanes = P.nlanes > 0 ? ctx_lanes(ctx) : nullptr;
   DevMem mem(&err);
-  double *Zd, *M, *F, *Rdev = R;
-  int32_t *ncs, *gsn, *ssn, *sch, *dsn, *dblk;
+  double *Zd, *Wd, *M, *F, *Rdev = R;
+  int32_t *ncs, *gsn, *ssn, *sch, *dsn, *dblk, *tbs, *tbb;
   int64_t *doff, *moff, *foff;
   peers::Tile *bc, *cc, *mt;
+  peers::TinvTile *tt;
   peers::SiQuery *qs;
   RC_TRY(mem.alloc(&Zd, P.dtotal));
+  RC_TRY(mem.alloc(&Wd, P.dtotal));
   RC_TRY(mem.alloc(&M, P.mtotal));
   RC_TRY(mem.alloc(&F, P.fbuf));
   RC_TRY(mem.upload(&ncs, P.ncs, st));
@@ -1521,6 +1764,9 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   RC_TRY(mem.upload(&sch, P.small_chunk, st));
   RC_TRY(mem.upload(&dsn, P.diag_sn, st));
   RC_TRY(mem.upload(&dblk, P.diag_blk, st));
+  RC_TRY(mem.upload(&tbs, P.tbase_sn, st));
+  RC_TRY(mem.upload(&tbb, P.tbase_blk, st));
+  RC_TRY(mem.upload(&tt, P.tinv_tiles, st));
   RC_TRY(mem.upload(&mt, P.m_tiles, st));
   int32_t *fsn;
   int64_t *qbeg;
@@ -1538,13 +1784,15 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
     RC_TRY(peers::raise_smem_limit(reinterpret_cast<const void *>(peers::k_si_small),
                                    si_small_smem, need, err));
   }
+  // the part above the lanes (phase 1 and depths) runs on the high-priority top stream
+  const cudaStream_t ts = lanes ? lanes->top : st;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   std::vector<cudaEvent_t> ev;
-  auto mark = [&]() {
+  auto mark = [&](cudaStream_t on) {
     if (ctx->timing) {
       cudaEvent_t e;
       cudaEventCreate(&e);
-      cudaEventRecord(e, st);
+      cudaEventRecord(e, on);
       ev.push_back(e);
     }
   };
@@ -1560,9 +1808,10 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   const int nl = lanes ? P.nlanes : 0;
   if (nl > 0) {
     CUDA_TRY(cudaEventRecord(lanes->start, st));
+    CUDA_TRY(cudaStreamWaitEvent(ts, lanes->start, 0));
     for (int L = 0; L < nl; ++L) CUDA_TRY(cudaStreamWaitEvent(lanes->stream[L], lanes->start, 0));
   }
-  auto stream_of = [&](int32_t lane) { return (lane >= 0 && nl > 0) ? lanes->stream[lane] : st; };
+  auto stream_of = [&](int32_t lane) { return (lane >= 0 && nl > 0) ? lanes->stream[lane] : ts; };
   peers::BiArgs b{};
   b.panel = num->panel;
   b.tinv = num->tinv;
@@ -1577,11 +1826,35 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   b.plen = ncs;
   b.Z = Zd;
   b.M = M;
-  // phase 1: T^{-1} (into Zd, ld = n_c) and M, by the block inverse's kernels, lane by lane
-  // (P.phase1[0] is the top part)
-  for (int32_t L = 0; L <= P.nlanes; ++L) {
-    const peers::SiPhase1 &ph = P.phase1[L];
-    const cudaStream_t ls = stream_of(L - 1);
+  b.status = num->status;
+  b.ztotal = P.dtotal;
+  b.nq = S.nq;
+  // phase 1: T^{-1} (into Zd, ld = n_c) and M, by the block inverse's kernels: the top part's
+  // depth by depth on the second top stream (each depth's event releases its groups), the
+  // lanes' on their own streams
+  const cudaStream_t ts1 = lanes ? lanes->top1 : st;
+  if (nl > 0) CUDA_TRY(cudaStreamWaitEvent(ts1, lanes->start, 0));
+  std::vector<cudaEvent_t> p1_done(P.phase1.size(), nullptr);
+  struct EventsGuard {
+    std::vector<cudaEvent_t> &v;
+    ~EventsGuard() {
+      for (cudaEvent_t e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } p1_guard{p1_done};
+  std::vector<int32_t> p1_of_depth;
+  bool lanes_released = false;
+  for (size_t k = 0; k < P.phase1.size(); ++k) {
+    const peers::SiPhase1 &ph = P.phase1[k];
+    const cudaStream_t ls = ph.lane >= 0 ? stream_of(ph.lane) : ts1;
+    if (ph.lane >= 0 && !lanes_released && k > 0 && p1_done[k - 1]) {
+      // the lanes' phase 1 starts once the top part's is done: the top part is the critical
+      // path, and its short launches would otherwise queue behind the lanes' long CTAs
+      // (stream priorities order the CTAs waiting for an SM, they do not preempt running ones)
+      for (int L = 0; L < nl; ++L)
+        CUDA_TRY(cudaStreamWaitEvent(lanes->stream[L], p1_done[k - 1], 0));
+      lanes_released = true;
+    }
     if (ph.small_e > ph.small_b) {
       peers::k_bi_small<<<static_cast<unsigned>(ph.small_e - ph.small_b), 256, 0, ls>>>(
           ssn + ph.small_b, sch + ph.small_b, b);
@@ -1593,10 +1866,24 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
                                                                      dblk + ph.diag_b, b);
       ++launches;
     }
+    if (ph.base_e > ph.base_b) {
+      peers::k_tinv_base<<<static_cast<unsigned>(ph.base_e - ph.base_b), 256, 0, ls>>>(
+          tbs + ph.base_b, tbb + ph.base_b, b);
+      ++launches;
+    }
+    for (const auto &lv : ph.tlevels) {
+      RC_TRY(peers::launch_tinv_level<0>(tt, lv, b, Wd, ls, &launches, err));
+      RC_TRY(peers::launch_tinv_level<1>(tt, lv, b, Wd, ls, &launches, err));
+    }
     RC_TRY(peers::launch_m_all(mt, ph.m_ptr, b, ls, &launches, err));
     CUDA_TRY(cudaGetLastError());
+    if (ph.lane < 0 && ts1 != ts) {
+      CUDA_TRY(cudaEventCreateWithFlags(&p1_done[k], cudaEventDisableTiming));
+      CUDA_TRY(cudaEventRecord(p1_done[k], ts1));
+      if (p1_of_depth.size() <= size_t(ph.depth)) p1_of_depth.resize(ph.depth + 1, -1);
+      p1_of_depth[ph.depth] = static_cast<int32_t>(k);
+    }
   }
-  mark();
   // phase 2: top-down by depth, the top part first, then every lane on its own stream
   peers::SiArgs a{};
   a.dinv = num->dinv;
@@ -1611,6 +1898,9 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   a.foff = foff;
   a.parent = par;
   a.F = F;
+  a.status = num->status;
+  a.fbuf = P.fbuf;
+  a.nq = S.nq;
   peers::SiSmallArgs sb{};
   sb.panel = num->panel;
   sb.tinv = num->tinv;
@@ -1625,12 +1915,14 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   for (const peers::SiGroup &G : P.groups) {
     if (G.lane >= 0 && !top_done) {
       // the lanes' first depth reads the top part's last fronts
-      CUDA_TRY(cudaEventRecord(lanes->top_done, st));
+      CUDA_TRY(cudaEventRecord(lanes->top_done, ts));
       for (int L = 0; L < nl; ++L)
         CUDA_TRY(cudaStreamWaitEvent(lanes->stream[L], lanes->top_done, 0));
       top_done = true;
     }
     const cudaStream_t gs = stream_of(G.lane);
+    if (G.lane < 0 && size_t(G.depth) < p1_of_depth.size() && p1_of_depth[G.depth] >= 0)
+      CUDA_TRY(cudaStreamWaitEvent(gs, p1_done[p1_of_depth[G.depth]], 0));
     if (G.fused_e > G.fused_b) {
       peers::k_si_small<<<static_cast<unsigned>(G.fused_e - G.fused_b), 256, G.fused_smem, gs>>>(
           fsn + G.fused_b, a, sb);
@@ -1663,19 +1955,18 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
       ++launches;
     }
     CUDA_TRY(cudaGetLastError());
-    if (G.lane < 0) mark();
+    if (G.lane < 0) mark(ts);
   }
   if (nl > 0) {
-    if (!top_done) {
-      CUDA_TRY(cudaEventRecord(lanes->top_done, st));
-      for (int L = 0; L < nl; ++L)
-        CUDA_TRY(cudaStreamWaitEvent(lanes->stream[L], lanes->top_done, 0));
-    }
+    CUDA_TRY(cudaEventRecord(lanes->top_done, ts));
+    CUDA_TRY(cudaStreamWaitEvent(st, lanes->top_done, 0));
+    CUDA_TRY(cudaEventRecord(lanes->top_done, ts1));
+    CUDA_TRY(cudaStreamWaitEvent(st, lanes->top_done, 0));
     for (int L = 0; L < nl; ++L) {
       CUDA_TRY(cudaEventRecord(lanes->done[L], lanes->stream[L]));
       CUDA_TRY(cudaStreamWaitEvent(st, lanes->done[L], 0));
     }
-    mark();
+    mark(st);
   }
   if (ctx->timing) {
     cudaEventRecord(e1, st);
@@ -1683,8 +1974,8 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     ctx->stats.sweep_s = ms * 1e-3;
-    // phase 1 (the top part's; the lanes' runs beside it), each depth of the top part, and
-    // the lanes' subtrees (concurrent streams) as one entry
+    // each depth of the top part (with the wait for its phase 1, which runs beside the
+    // depths above it), and the lanes' subtrees (concurrent streams) as one entry
     ctx->level_ms.clear();
     cudaEventElapsedTime(&ms, e0, ev[0]);
     ctx->level_ms.push_back(ms);
@@ -1704,7 +1995,7 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
     ctx->stats.d2h_bytes = int64_t(sizeof(double)) * S.nq;
   }
   CUDA_TRY(cudaStreamSynchronize(st));
-  return PEERS_OK;
+  return check_bounds_flag(num->status, st, "peers_query_selinv", err);
 }
 
 }  // namespace

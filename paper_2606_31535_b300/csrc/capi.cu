@@ -141,6 +141,8 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
   TRY(dalloc(num, &num->tinv, S.tinv_total, err));
   TRY(dalloc(num, &num->d, S.nr, err));
   TRY(dalloc(num, &num->dinv, S.nr, err));
+  TRY(dalloc(num, &num->status, 2, err));
+  CUDA_TRY(cudaMemsetAsync(num->status, 0, 2 * sizeof(int), st));
   // factorization-only data (freed below)
   std::vector<double> vals;
   peers::assembly_values(S, w ? w : S.w0.data(), vals);
@@ -163,7 +165,7 @@ int factor_impl(peers_ctx *ctx, const peers_symbolic *sym, const double *w, peer
   TRY(dalloc(num, &status, 2, err));
   D.args = peers::FactorArgs{num->panel, U, num->tinv, num->d, num->dinv, num->first, num->nb,
                              num->rmap, num->panel_off, num->tinv_off, u_off, num->rows_off,
-                             status};
+                             status, S.panel_total};
   D.a_dest = a_dest;
   D.a_val = a_val;
   D.fac_sn = fac_sn;
@@ -231,10 +233,34 @@ int factor_from_pool(peers_ctx *ctx, const peers_symbolic *sym, const double *w,
   return PEERS_OK;
 }
 
+int check_bounds_flag(int *d_status, cudaStream_t stream, const char *what, std::string &err) {
+#if defined(PEERS_BOUNDS) && PEERS_BOUNDS
+  if (!d_status) return PEERS_OK;
+  int h[2] = {0, 0};
+  CUDA_TRY(cudaMemcpyAsync(h, d_status, sizeof(h), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(h), stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  if (h[0] == peers::kErrBounds) {
+    err = std::string(what) + ": out-of-bounds access skipped at source line " + std::to_string(h[1]);
+    return PEERS_ECUDA;
+  }
+#else
+  (void)d_status;
+  (void)stream;
+  (void)what;
+  (void)err;
+#endif
+  return PEERS_OK;
+}
+
 const peers::Lanes *ctx_lanes(peers_ctx *ctx) {
   if (ctx->lanes_ready) return &ctx->lanes;
   peers::Lanes L{};
-  bool ok = cudaEventCreateWithFlags(&L.start, cudaEventDisableTiming) == cudaSuccess &&
+  int least = 0, greatest = 0;
+  bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&L.top, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&L.top1, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+            cudaEventCreateWithFlags(&L.start, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&L.top_done, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; i < peers::kLanes && ok; ++i)
     ok = cudaStreamCreateWithFlags(&L.stream[i], cudaStreamNonBlocking) == cudaSuccess &&
@@ -304,6 +330,10 @@ int query_impl(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, do
   a.spill = num->spill;
   a.spill_stride = S.spill_stride;
   a.spill_counter = num->spill_counter;
+  a.status = num->status;
+  a.carry_slots = S.carry_slots;
+  a.nq = S.nq;
+  a.nldesc = static_cast<int64_t>(S.ldesc.size());
   std::vector<cudaEvent_t> ev;
   if (ctx->timing) {
     ev.resize(2 * static_cast<size_t>(S.nlevels));
@@ -343,7 +373,7 @@ int query_impl(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, do
   }
   CUDA_TRY(cudaStreamSynchronize(st));
   CUDA_TRY(cudaGetLastError());
-  return PEERS_OK;
+  return check_bounds_flag(num->status, st, "peers_query", err);
 }
 
 }  // namespace
@@ -411,6 +441,8 @@ void peers_destroy(peers_ctx *ctx) {
       }
       cudaEventDestroy(ctx->lanes.start);
       cudaEventDestroy(ctx->lanes.top_done);
+      cudaStreamDestroy(ctx->lanes.top);
+      cudaStreamDestroy(ctx->lanes.top1);
     }
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   }
@@ -584,11 +616,16 @@ int peers_query_noalloc(peers_ctx *ctx, const peers_symbolic *sym, const peers_n
   a.qorig = num->qorig;
   a.ldesc = num->ldesc;
   a.nbmax = S.nbmax;
+  a.status = num->status;
+  a.carry_slots = S.carry_slots;
+  a.nq = S.nq;
+  a.nldesc = static_cast<int64_t>(S.ldesc.size());
   std::string err;
   int64_t launches = 0;
   int rc = peers::query_noalloc(ctx->stream, ctx->device, S, a, num->items,
                                 num->wave_item_off.data(), num->two_user, num->two_a,
                                 num->two_b, R_device, &launches, err);
+  if (rc == PEERS_OK) rc = check_bounds_flag(num->status, ctx->stream, "peers_query_noalloc", err);
   if (rc != PEERS_OK) return fail(rc, err);
   ctx->stats.sweep_launches = launches;
   ctx->stats.h2d_bytes = 0;

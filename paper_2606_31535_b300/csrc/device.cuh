@@ -49,10 +49,34 @@ class DeviceGuard {
   CUDA_TRY(device_guard_.status())
 
 constexpr int kErrNotSpd = 1;
+constexpr int kErrBounds = 2;
+
+// Bounds checks of the PEERS_BOUNDS=1 build (libpeers_bounds.so): PEERS_IN(i, n, status) is
+// true when 0 <= i < n; otherwise it records kErrBounds and the source line in `status` (the
+// first failure wins) and is false, and the caller skips the access.  In the regular build
+// it is the constant true and costs nothing.
+#if defined(PEERS_BOUNDS) && PEERS_BOUNDS
+#define PEERS_IN(i, n, status) ::peers::in_bounds((i), (n), (status), __LINE__)
+#else
+#define PEERS_IN(i, n, status) true
+#endif
 
 // Records the first error code and where it happened; later errors are dropped.
 __device__ inline void flag_error(int *status, int code, int where) {
   if (atomicCAS(status, 0, code) == 0) atomicExch(status + 1, where);
+}
+
+__device__ inline bool in_bounds(int64_t i, int64_t n, int *status, int line) {
+  if (i >= 0 && i < n) return true;
+  if (status) flag_error(status, kErrBounds, line);
+  return false;
+}
+
+// Dynamic shared memory of the running launch, in doubles.
+__device__ inline int64_t dynamic_smem_doubles() {
+  uint32_t bytes;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(bytes));
+  return bytes / 8;
 }
 
 // Device pointers used by the factorization kernels.
@@ -61,6 +85,7 @@ struct FactorArgs {
   const int32_t *first, *nb, *rmap;
   const int64_t *panel_off, *tinv_off, *u_off, *rows_off;
   int *status;
+  int64_t panel_total;   // extent of `panel` (bounds-checked build)
 };
 
 struct FactorDevice {
@@ -95,15 +120,22 @@ struct SweepArgs {
   double *spill;
   int64_t spill_stride;
   int *spill_counter;
+  // extents for the bounds-checked build: error flag (2 ints), carry slots, results, the
+  // two-branch step list
+  int *status;
+  int64_t carry_slots, nq, nldesc;
 };
 
 // CUDA streams over which a call spreads the lanes' independent subtrees (see kLanes), and
 // the events that order them against the context's stream.
 struct Lanes {
   cudaStream_t stream[kLanes];
+  cudaStream_t top, top1;     // the device's highest stream priority: the part above the
+                              // lanes, on the critical path, gets SMs first (top1 carries
+                              // work that overlaps the top stream's, e.g. its phase 1)
   cudaEvent_t done[kLanes];   // recorded on a lane's stream when its work is issued
   cudaEvent_t start;          // recorded on the context's stream where the lanes may begin
-  cudaEvent_t top_done;       // recorded on the context's stream when the top part is issued
+  cudaEvent_t top_done;       // recorded on the top stream when the top part is issued
 };
 
 // Runs the whole factorization on `stream` (and the lanes' subtrees on `lanes`' streams when

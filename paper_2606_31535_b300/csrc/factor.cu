@@ -25,10 +25,11 @@ namespace peers {
 
 // panel[dest[e]] = val[e]: the entries of L_r (off-diagonals -w, diagonals = degrees).
 __global__ void k_assemble(const int64_t *__restrict__ dest, const double *__restrict__ val,
-                           int64_t cnt, double *__restrict__ panel) {
+                           int64_t cnt, double *__restrict__ panel, int64_t panel_total,
+                           int *status) {
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < cnt;
        e += int64_t(gridDim.x) * blockDim.x)
-    panel[dest[e]] = val[e];
+    if (PEERS_IN(dest[e], panel_total, status)) panel[dest[e]] = val[e];
 }
 
 // One CTA per (pair, chunk of 8 child columns).  pairs = (parent, child) interleaved.
@@ -44,100 +45,150 @@ __global__ void __launch_bounds__(256) k_extend_add(const int32_t *__restrict__ 
   const double *Uc = a.U + a.u_off[c];
   double *Pp = a.panel + a.panel_off[p];
   double *Up = a.U + a.u_off[p];
+#if defined(PEERS_BOUNDS) && PEERS_BOUNDS
+  const int64_t pext = a.panel_off[p + 1] - a.panel_off[p], uext = a.u_off[p + 1] - a.u_off[p];
+  if (!PEERS_IN(int64_t(nbc) * nbc - 1, a.u_off[c + 1] - a.u_off[c], a.status) ||
+      !PEERS_IN(nbc - 1, a.rows_off[c + 1] - a.rows_off[c], a.status))
+    return;
+#endif
   for (int32_t j = j0; j < j1; ++j) {
     const int32_t rj = rm[j];
     for (int32_t i = j + threadIdx.x; i < nbc; i += blockDim.x) {
       const double v = Uc[int64_t(j) * nbc + i];
       const int32_t ri = rm[i];
-      if (rj < ncp)
-        Pp[int64_t(rj) * Np + ri] += v;
-      else
+      if (rj < ncp) {
+        if (PEERS_IN(int64_t(rj) * Np + ri, pext, a.status)) Pp[int64_t(rj) * Np + ri] += v;
+      } else if (PEERS_IN(int64_t(rj - ncp) * nbp + (ri - ncp), uext, a.status) &&
+                 PEERS_IN(ri - ncp, nbp, a.status)) {
         Up[int64_t(rj - ncp) * nbp + (ri - ncp)] += v;
+      }
     }
   }
 }
 
-// Diagonal block J of each active supernode: dense L D L^T without pivoting (L_r is SPD),
-// then the inverse of the unit-lower block for the sweep.  One CTA (one warp) per supernode.
-__global__ void __launch_bounds__(32) k_diag_block(const int32_t *__restrict__ sns, int32_t J,
-                                                   FactorArgs a) {
+// Dense L D L^T of the bw x bw lower block A (shared memory, A[i][j] = row i, column j)
+// without pivoting (L_r is SPD): afterwards A holds L below the diagonal (unit diagonal
+// implied) and d on it.  Step k scales column k by 1/d_k, then every (i, j) with
+// k < j <= i takes A[i][j] -= (L[i][k] d_k) L[j][k]; the pairs of a step are shared by all
+// threads of the CTA, so a step costs one multiply-add per thread instead of a row's worth.
+__device__ void ldlt_block(double (*A)[kBlock + 1], int bw, int *status, int col0) {
+  for (int k = 0; k < bw; ++k) {
+    const double dk = A[k][k];
+    if (threadIdx.x == 0 && !(dk > 0.0 && dk < INFINITY)) flag_error(status, kErrNotSpd, col0 + k);
+    for (int i = k + 1 + threadIdx.x; i < bw; i += blockDim.x) A[i][k] = A[i][k] / dk;
+    __syncthreads();
+    const int m = bw - k - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) A[i][j] = fma(-(A[i][k] * dk), A[j][k], A[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+// X = the inverse of the unit-lower L held below the diagonal of A, by column sweeps: X
+// starts as the identity and step k takes X[i][j] -= L[i][k] X[k][j] for i > k >= j.  Every
+// entry adds its terms in increasing k, as row-by-row substitution does.
+__device__ void unit_lower_inverse(const double (*A)[kBlock + 1], double (*X)[kBlock + 1],
+                                   int bw) {
+  for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
+    const int i = e / kBlock, j = e % kBlock;
+    X[i][j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < bw; ++k) {
+    const int rows = bw - k - 1, cols = k + 1;
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int i = k + 1 + e / cols, j = e % cols;
+      X[i][j] = fma(-A[i][k], X[k][j], X[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+// Row i of the panel below the diagonal block: w = F[i, J] L_JJ^{-T}, then L[i, J] = w / d,
+// from the block's inverse X: w_k = sum_{j <= k} F[i][j] X[k][j].  The columns k of a row are
+// independent sums, dealt to kPanelSplit threads (k = q, q + kPanelSplit, ...).
+constexpr int kPanelSplit = 4;
+__device__ __forceinline__ void panel_row_from_inverse(const double *Frow, int64_t fstride,
+                                                       const double (*X)[kBlock + 1],
+                                                       const double *dk, int bw, int q,
+                                                       double *Lrow, int64_t lstride) {
+  for (int k = q; k < bw; k += kPanelSplit) {
+    double w = 0.0;
+    for (int j = 0; j <= k; ++j) w = fma(Frow[j * fstride], X[k][j], w);
+    Lrow[k * lstride] = w / dk[k];
+  }
+}
+
+// Diagonal block J of each active supernode: dense L D L^T without pivoting, its d and 1/d,
+// and the inverse of the unit-lower block (used by the panel rows and the sweep).  One CTA
+// of 256 threads per supernode.
+__global__ void __launch_bounds__(256) k_diag_block(const int32_t *__restrict__ sns, int32_t J,
+                                                    FactorArgs a) {
   __shared__ double A[kBlock][kBlock + 1];
   __shared__ double X[kBlock][kBlock + 1];
   const int32_t s = sns[blockIdx.x];
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, N = nc + a.nb[s];
   const int32_t c0 = J * kBlock, bw = min(kBlock, nc - c0);
   double *P = a.panel + a.panel_off[s];
-  const int lane = threadIdx.x;
-  for (int j = 0; j < bw; ++j)
-    A[lane][j] = (lane < bw && lane >= j) ? P[int64_t(c0 + j) * N + c0 + lane] : 0.0;
-  __syncwarp();
-  for (int k = 0; k < bw; ++k) {
-    const double dk = A[k][k];
-    if (lane == 0 && !(dk > 0.0 && dk < INFINITY)) flag_error(a.status, kErrNotSpd, f + c0 + k);
-    if (lane > k && lane < bw) A[lane][k] = A[lane][k] / dk;
-    __syncwarp();
-    if (lane > k && lane < bw) {
-      const double lk = A[lane][k] * dk;
-      for (int j = k + 1; j <= lane; ++j) A[lane][j] = fma(-lk, A[j][k], A[lane][j]);
-    }
-    __syncwarp();
+  // the block's panel columns and inverse lie inside the supernode's stored extents
+  if (!PEERS_IN(int64_t(c0 + bw) * N - 1, a.panel_off[s + 1] - a.panel_off[s], a.status) ||
+      !PEERS_IN(int64_t(J) * kBlock * kBlock + bw * bw - 1, a.tinv_off[s + 1] - a.tinv_off[s],
+                a.status))
+    return;
+  for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
+    const int i = e % kBlock, j = e / kBlock;   // consecutive threads read down a column
+    A[i][j] = (i < bw && j < bw && i >= j) ? P[int64_t(c0 + j) * N + c0 + i] : 0.0;
   }
-  // write L_JJ (strict lower), d (diagonal slot keeps d), 1/d
-  if (lane < bw) {
-    for (int j = 0; j < lane; ++j) P[int64_t(c0 + j) * N + c0 + lane] = A[lane][j];
-    const double dk = A[lane][lane];
-    P[int64_t(c0 + lane) * N + c0 + lane] = dk;
-    a.d[f + c0 + lane] = dk;
-    a.dinv[f + c0 + lane] = 1.0 / dk;
+  __syncthreads();
+  ldlt_block(A, bw, a.status, f + c0);
+  // write L_JJ (strict lower), d (the diagonal slot keeps d), 1/d
+  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
+    const int i = e % bw, j = e / bw;
+    if (i >= j) P[int64_t(c0 + j) * N + c0 + i] = A[i][j];
   }
-  // inverse of the unit-lower L_JJ, column `lane`: X[i][lane] for i >= lane
-  if (lane < bw) {
-    X[lane][lane] = 1.0;
-    for (int i = lane + 1; i < bw; ++i) {
-      double t = 0.0;
-      for (int k = lane; k < i; ++k) t = fma(A[i][k], X[k][lane], t);
-      X[i][lane] = -t;
-    }
+  if (threadIdx.x < bw) {
+    const double dk = A[threadIdx.x][threadIdx.x];
+    a.d[f + c0 + threadIdx.x] = dk;
+    a.dinv[f + c0 + threadIdx.x] = 1.0 / dk;
   }
-  __syncwarp();
+  unit_lower_inverse(A, X, bw);
   double *T = a.tinv + a.tinv_off[s] + int64_t(J) * kBlock * kBlock;
-  for (int i = 0; i < bw; ++i)
-    if (lane < bw) T[i * bw + lane] = lane <= i ? X[i][lane] : 0.0;
+  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
+    const int i = e / bw, j = e % bw;
+    T[i * bw + j] = j <= i ? X[i][j] : 0.0;
+  }
 }
 
-// Rows below the diagonal block: L[i, c0+k] = w_k / d_k with w L_JJ^T = F[i, J] (forward
-// substitution along the row).  grid = (active supernode, chunk of 128 rows).
-__global__ void __launch_bounds__(128) k_panel_rows(const int32_t *__restrict__ sns, int32_t J,
-                                                    FactorArgs a) {
-  __shared__ double Ls[kBlock][kBlock + 1];
+// Rows below the diagonal block: L[i, c0+k] = w_k / d_k, w = F[i, J] L_JJ^{-T}, from the
+// block's inverse formed by k_diag_block.  grid = (active supernode, chunk of 32 rows); the
+// 32 rows of a chunk are staged in shared memory and each row's columns are shared by
+// kPanelSplit warps.
+__global__ void __launch_bounds__(kBlock * kPanelSplit) k_panel_rows(const int32_t *__restrict__ sns,
+                                                                     int32_t J, FactorArgs a) {
+  __shared__ double X[kBlock][kBlock + 1];
+  __shared__ double Fr[kBlock][kBlock + 1];   // Fr[j][r]: column j of the chunk's row r
   __shared__ double dk[kBlock];
   const int32_t s = sns[blockIdx.x];
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, N = nc + a.nb[s];
   const int32_t c0 = J * kBlock, bw = min(kBlock, nc - c0);
-  const int32_t r0 = c0 + bw + blockIdx.y * blockDim.x;
+  const int32_t r0 = c0 + bw + blockIdx.y * kBlock;
   if (r0 >= N) return;
   double *P = a.panel + a.panel_off[s];
-  for (int idx = threadIdx.x; idx < kBlock * kBlock; idx += blockDim.x) {
-    const int i = idx / kBlock, j = idx % kBlock;
-    Ls[i][j] = (i < bw && j < i) ? P[int64_t(c0 + j) * N + c0 + i] : 0.0;
+  if (!PEERS_IN(int64_t(c0 + bw) * N - 1, a.panel_off[s + 1] - a.panel_off[s], a.status)) return;
+  const double *T = a.tinv + a.tinv_off[s] + int64_t(J) * kBlock * kBlock;
+  for (int e = threadIdx.x; e < kBlock * kBlock; e += blockDim.x) {
+    const int i = e / kBlock, j = e % kBlock;
+    X[i][j] = (i < bw && j < bw) ? T[i * bw + j] : 0.0;
+    const int r = e % kBlock, c = e / kBlock;   // coalesced down each panel column
+    Fr[c][r] = (c < bw && r0 + r < N) ? P[int64_t(c0 + c) * N + r0 + r] : 0.0;
   }
   if (threadIdx.x < kBlock) dk[threadIdx.x] = threadIdx.x < bw ? a.d[f + c0 + threadIdx.x] : 1.0;
   __syncthreads();
-  const int32_t i = r0 + threadIdx.x;
-  if (i >= N) return;
-  double w[kBlock];
-#pragma unroll
-  for (int k = 0; k < kBlock; ++k) w[k] = k < bw ? P[int64_t(c0 + k) * N + i] : 0.0;
-#pragma unroll
-  for (int k = 0; k < kBlock; ++k) {
-    double t = w[k];
-#pragma unroll
-    for (int j = 0; j < k; ++j) t = fma(-w[j], Ls[k][j], t);
-    w[k] = t;
-  }
-#pragma unroll
-  for (int k = 0; k < kBlock; ++k)
-    if (k < bw) P[int64_t(c0 + k) * N + i] = w[k] / dk[k];
+  const int r = threadIdx.x % kBlock, q = threadIdx.x / kBlock;
+  if (r0 + r < N)
+    panel_row_from_inverse(&Fr[0][r], kBlock + 1, X, dk, bw, q, P + int64_t(c0) * N + r0 + r, N);
 }
 
 // Trailing update of block J: F[i, j] -= sum_k L[i, c0+k] d_k L[j, c0+k] for t0 <= j <= i < N,
@@ -169,6 +220,10 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
   const int32_t c0 = J * kBlock, bw = min(kBlock, nc - c0), t0 = c0 + bw;
   const int32_t R0 = t0 + int32_t(ti) * TS, C0 = t0 + int32_t(tj) * TS;
   const double *P = a.panel + a.panel_off[s];
+#if defined(PEERS_BOUNDS) && PEERS_BOUNDS
+  const int64_t pext = a.panel_off[s + 1] - a.panel_off[s], uext = a.u_off[s + 1] - a.u_off[s];
+  if (!PEERS_IN(int64_t(c0 + bw) * N - 1, pext, a.status)) return;
+#endif
   for (int idx = threadIdx.x; idx < kBlock * TS; idx += blockDim.x) {
     const int k = idx / TS, r = idx % TS;
     const bool kin = k < bw;
@@ -197,10 +252,11 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
     for (int u = 0; u < U; ++u) {
       const int32_t i = R0 + tx + 16 * u;
       if (i >= N || i < j) continue;
-      if (j < nc)
-        Pw[int64_t(j) * N + i] -= acc[u][v];
-      else
+      if (j < nc) {
+        if (PEERS_IN(int64_t(j) * N + i, pext, a.status)) Pw[int64_t(j) * N + i] -= acc[u][v];
+      } else if (PEERS_IN(int64_t(j - nc) * nbv + (i - nc), uext, a.status)) {
         Uw[int64_t(j - nc) * nbv + (i - nc)] -= acc[u][v];
+      }
     }
   }
 }
@@ -218,6 +274,7 @@ __global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict_
                                                       const int32_t *__restrict__ child_list,
                                                       FactorArgs a) {
   extern __shared__ double sm_fac[];
+  __shared__ double A[kBlock][kBlock + 1];
   __shared__ double X[kBlock][kBlock + 1];
   __shared__ double dk[kBlock];
   const int32_t s = sns[blockIdx.x];
@@ -225,11 +282,14 @@ __global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict_
   const int bw = nc;   // one column block
   double *F = sm_fac;
   double *P = a.panel + a.panel_off[s];
-  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
-  for (int idx = tid; idx < N * N; idx += blockDim.x) {
-    const int j = idx / N, i = idx - j * N;
-    F[idx] = j < nc ? P[idx] : 0.0;
-  }
+  const int tid = threadIdx.x;
+  // the front fits the launch's shared memory; panel, inverse and update matrix their extents
+  if (!PEERS_IN(int64_t(N) * N - 1, dynamic_smem_doubles(), a.status) ||
+      !PEERS_IN(int64_t(N) * nc - 1, a.panel_off[s + 1] - a.panel_off[s], a.status) ||
+      !PEERS_IN(int64_t(nc) * nc - 1, a.tinv_off[s + 1] - a.tinv_off[s], a.status) ||
+      !(nbv == 0 || PEERS_IN(int64_t(nbv) * nbv - 1, a.u_off[s + 1] - a.u_off[s], a.status)))
+    return;
+  for (int idx = tid; idx < N * N; idx += blockDim.x) F[idx] = idx / N < nc ? P[idx] : 0.0;
   __syncthreads();
   for (int32_t c = child_ptr[s]; c < child_ptr[s + 1]; ++c) {
     const int32_t ch = child_list[c];
@@ -238,57 +298,47 @@ __global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict_
     const double *Uc = a.U + a.u_off[ch];
     for (int idx = tid; idx < nbc * nbc; idx += blockDim.x) {
       const int j = idx / nbc, i = idx - j * nbc;
-      if (i >= j) F[rm[j] * N + rm[i]] += Uc[idx];
+      if (i >= j && PEERS_IN(idx, a.u_off[ch + 1] - a.u_off[ch], a.status) &&
+          PEERS_IN(int64_t(rm[j]) * N + rm[i], int64_t(N) * N, a.status))
+        F[rm[j] * N + rm[i]] += Uc[idx];
     }
     __syncthreads();
   }
-  // diagonal block: L_JJ D_J L_JJ^T (k_diag_block)
-  if (warp == 0) {
-    for (int k = 0; k < bw; ++k) {
-      const double d = F[k * N + k];
-      if (lane == 0 && !(d > 0.0 && d < INFINITY)) flag_error(a.status, kErrNotSpd, f + k);
-      if (lane > k && lane < bw) F[k * N + lane] = F[k * N + lane] / d;
-      __syncwarp();
-      if (lane > k && lane < bw) {
-        const double lk = F[k * N + lane] * d;
-        for (int j = k + 1; j <= lane; ++j) F[j * N + lane] = fma(-lk, F[k * N + j], F[j * N + lane]);
-      }
-      __syncwarp();
-    }
-    if (lane < bw) {
-      const double d = F[lane * N + lane];
-      dk[lane] = d;
-      P[int64_t(lane) * N + lane] = d;
-      for (int j = 0; j < lane; ++j) P[int64_t(j) * N + lane] = F[j * N + lane];
-      a.d[f + lane] = d;
-      a.dinv[f + lane] = 1.0 / d;
-      // inverse of the unit-lower L_JJ, column `lane`
-      X[lane][lane] = 1.0;
-      for (int i = lane + 1; i < bw; ++i) {
-        double t = 0.0;
-        for (int k = lane; k < i; ++k) t = fma(F[k * N + i], X[k][lane], t);
-        X[i][lane] = -t;
-      }
-    }
-    __syncwarp();
-    double *T = a.tinv + a.tinv_off[s];
-    for (int i = 0; i < bw; ++i)
-      if (lane < bw) T[i * bw + lane] = lane <= i ? X[i][lane] : 0.0;
+  // diagonal block: L_JJ D_J L_JJ^T and its inverse (k_diag_block's operations)
+  for (int e = tid; e < kBlock * kBlock; e += blockDim.x) {
+    const int i = e % kBlock, j = e / kBlock;
+    A[i][j] = (i < bw && j < bw && i >= j) ? F[j * N + i] : 0.0;
   }
   __syncthreads();
-  // rows below the block: L[i, k] = w_k / d_k, w L_JJ^T = F[i, J] (k_panel_rows)
-  // (w is formed in place in row i of F: w_k overwrites F[i, k] once its sum is complete)
-  for (int i = bw + tid; i < N; i += blockDim.x) {
-    for (int k = 0; k < bw; ++k) {
-      double t = F[k * N + i];
-      for (int j = 0; j < k; ++j) t = fma(-F[j * N + i], F[j * N + k], t);
-      F[k * N + i] = t;
+  ldlt_block(A, bw, a.status, f);
+  for (int e = tid; e < bw * bw; e += blockDim.x) {
+    const int i = e % bw, j = e / bw;
+    if (i >= j) P[int64_t(j) * N + i] = A[i][j];
+  }
+  if (tid < bw) {
+    const double d = A[tid][tid];
+    dk[tid] = d;
+    a.d[f + tid] = d;
+    a.dinv[f + tid] = 1.0 / d;
+  }
+  unit_lower_inverse(A, X, bw);
+  {
+    double *T = a.tinv + a.tinv_off[s];
+    for (int e = tid; e < bw * bw; e += blockDim.x) {
+      const int i = e / bw, j = e % bw;
+      T[i * bw + j] = j <= i ? X[i][j] : 0.0;
     }
-    for (int k = 0; k < bw; ++k) {
-      const double l = F[k * N + i] / dk[k];
-      F[k * N + i] = l;
-      P[int64_t(k) * N + i] = l;
-    }
+  }
+  // rows below the block (k_panel_rows' operations), written to the panel and read back
+  const int rows = N - bw;
+  for (int e = tid; e < rows * kPanelSplit; e += blockDim.x) {
+    const int i = bw + e % rows, q = e / rows;
+    panel_row_from_inverse(F + i, N, X, dk, bw, q, P + i, N);
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * bw; e += blockDim.x) {
+    const int i = bw + e % rows, k = e / rows;
+    F[k * N + i] = P[int64_t(k) * N + i];
   }
   __syncthreads();
   // trailing update of the update matrix: F[i, j] -= sum_k L[i, k] (L[j, k] d_k) (k_trailing)
@@ -315,7 +365,8 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, co
     const int64_t cnt = static_cast<int64_t>(S.a_dest.size());
     const int blocks = static_cast<int>(std::min<int64_t>((cnt + 255) / 256, 148 * 16));
     if (cnt > 0) {
-      k_assemble<<<blocks, 256, 0, stream>>>(D.a_dest, D.a_val, cnt, a.panel);
+      k_assemble<<<blocks, 256, 0, stream>>>(D.a_dest, D.a_val, cnt, a.panel, S.panel_total,
+                                             a.status);
       ++*launches;
     }
     CUDA_TRY(cudaGetLastError());
@@ -382,7 +433,7 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, co
       const int64_t tp = G.trail_base + J;
       const int32_t na = static_cast<int32_t>(S.trail_na[tp]);
       if (na == 0) continue;
-      k_diag_block<<<na, 32, 0, st>>>(sns, J, a);
+      k_diag_block<<<na, 256, 0, st>>>(sns, J, a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
       int32_t maxrows = 0;
@@ -392,8 +443,8 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, co
         maxrows = std::max(maxrows, N - std::min(nc, (J + 1) * kBlock));
       }
       if (maxrows > 0) {
-        dim3 grid(static_cast<unsigned>(na), static_cast<unsigned>((maxrows + 127) / 128));
-        k_panel_rows<<<grid, 128, 0, st>>>(sns, J, a);
+        dim3 grid(static_cast<unsigned>(na), static_cast<unsigned>((maxrows + kBlock - 1) / kBlock));
+        k_panel_rows<<<grid, kBlock * kPanelSplit, 0, st>>>(sns, J, a);
         ++*launches;
         CUDA_TRY(cudaGetLastError());
       }
@@ -420,6 +471,10 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, co
   if (status[0] == kErrNotSpd) {
     err = "non-positive pivot at elimination position " + std::to_string(status[1]);
     return PEERS_ENOTSPD;
+  }
+  if (status[0] == kErrBounds) {
+    err = "peers_factor: out-of-bounds access skipped at source line " + std::to_string(status[1]);
+    return PEERS_ECUDA;
   }
   return PEERS_OK;
 }

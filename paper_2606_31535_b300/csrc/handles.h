@@ -69,6 +69,7 @@ struct peers_numeric {
   double *carry = nullptr, *racc = nullptr, *Rdev = nullptr;
   double *spill = nullptr;        // kSpillGrid x spill_stride front scratch (if the plan spills)
   int *spill_counter = nullptr;   // one work counter per level
+  int *status = nullptr;          // error flag of the sweep kernels (2 ints; bounds checks)
 };
 
 
@@ -95,6 +96,10 @@ inline peers::SweepArgs sweep_args_of(const peers_numeric *num, const Symbolic &
   a.spill = num->spill;
   a.spill_stride = S.spill_stride;
   a.spill_counter = num->spill_counter;
+  a.status = num->status;
+  a.carry_slots = S.carry_slots;
+  a.nq = S.nq;
+  a.nldesc = static_cast<int64_t>(S.ldesc.size());
   return a;
 }
 
@@ -110,6 +115,11 @@ int peers_fail(int status, const std::string &msg);
 // stream (stream-ordered; see peers_numeric::pool).  Returns a PEERS_* status (capi.cu).
 int factor_from_pool(peers_ctx *ctx, const peers_symbolic *sym, const double *w,
                      cudaMemPool_t pool, peers_numeric **out, std::string &err);
+
+// Bounds-checked build only: reads and clears a kernel error flag (2 ints) after the work on
+// `stream`, and turns a recorded out-of-bounds access into PEERS_ECUDA with its source line.
+// The regular build returns PEERS_OK without touching the device (capi.cu).
+int check_bounds_flag(int *d_status, cudaStream_t stream, const char *what, std::string &err);
 
 // Allocates the sweep's carry buffer of a factored plan if it has none (capi.cu).
 int ensure_carry(peers_numeric *num, const Symbolic &S, std::string &err);

@@ -39,9 +39,11 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
                                            double *smem) {
   if (it.kind == 2) {   // combine two-branch sums (multi-graph launches)
     for (int64_t k = it.q0 + threadIdx.x; k < int64_t(it.q0) + it.nq; k += kSweepThreads) {
-      double r = a.racc[int64_t(a.two_a[k]) - a.wave_base];
-      if (a.two_b[k] >= 0) r += a.racc[int64_t(a.two_b[k]) - a.wave_base];
-      a.R[a.two_user[k]] = r;
+      const int64_t sa = int64_t(a.two_a[k]) - a.wave_base, sb = int64_t(a.two_b[k]) - a.wave_base;
+      if (!PEERS_IN(sa, a.carry_slots, a.status)) continue;
+      double r = a.racc[sa];
+      if (a.two_b[k] >= 0 && PEERS_IN(sb, a.carry_slots, a.status)) r += a.racc[sb];
+      if (PEERS_IN(a.two_user[k], a.nq, a.status)) a.R[a.two_user[k]] = r;
     }
     return;
   }
@@ -55,8 +57,22 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
   double *T = Y + kBlock * QP;         // kBlock x QP   y^2 / d of the current block
   const int tid = threadIdx.x;
   const int32_t j0 = it.j0;
+  const int64_t NX = int64_t(N) * QP;   // doubles of the tile's fronts
+#if defined(PEERS_BOUNDS) && PEERS_BOUNDS
+  // the tile must fit its launch: fronts and y blocks in shared memory, or the fronts in this
+  // CTA's slice of the global scratch
+  if (!(SPILL ? PEERS_IN(NX - 1, a.spill_stride, a.status) &&
+                    PEERS_IN(int64_t(blockIdx.x), kSpillGrid, a.status) &&
+                    PEERS_IN(2 * kBlock * QP - 1, dynamic_smem_doubles(), a.status)
+              : PEERS_IN(NX + 2 * kBlock * QP - 1, dynamic_smem_doubles(), a.status)) ||
+      !PEERS_IN(int64_t(it.q0) - (it.kind == 1 ? 0 : a.wave_base) + Q - 1,
+                it.kind == 1 ? a.nldesc : a.carry_slots, a.status))
+    return;
+  const int64_t cbase = a.panel_off[s], cext = a.panel_off[s + 1] - a.panel_off[s];
+  const int64_t tbase = a.tinv_off[s], text = a.tinv_off[s + 1] - a.tinv_off[s];
+#endif
 
-  for (int64_t idx = int64_t(j0) * QP + tid; idx < int64_t(N) * QP; idx += kSweepThreads)
+  for (int64_t idx = int64_t(j0) * QP + tid; idx < NX; idx += kSweepThreads)
     X[idx] = 0.0;
   __syncthreads();
   if (it.kind == 1) {
@@ -65,13 +81,18 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
     for (int q = warp; q < Q; q += kSweepThreads / 32) {
       const SweepDesc d = a.ldesc[it.q0 + q];
       const int64_t sa = int64_t(d.a) - a.wave_base;
+      if (!PEERS_IN(sa, a.carry_slots, a.status)) continue;
       if (d.src_a >= 0) {
         const int32_t nbc = a.nb[d.src_a];
         const int32_t *rm = a.rmap + a.rows_off[d.src_a];
-        for (int32_t t = lane; t < nbc; t += 32) X[rm[t] * QP + q] = a.carry[sa * a.nbmax + t];
+        for (int32_t t = lane; t < nbc; t += 32)
+          if (PEERS_IN(t, a.nbmax, a.status) && PEERS_IN(int64_t(rm[t]) * QP + q, NX, a.status))
+            X[rm[t] * QP + q] = a.carry[sa * a.nbmax + t];
       } else if (lane == 0) {
-        if (a.qa[d.a] >= 0) X[a.qa[d.a] * QP + q] = 1.0;
-        if (a.qb[d.a] >= 0) X[a.qb[d.a] * QP + q] = -1.0;
+        if (a.qa[d.a] >= 0 && PEERS_IN(int64_t(a.qa[d.a]) * QP + q, NX, a.status))
+          X[a.qa[d.a] * QP + q] = 1.0;
+        if (a.qb[d.a] >= 0 && PEERS_IN(int64_t(a.qb[d.a]) * QP + q, NX, a.status))
+          X[a.qb[d.a] * QP + q] = -1.0;
       }
     }
     __syncthreads();
@@ -82,9 +103,12 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
         const int64_t sb = int64_t(d.b) - a.wave_base;
         const int32_t nbc = a.nb[d.src_b];
         const int32_t *rm = a.rmap + a.rows_off[d.src_b];
-        for (int32_t t = lane; t < nbc; t += 32) X[rm[t] * QP + q] += a.carry[sb * a.nbmax + t];
+        if (!PEERS_IN(sb, a.carry_slots, a.status)) continue;
+        for (int32_t t = lane; t < nbc; t += 32)
+          if (PEERS_IN(t, a.nbmax, a.status) && PEERS_IN(int64_t(rm[t]) * QP + q, NX, a.status))
+            X[rm[t] * QP + q] += a.carry[sb * a.nbmax + t];
       } else if (d.seed_b >= 0 && lane == 0) {
-        X[d.seed_b * QP + q] -= 1.0;
+        if (PEERS_IN(int64_t(d.seed_b) * QP + q, NX, a.status)) X[d.seed_b * QP + q] -= 1.0;
       }
     }
   } else if (it.src >= 0) {
@@ -94,14 +118,15 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
     const double *cin = a.carry + (int64_t(it.q0) - a.wave_base) * a.nbmax;
     for (int32_t idx = tid; idx < Q * nbc; idx += kSweepThreads) {
       const int32_t q = idx / nbc, t = idx - q * nbc;
-      X[rm[t] * QP + q] = cin[int64_t(q) * a.nbmax + t];
+      if (PEERS_IN(t, a.nbmax, a.status) && PEERS_IN(int64_t(rm[t]) * QP + q, NX, a.status))
+        X[rm[t] * QP + q] = cin[int64_t(q) * a.nbmax + t];
     }
   } else {
     // queries starting here: e_lo - e_hi in local rows (eq. 4: no -1 when hi is the ground)
     for (int32_t q = tid; q < Q; q += kSweepThreads) {
       const int32_t qa = a.qa[it.q0 + q], qb = a.qb[it.q0 + q];
-      if (qa >= 0) X[qa * QP + q] = 1.0;
-      if (qb >= 0) X[qb * QP + q] = -1.0;
+      if (qa >= 0 && PEERS_IN(int64_t(qa) * QP + q, NX, a.status)) X[qa * QP + q] = 1.0;
+      if (qb >= 0 && PEERS_IN(int64_t(qb) * QP + q, NX, a.status)) X[qb * QP + q] = -1.0;
     }
   }
 
@@ -113,6 +138,12 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
     __syncthreads();
     // y_J = inv(T_JJ) x_J and its y^2 / d terms
     const double *TI = tinv + int64_t(J / kBlock) * kBlock * kBlock;
+#if defined(PEERS_BOUNDS) && PEERS_BOUNDS
+    // this block's inverse and panel columns lie inside the supernode's stored extents
+    if (!PEERS_IN(int64_t(J / kBlock) * kBlock * kBlock + bw * bw - 1, text, a.status) ||
+        !PEERS_IN(int64_t(J + bw) * N - 1, cext, a.status))
+      break;
+#endif
     for (int u = tid; u < bw * Q; u += kSweepThreads) {
       const int k = u / Q, q = u - k * Q;
       double acc = X[(J + k) * QP + q];
@@ -172,14 +203,18 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
     const int warp = tid / 32, lane = tid % 32;
     for (int q = warp; q < Q; q += kSweepThreads / 32) {
       const int64_t sa = int64_t(a.ldesc[it.q0 + q].a) - a.wave_base;
-      for (int32_t t = lane; t < nbv; t += 32) a.carry[sa * a.nbmax + t] = X[(nc + t) * QP + q];
+      if (!PEERS_IN(sa, a.carry_slots, a.status)) continue;
+      for (int32_t t = lane; t < nbv; t += 32)
+        if (PEERS_IN(t, a.nbmax, a.status)) a.carry[sa * a.nbmax + t] = X[(nc + t) * QP + q];
     }
     if (tid < Q) {
       const SweepDesc d = a.ldesc[it.q0 + tid];
       double tot = r;
       if (d.src_a >= 0) tot += a.racc[int64_t(d.a) - a.wave_base];
-      if (d.b >= 0) tot += a.racc[int64_t(d.b) - a.wave_base];
-      a.racc[int64_t(d.a) - a.wave_base] = tot;
+      if (d.b >= 0 && PEERS_IN(int64_t(d.b) - a.wave_base, a.carry_slots, a.status))
+        tot += a.racc[int64_t(d.b) - a.wave_base];
+      if (PEERS_IN(int64_t(d.a) - a.wave_base, a.carry_slots, a.status))
+        a.racc[int64_t(d.a) - a.wave_base] = tot;
     }
     return;
   }
@@ -187,7 +222,7 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
     double *cout = a.carry + (int64_t(it.q0) - a.wave_base) * a.nbmax;
     for (int32_t idx = tid; idx < Q * nbv; idx += kSweepThreads) {
       const int32_t q = idx / nbv, t = idx - q * nbv;
-      cout[int64_t(q) * a.nbmax + t] = X[(nc + t) * QP + q];
+      if (PEERS_IN(t, a.nbmax, a.status)) cout[int64_t(q) * a.nbmax + t] = X[(nc + t) * QP + q];
     }
   }
   if (tid < Q) {
@@ -196,7 +231,7 @@ __device__ __forceinline__ void sweep_item(const SweepItem &it, const SweepArgs 
     const double tot = prev + r;
     if (nbv > 0)
       a.racc[slot - a.wave_base] = tot;
-    else
+    else if (PEERS_IN(a.qorig[slot], a.nq, a.status))
       a.R[a.qorig[slot]] = tot;
   }
 }

@@ -69,11 +69,12 @@ class Info(ctypes.Structure):
 
 
 def load(path: str | None = None):
-    """Loads libpeers.so; raises if it has not been built."""
+    """Loads libpeers.so (or the library named by $PEERS_LIB, e.g. the bounds-checked
+    libpeers_bounds.so); raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or os.environ.get("PEERS_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with `python -m paper_2606_31535_b300.build`")
     lib = ctypes.CDLL(path)

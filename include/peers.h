@@ -184,9 +184,12 @@ int64_t peers_blockinv_fma(const peers_symbolic *sym);
  * 2 Sigma_uv (eq. 2).  The work is about one factorization, far below both the walk and the
  * block inverse; the memory is two depths of dense inverse fronts.  The paper does not use it
  * (§II-C); it is an independent second route to the same numbers.  A plan with listed pairs
- * outside the pattern is rejected with PEERS_EINVAL (use peers_query).  Device memory is
- * allocated and freed inside the call; the host-side plan is kept with `sym` after the first
- * call, as for peers_query_blockinv (rebuilt for a device with another SM count).  Errors:
+ * outside the pattern is rejected with PEERS_EINVAL (use peers_query).  The host-side plan is
+ * kept with `sym` after the first call, as for peers_query_blockinv (rebuilt for a device with
+ * another SM count).  The first call on a factor also copies that plan to the device and
+ * allocates its working buffers (T^{-1}, M and two depths of inverse fronts per stream of
+ * independent subtrees: about 2.7 GB for a 1M-node mesh), which stay with `num` for later calls
+ * until it is freed or the plan is rebuilt; calls on one `num` are serialised.  Errors:
  * PEERS_EINVAL, PEERS_ENOMEM, PEERS_ECUDA. */
 int peers_query_selinv(peers_ctx *ctx, const peers_symbolic *sym, const peers_numeric *num,
                        double *R, int flags);

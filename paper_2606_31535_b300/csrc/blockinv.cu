@@ -294,10 +294,10 @@ __device__ __forceinline__ void rows_gemm_dispatch(const RowsGemm &g, const Tile
 // product.  Z[C_t, C_t] = T_t^{-1} is lower triangular, so a column chunk starting at c0 only
 // needs k >= c0 (the entries above the diagonal are stored zeros).
 constexpr int kMRows = 64;
-// Column chunk of M's tiles: 32 rather than the widest 64, so that a tile (64 x 32 over up to
+// Column chunk of M's tiles: 16 rather than the widest 64, so that a tile (64 x 16 over up to
 // n_c terms) holds its SM for a short time; the tiles of a low-priority stream then do not
 // keep the critical path's launches waiting for long.
-constexpr int kMWidth = 32;
+constexpr int kMWidth = 16;
 template <int G>
 __global__ void __launch_bounds__(kRowsMaxThreads) k_bi_m(const Tile *__restrict__ tiles, BiArgs a) {
   __shared__ double Ms[kRowsK * rows_group_width(G)];
@@ -386,7 +386,8 @@ struct TinvTile {
   int32_t r;          // row chunk of the product (rows of C, kTinvRows each)
   int32_t col0, w;    // first column (of A) of the tile and its width (rows_width)
 };
-constexpr int kTinvRows = 64;
+constexpr int kTinvRows = 32;
+constexpr int kTinvWidth = 16;   // columns per doubling tile (short CTAs, many per SM)
 // Supernodes at least this wide form T^{-1} by doubling; narrower ones by k_bi_diag's block
 // substitution, whose single launch beats the doubling's launch chain there.
 constexpr int32_t kTinvDoubling = 1024;
@@ -477,8 +478,8 @@ inline void tinv_plan_of(const Symbolic &S, const std::vector<int32_t> &wide, Ti
         any = true;
         const int32_t c0 = a0 + s, ha = s, hc = std::min(s, nc - c0);
         for (int32_t r = 0; r * kTinvRows < hc; ++r)
-          for (int32_t col0 = 0; col0 < ha; col0 += 32) {
-            const int w = rows_width(std::min(32, ha - col0));
+          for (int32_t col0 = 0; col0 < ha; col0 += kTinvWidth) {
+            const int w = rows_width(std::min(kTinvWidth, ha - col0));
             grp[rows_group(w)].push_back({t, a0, c0, ha, hc, r, col0, w});
           }
       }
@@ -1409,10 +1410,11 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
   }
   // groups: the top part depth by depth, then the lanes, depth by depth
   for (int32_t L = 0; L <= nl; ++L) {
-    // every launch is sized as if alone: the lanes overlap, but a launch of few one-warp CTAs
-    // leaves the FP64 units of its SMs half idle (two to three warps per SM sub-partition
-    // keep them busy)
-    const int64_t target_ctas = int64_t(std::max(sms, 1)) * 16;
+    // every launch is sized as if alone, for at least 32 CTAs per SM: the lanes overlap, but a
+    // launch of few one-warp CTAs leaves the FP64 units of its SMs half idle (two to three
+    // warps per SM sub-partition keep them busy), and many short CTAs end a launch with a
+    // short partial wave
+    const int64_t target_ctas = int64_t(std::max(sms, 1)) * 32;
     for (int32_t d = 0; d <= maxd; ++d) {
       const std::vector<int32_t> &mem = members[L][d];
       if (mem.empty()) continue;
@@ -1689,13 +1691,18 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   return rc;
 }
 
-// Device buffers of one call, freed together.
+// Device buffers of one call, freed together (unless released to a longer-lived owner).
 struct DevMem {
   std::vector<void *> ptrs;
   std::string *err;
   explicit DevMem(std::string *e) : err(e) {}
   ~DevMem() {
     for (void *p : ptrs) cudaFree(p);
+  }
+  std::vector<void *> release() {
+    std::vector<void *> out;
+    out.swap(ptrs);
+    return out;
   }
   template <class T>
   int alloc(T **p, int64_t count) {
@@ -1730,6 +1737,65 @@ struct DevMem {
     if (rc_ != PEERS_OK) return rc_; \
   } while (0)
 
+// The selected inversion's plan on the device and its working buffers for one factor: made
+// by the first call and kept with the numeric handle while the plan stays the same, so that
+// repeated calls neither allocate nor upload.
+struct SiDevice {
+  std::shared_ptr<const peers::SelInvPlan> plan;
+  int device = 0;
+  std::vector<void *> ptrs;
+  double *Zd = nullptr, *Wd = nullptr, *M = nullptr, *F = nullptr, *Rdev = nullptr;
+  int32_t *ncs = nullptr, *gsn = nullptr, *ssn = nullptr, *sch = nullptr, *dsn = nullptr,
+          *dblk = nullptr, *tbs = nullptr, *tbb = nullptr, *fsn = nullptr, *par = nullptr;
+  int64_t *doff = nullptr, *moff = nullptr, *foff = nullptr, *qbeg = nullptr;
+  peers::Tile *bc = nullptr, *cc = nullptr, *mt = nullptr;
+  peers::TinvTile *tt = nullptr;
+  peers::SiQuery *qs = nullptr;
+  ~SiDevice() {
+    peers::DeviceGuard guard(device);
+    for (void *p : ptrs) cudaFree(p);
+  }
+};
+
+int si_device(peers_ctx *ctx, const Symbolic &S, const std::shared_ptr<const peers::SelInvPlan> &plan,
+              std::shared_ptr<SiDevice> &out, std::string &err) {
+  const peers::SelInvPlan &P = *plan;
+  const cudaStream_t st = ctx->stream;
+  auto d = std::make_shared<SiDevice>();
+  d->plan = plan;
+  d->device = ctx->device;
+  DevMem mem(&err);
+  RC_TRY(mem.alloc(&d->Zd, P.dtotal));
+  RC_TRY(mem.alloc(&d->Wd, P.dtotal));
+  RC_TRY(mem.alloc(&d->M, P.mtotal));
+  RC_TRY(mem.alloc(&d->F, P.fbuf));
+  RC_TRY(mem.alloc(&d->Rdev, S.nq));
+  RC_TRY(mem.upload(&d->ncs, P.ncs, st));
+  RC_TRY(mem.upload(&d->doff, P.doff, st));
+  RC_TRY(mem.upload(&d->moff, P.moff, st));
+  RC_TRY(mem.upload(&d->foff, P.foff, st));
+  RC_TRY(mem.upload(&d->gsn, P.gather_sn, st));
+  RC_TRY(mem.upload(&d->bc, P.bc, st));
+  RC_TRY(mem.upload(&d->cc, P.cc, st));
+  RC_TRY(mem.upload(&d->qs, P.queries, st));
+  RC_TRY(mem.upload(&d->ssn, P.small_sn, st));
+  RC_TRY(mem.upload(&d->sch, P.small_chunk, st));
+  RC_TRY(mem.upload(&d->dsn, P.diag_sn, st));
+  RC_TRY(mem.upload(&d->dblk, P.diag_blk, st));
+  RC_TRY(mem.upload(&d->tbs, P.tbase_sn, st));
+  RC_TRY(mem.upload(&d->tbb, P.tbase_blk, st));
+  RC_TRY(mem.upload(&d->tt, P.tinv_tiles, st));
+  RC_TRY(mem.upload(&d->mt, P.m_tiles, st));
+  RC_TRY(mem.upload(&d->fsn, P.fused_sn, st));
+  RC_TRY(mem.upload(&d->qbeg, S.qbeg, st));
+  std::vector<int32_t> parent_host(S.parent);
+  RC_TRY(mem.upload(&d->par, parent_host, st));
+  CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors above must outlive their copies
+  d->ptrs = mem.release();
+  out = d;
+  return PEERS_OK;
+}
+
 int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, double *R, int flags,
              std::string &err) {
   const Symbolic &S = sym->S;
@@ -1741,42 +1807,22 @@ int si_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
   RC_TRY(peers::cached_selinv_plan(sym, sms, plan, err));
   const peers::SelInvPlan &P = *plan;
   const peers::Lanes *lanes = P.nlanes > 0 ? ctx_lanes(ctx) : nullptr;
-  DevMem mem(&err);
-  double *Zd, *Wd, *M, *F, *Rdev = R;
-  int32_t *ncs, *gsn, *ssn, *sch, *dsn, *dblk, *tbs, *tbb;
-  int64_t *doff, *moff, *foff;
-  peers::Tile *bc, *cc, *mt;
-  peers::TinvTile *tt;
-  peers::SiQuery *qs;
-  RC_TRY(mem.alloc(&Zd, P.dtotal));
-  RC_TRY(mem.alloc(&Wd, P.dtotal));
-  RC_TRY(mem.alloc(&M, P.mtotal));
-  RC_TRY(mem.alloc(&F, P.fbuf));
-  RC_TRY(mem.upload(&ncs, P.ncs, st));
-  RC_TRY(mem.upload(&doff, P.doff, st));
-  RC_TRY(mem.upload(&moff, P.moff, st));
-  RC_TRY(mem.upload(&foff, P.foff, st));
-  RC_TRY(mem.upload(&gsn, P.gather_sn, st));
-  RC_TRY(mem.upload(&bc, P.bc, st));
-  RC_TRY(mem.upload(&cc, P.cc, st));
-  RC_TRY(mem.upload(&qs, P.queries, st));
-  RC_TRY(mem.upload(&ssn, P.small_sn, st));
-  RC_TRY(mem.upload(&sch, P.small_chunk, st));
-  RC_TRY(mem.upload(&dsn, P.diag_sn, st));
-  RC_TRY(mem.upload(&dblk, P.diag_blk, st));
-  RC_TRY(mem.upload(&tbs, P.tbase_sn, st));
-  RC_TRY(mem.upload(&tbb, P.tbase_blk, st));
-  RC_TRY(mem.upload(&tt, P.tinv_tiles, st));
-  RC_TRY(mem.upload(&mt, P.m_tiles, st));
-  int32_t *fsn;
-  int64_t *qbeg;
-  RC_TRY(mem.upload(&fsn, P.fused_sn, st));
-  RC_TRY(mem.upload(&qbeg, S.qbeg, st));
-  std::vector<int32_t> parent_host(S.parent);
-  int32_t *par;
-  RC_TRY(mem.upload(&par, parent_host, st));
+  std::lock_guard<std::mutex> route_lock(num->route_mu);
+  std::shared_ptr<SiDevice> dev = std::static_pointer_cast<SiDevice>(num->selinv_dev);
+  if (!dev || dev->plan != plan) {
+    num->selinv_dev.reset();
+    RC_TRY(si_device(ctx, S, plan, dev, err));
+    num->selinv_dev = dev;
+  }
+  double *Zd = dev->Zd, *Wd = dev->Wd, *M = dev->M, *F = dev->F, *Rdev = R;
+  int32_t *ncs = dev->ncs, *gsn = dev->gsn, *ssn = dev->ssn, *sch = dev->sch, *dsn = dev->dsn,
+          *dblk = dev->dblk, *tbs = dev->tbs, *tbb = dev->tbb, *fsn = dev->fsn, *par = dev->par;
+  int64_t *doff = dev->doff, *moff = dev->moff, *foff = dev->foff, *qbeg = dev->qbeg;
+  peers::Tile *bc = dev->bc, *cc = dev->cc, *mt = dev->mt;
+  peers::TinvTile *tt = dev->tt;
+  peers::SiQuery *qs = dev->qs;
   const bool host_out = !(flags & PEERS_OUT_DEVICE);
-  if (host_out) RC_TRY(mem.alloc(&Rdev, S.nq));
+  if (host_out) Rdev = dev->Rdev;
   {
     int64_t need = 0;
     for (const peers::SiGroup &G : P.groups) need = std::max(need, G.fused_smem);

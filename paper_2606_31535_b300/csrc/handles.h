@@ -70,6 +70,11 @@ struct peers_numeric {
   double *spill = nullptr;        // kSpillGrid x spill_stride front scratch (if the plan spills)
   int *spill_counter = nullptr;   // one work counter per level
   int *status = nullptr;          // error flag of the sweep kernels (2 ints; bounds checks)
+  // device copy of the selected inversion's plan and its working buffers, made by the first
+  // peers_query_selinv on this factor and reused while the plan is the same (blockinv.cu);
+  // route_mu serialises the calls that use it
+  std::mutex route_mu;
+  std::shared_ptr<void> selinv_dev;
 };
 
 

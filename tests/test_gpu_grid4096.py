@@ -1,7 +1,9 @@
 """The 4096 x 4096 grid (16.7M nodes, 33.5M edges, conductances log-uniform 1e-3..1e3): the
-full-size factorization on the device, then 2000 seeded edges swept and compared with the
-oracle's values stored by tests/golden/make_grid4096_sample.py (the oracle needs about 20
-minutes of one CPU core to factor this graph, so its values are computed once)."""
+full-size factorization on the device, then 3000 edges swept and compared with the oracle's
+values stored by tests/golden/make_grid4096_sample.py (the oracle needs about 20 minutes of
+one CPU core to factor this graph, so its values are computed once): 2000 drawn uniformly
+with a fixed seed and the 1000 of largest conductance, whose small resistances
+(R_e <= 1/w_e, down to about 1e-3 here) come from the most cancellation in y = z_lo - z_hi."""
 import json
 import os
 
@@ -31,6 +33,7 @@ def test_grid4096_sampled_parity(P):
     g = I.grid4096()
     u, v = g.all_edges()
     idx = np.array(d["edge_index"])
+    assert idx.size == 3000 and d["selection"]["largest_conductance"] == 1000
     # the stored sample still names the same edges of the same generator
     assert np.array_equal(u[idx], d["u"]) and np.array_equal(v[idx], d["v"])
     ctx = P.Context(0)
@@ -47,7 +50,8 @@ def test_grid4096_sampled_parity(P):
 
 def test_grid4096_all_edges_by_selected_inversion(P):
     """All 33 546 240 edges of the 16.7M-node grid from the selected inverse: the stored oracle
-    sample to 1e-9 and Foster's theorem over every edge."""
+    sample (uniform and largest-conductance edges) to 1e-9 and Foster's theorem over every
+    edge."""
     d = json.load(open(GOLDEN))
     g = I.grid4096()
     ctx = P.Context(0)

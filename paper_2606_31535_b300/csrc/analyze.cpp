@@ -950,6 +950,10 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   S.trail_na.clear();
   S.trail_ts.clear();
   S.trail_prefix.clear();
+  S.split_off.clear();
+  S.next_na.clear();
+  S.pr_ts.clear();
+  S.up_ts.clear();
   S.ea_off.clear();
   S.ea_pairs.clear();
   auto add_group = [&](int32_t lane, int32_t l) {
@@ -972,33 +976,68 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     const int32_t *ls = S.fac_sn.data() + G.fac_b;
     const int32_t cnt = G.fac_e - G.fac_b;
     G.nblocks = cnt > 0 ? (sn_nc(S, ls[0]) + kBlock - 1) / kBlock : 0;
+    // groups of several column blocks: each block's update is split so that the next block's
+    // chain (diagonal block, panel rows, next columns) does not wait for the bulk of it
+    G.split = G.nblocks >= 2;
     G.trail_base = static_cast<int64_t>(S.trail_na.size());
     for (int32_t J = 0; J < G.nblocks; ++J) {
       int32_t na = 0;
       while (na < cnt && sn_nc(S, ls[na]) > J * kBlock) ++na;
-      // tiles of 64, or of 32 when 64-tiles would not give every SM a few of them
-      auto tiles = [&](int64_t ts) {
-        int64_t acc = 0;
-        for (int32_t i = 0; i < na; ++i) {
-          const int64_t nc = sn_nc(S, ls[i]), N = nc + S.nb[ls[i]];
-          const int64_t T = (N - std::min<int64_t>(nc, (J + 1) * kBlock) + ts - 1) / ts;
-          acc += T * (T + 1) / 2;
-        }
-        return acc;
+      // tiles of one supernode's part of the update: the triangle of columns (and rows) from
+      // `lo`, or (rect) the columns [lo, nc) over the rows from lo
+      auto part_tiles = [&](int32_t i, int64_t lo, int64_t ts, bool rect) -> int64_t {
+        const int64_t nc = sn_nc(S, ls[i]), N = nc + S.nb[ls[i]];
+        const int64_t T = (N - lo + ts - 1) / ts;
+        if (!rect) return T * (T + 1) / 2;
+        const int64_t Tc = (nc - lo + ts - 1) / ts;
+        return Tc * T - Tc * (Tc - 1) / 2;
       };
-      const int64_t ts = tiles(kTile) < kTrailFewTiles ? kTile / 2 : kTile;
+      auto t0_of = [&](int32_t i) { return std::min<int64_t>(sn_nc(S, ls[i]), (J + 1) * kBlock); };
+      auto t1_of = [&](int32_t i) { return std::min<int64_t>(sn_nc(S, ls[i]), (J + 2) * kBlock); };
+      auto nc_of = [&](int32_t i) { return static_cast<int64_t>(sn_nc(S, ls[i])); };
+      // tiles of 64, or of 32 when 64-tiles would not give every SM a few of them
+      auto pick_ts = [&](auto lo_of, bool rect) -> int64_t {
+        int64_t acc = 0;
+        for (int32_t i = 0; i < na; ++i) acc += part_tiles(i, lo_of(i), kTile, rect);
+        return acc < kTrailFewTiles ? kTile / 2 : kTile;
+      };
+      auto push_prefix = [&](int32_t cnt_sn, auto lo_of, int64_t ts, bool rect) {
+        int64_t acc = 0;
+        S.trail_prefix.push_back(0);
+        for (int32_t i = 0; i < cnt_sn; ++i) {
+          acc += part_tiles(i, lo_of(i), ts, rect);
+          S.trail_prefix.push_back(acc);
+        }
+      };
+      const int64_t ts = pick_ts(t0_of, false);
       S.trail_off.push_back(static_cast<int64_t>(S.trail_prefix.size()));
       S.trail_na.push_back(na);
       S.trail_ts.push_back(static_cast<int32_t>(ts));
-      int64_t acc = 0;
-      S.trail_prefix.push_back(0);
-      for (int32_t i = 0; i < na; ++i) {
-        const int32_t s = ls[i];
-        const int64_t nc = sn_nc(S, s), N = nc + S.nb[s];
-        const int64_t t0 = std::min<int64_t>(nc, (J + 1) * kBlock);
-        const int64_t T = (N - t0 + ts - 1) / ts;
-        acc += T * (T + 1) / 2;
-        S.trail_prefix.push_back(acc);
+      push_prefix(na, t0_of, ts, false);
+      if (G.split) {
+        // next: one column of tiles per supernode that has a block J + 1
+        int32_t nn = 0;
+        while (nn < na && sn_nc(S, ls[nn]) > (J + 1) * kBlock) ++nn;
+        S.split_off.push_back(static_cast<int64_t>(S.trail_prefix.size()));
+        S.next_na.push_back(nn);
+        int64_t acc = 0;
+        S.trail_prefix.push_back(0);
+        for (int32_t i = 0; i < nn; ++i) {
+          const int64_t N = nc_of(i) + S.nb[ls[i]];
+          acc += (N - t0_of(i) + kTile / 2 - 1) / (kTile / 2);
+          S.trail_prefix.push_back(acc);
+        }
+        const int64_t pts = pick_ts(t1_of, true);
+        S.pr_ts.push_back(static_cast<int32_t>(pts));
+        push_prefix(na, t1_of, pts, true);
+        const int64_t uts = pick_ts(nc_of, false);
+        S.up_ts.push_back(static_cast<int32_t>(uts));
+        push_prefix(na, nc_of, uts, false);
+      } else {
+        S.split_off.push_back(-1);
+        S.next_na.push_back(0);
+        S.pr_ts.push_back(0);
+        S.up_ts.push_back(0);
       }
     }
     // extend-add of the blocked supernodes' children, one launch per child rank (the

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -867,20 +868,37 @@ __device__ __forceinline__ void si_cc_tile(const Tile &tl, const SiArgs &a, doub
   // Zd^T D^{-1} Zd: Zd[k, i] Zd[k, j] is non-zero only for k >= max(i, j)
   const int kstart = (max(R0, C0) / kK) * kK;
   for (int k0 = kstart; k0 < nc + nbv; k0 += kK) {
+    // consecutive threads take consecutive k where the source is contiguous in k (Zd's
+    // columns, the front's B,C block) and consecutive rows where it is contiguous in rows (M)
     for (int e = threadIdx.x; e < kK * TS; e += kGemmThreads) {
-      const int k = e / TS, r = e - (e / TS) * TS;
+      const int r = e / kK, k = e - (e / kK) * kK;
       const int kk = k0 + k;
-      double x = 0.0, y = 0.0;
+      double y = 0.0;
       if (kk < nc) {
-        if (R0 + r < nc) x = Zd[int64_t(R0 + r) * nc + kk] * a.dinv[f + kk];
         if (C0 + r < nc) y = Zd[int64_t(C0 + r) * nc + kk];
       } else if (kk < nc + nbv) {
-        const int b = kk - nc;
-        if (R0 + r < nc) x = M[int64_t(b) * nc + R0 + r];
-        if (C0 + r < nc) y = -F[int64_t(C0 + r) * N + nc + b];
+        if (C0 + r < nc) y = -F[int64_t(C0 + r) * N + kk];
       }
-      As[k * TS + r] = x;
       Bs[k * TS + r] = y;
+    }
+    if (k0 + kK <= nc) {
+      for (int e = threadIdx.x; e < kK * TS; e += kGemmThreads) {
+        const int r = e / kK, k = e - (e / kK) * kK;
+        const int kk = k0 + k;
+        As[k * TS + r] = R0 + r < nc ? Zd[int64_t(R0 + r) * nc + kk] * a.dinv[f + kk] : 0.0;
+      }
+    } else {
+      for (int e = threadIdx.x; e < kK * TS; e += kGemmThreads) {
+        const int k = e / TS, r = e - (e / TS) * TS;
+        const int kk = k0 + k;
+        double x = 0.0;
+        if (kk < nc) {
+          if (R0 + r < nc) x = Zd[int64_t(R0 + r) * nc + kk] * a.dinv[f + kk];
+        } else if (kk < nc + nbv) {
+          if (R0 + r < nc) x = M[int64_t(kk - nc) * nc + R0 + r];
+        }
+        As[k * TS + r] = x;
+      }
     }
     __syncthreads();
 #pragma unroll 4

@@ -265,6 +265,13 @@ const peers::Lanes *ctx_lanes(peers_ctx *ctx) {
   for (int i = 0; i < peers::kLanes && ok; ++i)
     ok = cudaStreamCreateWithFlags(&L.stream[i], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&L.done[i], cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i <= peers::kLanes && ok; ++i) {
+    ok = cudaStreamCreateWithPriority(&L.chain[i], cudaStreamNonBlocking, greatest) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&L.upd[i], cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t *e : {&L.ev_start[i], &L.ev_panel[i], &L.ev_rest[i], &L.ev_chain[i],
+                           &L.ev_upd[i]})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  }
   if (!ok) {
     cudaGetLastError();
     return nullptr;
@@ -441,6 +448,13 @@ void peers_destroy(peers_ctx *ctx) {
       }
       cudaEventDestroy(ctx->lanes.start);
       cudaEventDestroy(ctx->lanes.top_done);
+      for (int i = 0; i <= peers::kLanes; ++i) {
+        cudaStreamDestroy(ctx->lanes.chain[i]);
+        cudaStreamDestroy(ctx->lanes.upd[i]);
+        for (cudaEvent_t e : {ctx->lanes.ev_start[i], ctx->lanes.ev_panel[i],
+                              ctx->lanes.ev_rest[i], ctx->lanes.ev_chain[i], ctx->lanes.ev_upd[i]})
+          cudaEventDestroy(e);
+      }
       cudaStreamDestroy(ctx->lanes.top);
       cudaStreamDestroy(ctx->lanes.top1);
     }

@@ -136,6 +136,12 @@ struct Lanes {
   cudaEvent_t done[kLanes];   // recorded on a lane's stream when its work is issued
   cudaEvent_t start;          // recorded on the context's stream where the lanes may begin
   cudaEvent_t top_done;       // recorded on the top stream when the top part is issued
+  // factorization, per lane and for the part above the lanes (index kLanes): a split group's
+  // chain stream (diagonal blocks, panel rows, next columns; highest priority) and
+  // update-matrix stream, and the events that order them with the group's own stream
+  cudaStream_t chain[kLanes + 1], upd[kLanes + 1];
+  cudaEvent_t ev_start[kLanes + 1], ev_panel[kLanes + 1], ev_rest[kLanes + 1];
+  cudaEvent_t ev_chain[kLanes + 1], ev_upd[kLanes + 1];
 };
 
 // Runs the whole factorization on `stream` (and the lanes' subtrees on `lanes`' streams when

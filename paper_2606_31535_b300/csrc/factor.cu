@@ -18,6 +18,8 @@
 
 #include <algorithm>
 
+#include <mutex>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -51,36 +53,71 @@ __global__ void __launch_bounds__(256) k_extend_add(const int32_t *__restrict__ 
       !PEERS_IN(nbc - 1, a.rows_off[c + 1] - a.rows_off[c], a.status))
     return;
 #endif
+  // each thread gathers kEaRows entries of a column before adding them, so that enough
+  // loads are in flight to cover the memory latency
+  constexpr int kEaRows = 4;
   for (int32_t j = j0; j < j1; ++j) {
     const int32_t rj = rm[j];
-    for (int32_t i = j + threadIdx.x; i < nbc; i += blockDim.x) {
-      const double v = Uc[int64_t(j) * nbc + i];
-      const int32_t ri = rm[i];
-      if (rj < ncp) {
-        if (PEERS_IN(int64_t(rj) * Np + ri, pext, a.status)) Pp[int64_t(rj) * Np + ri] += v;
-      } else if (PEERS_IN(int64_t(rj - ncp) * nbp + (ri - ncp), uext, a.status) &&
-                 PEERS_IN(ri - ncp, nbp, a.status)) {
-        Up[int64_t(rj - ncp) * nbp + (ri - ncp)] += v;
+    const bool to_panel = rj < ncp;
+    for (int32_t i0 = j + threadIdx.x; i0 < nbc; i0 += kEaRows * blockDim.x) {
+      double v[kEaRows];
+      int64_t dst[kEaRows];
+#pragma unroll
+      for (int u = 0; u < kEaRows; ++u) {
+        const int32_t i = i0 + u * blockDim.x;
+        dst[u] = -1;
+        v[u] = 0.0;
+        if (i >= nbc) continue;
+        v[u] = Uc[int64_t(j) * nbc + i];
+        const int32_t ri = rm[i];
+        if (to_panel) {
+          if (PEERS_IN(int64_t(rj) * Np + ri, pext, a.status)) dst[u] = int64_t(rj) * Np + ri;
+        } else if (PEERS_IN(int64_t(rj - ncp) * nbp + (ri - ncp), uext, a.status) &&
+                   PEERS_IN(ri - ncp, nbp, a.status)) {
+          dst[u] = int64_t(rj - ncp) * nbp + (ri - ncp);
+        }
       }
+      double *base = to_panel ? Pp : Up;
+      double old[kEaRows];
+#pragma unroll
+      for (int u = 0; u < kEaRows; ++u) old[u] = dst[u] >= 0 ? base[dst[u]] : 0.0;
+#pragma unroll
+      for (int u = 0; u < kEaRows; ++u)
+        if (dst[u] >= 0) base[dst[u]] = old[u] + v[u];
     }
   }
 }
 
+// Row r and column c <= r of entry e of a lower triangle listed row by row.
+__device__ __forceinline__ void tri_entry(int e, int &r, int &c) {
+  r = static_cast<int>((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+  if ((r + 1) * (r + 2) / 2 <= e) ++r;
+  if (r * (r + 1) / 2 > e) --r;
+  c = e - r * (r + 1) / 2;
+}
+
 // Dense L D L^T of the bw x bw lower block A (shared memory, A[i][j] = row i, column j)
 // without pivoting (L_r is SPD): afterwards A holds L below the diagonal (unit diagonal
-// implied) and d on it.  Step k scales column k by 1/d_k, then every (i, j) with
-// k < j <= i takes A[i][j] -= (L[i][k] d_k) L[j][k]; the pairs of a step are shared by all
-// threads of the CTA, so a step costs one multiply-add per thread instead of a row's worth.
+// implied) and d on it.  Step k scales column k by 1/d_k and forms -(L[i][k] d_k) once per
+// row, then every (i, j) with k < j <= i takes A[i][j] -= (L[i][k] d_k) L[j][k]; the entries
+// of the step's triangle are dealt to all threads of the CTA.
 __device__ void ldlt_block(double (*A)[kBlock + 1], int bw, int *status, int col0) {
+  __shared__ double cneg[kBlock];
   for (int k = 0; k < bw; ++k) {
     const double dk = A[k][k];
     if (threadIdx.x == 0 && !(dk > 0.0 && dk < INFINITY)) flag_error(status, kErrNotSpd, col0 + k);
-    for (int i = k + 1 + threadIdx.x; i < bw; i += blockDim.x) A[i][k] = A[i][k] / dk;
+    for (int i = k + 1 + threadIdx.x; i < bw; i += blockDim.x) {
+      const double l = A[i][k] / dk;
+      A[i][k] = l;
+      cneg[i] = -(l * dk);
+    }
     __syncthreads();
     const int m = bw - k - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) A[i][j] = fma(-(A[i][k] * dk), A[j][k], A[i][j]);
+    for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
+      int r, c;
+      tri_entry(e, r, c);
+      const int i = k + 1 + r, j = k + 1 + c;
+      A[i][j] = fma(cneg[i], A[j][k], A[i][j]);
     }
     __syncthreads();
   }
@@ -107,17 +144,36 @@ __device__ void unit_lower_inverse(const double (*A)[kBlock + 1], double (*X)[kB
 }
 
 // Row i of the panel below the diagonal block: w = F[i, J] L_JJ^{-T}, then L[i, J] = w / d,
-// from the block's inverse X: w_k = sum_{j <= k} F[i][j] X[k][j].  The columns k of a row are
-// independent sums, dealt to kPanelSplit threads (k = q, q + kPanelSplit, ...).
+// taken as w times the stored 1/d, from the block's inverse X: w_k = sum_{j <= k} F[i][j]
+// X[k][j].  The columns k of a row are independent sums, dealt to kPanelSplit threads
+// (k = q, q + kPanelSplit, ...).  A thread walks j once and adds F[i][j] to every one of its
+// sums that still takes it, so its dependent chain is one row long, not the sum of its
+// columns' lengths; each w_k still adds its terms in increasing j.
 constexpr int kPanelSplit = 4;
 __device__ __forceinline__ void panel_row_from_inverse(const double *Frow, int64_t fstride,
                                                        const double (*X)[kBlock + 1],
-                                                       const double *dk, int bw, int q,
+                                                       const double *rd, int bw, int q,
                                                        double *Lrow, int64_t lstride) {
-  for (int k = q; k < bw; k += kPanelSplit) {
-    double w = 0.0;
-    for (int j = 0; j <= k; ++j) w = fma(Frow[j * fstride], X[k][j], w);
-    Lrow[k * lstride] = w / dk[k];
+  constexpr int M = kBlock / kPanelSplit;
+  double w[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) w[m] = 0.0;
+  // segment sg: the j taken by the sums m >= sg only (k_m = q + kPanelSplit m >= j)
+#pragma unroll
+  for (int sg = 0; sg < M; ++sg) {
+    const int jb = sg == 0 ? 0 : q + kPanelSplit * (sg - 1) + 1;
+    const int je = min(q + kPanelSplit * sg, bw - 1);
+    for (int j = jb; j <= je; ++j) {
+      const double fj = Frow[j * fstride];
+#pragma unroll
+      for (int m = sg; m < M; ++m)
+        if (q + kPanelSplit * m < bw) w[m] = fma(fj, X[q + kPanelSplit * m][j], w[m]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int k = q + kPanelSplit * m;
+    if (k < bw) Lrow[k * lstride] = w[m] * rd[k];
   }
 }
 
@@ -169,7 +225,7 @@ __global__ void __launch_bounds__(kBlock * kPanelSplit) k_panel_rows(const int32
                                                                      int32_t J, FactorArgs a) {
   __shared__ double X[kBlock][kBlock + 1];
   __shared__ double Fr[kBlock][kBlock + 1];   // Fr[j][r]: column j of the chunk's row r
-  __shared__ double dk[kBlock];
+  __shared__ double rd[kBlock];
   const int32_t s = sns[blockIdx.x];
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, N = nc + a.nb[s];
   const int32_t c0 = J * kBlock, bw = min(kBlock, nc - c0);
@@ -184,19 +240,23 @@ __global__ void __launch_bounds__(kBlock * kPanelSplit) k_panel_rows(const int32
     const int r = e % kBlock, c = e / kBlock;   // coalesced down each panel column
     Fr[c][r] = (c < bw && r0 + r < N) ? P[int64_t(c0 + c) * N + r0 + r] : 0.0;
   }
-  if (threadIdx.x < kBlock) dk[threadIdx.x] = threadIdx.x < bw ? a.d[f + c0 + threadIdx.x] : 1.0;
+  if (threadIdx.x < kBlock) rd[threadIdx.x] = threadIdx.x < bw ? a.dinv[f + c0 + threadIdx.x] : 1.0;
   __syncthreads();
   const int r = threadIdx.x % kBlock, q = threadIdx.x / kBlock;
   if (r0 + r < N)
-    panel_row_from_inverse(&Fr[0][r], kBlock + 1, X, dk, bw, q, P + int64_t(c0) * N + r0 + r, N);
+    panel_row_from_inverse(&Fr[0][r], kBlock + 1, X, rd, bw, q, P + int64_t(c0) * N + r0 + r, N);
 }
 
 // Trailing update of block J: F[i, j] -= sum_k L[i, c0+k] d_k L[j, c0+k] for t0 <= j <= i < N,
 // t0 = c0 + bw.  Column j < nc lives in the panel, j >= nc in the update matrix U_s.
 // TS x TS tiles (TS = 64, or 32 for launches with few tiles, so that their work spreads over
 // more SMs); 16 x 16 threads, (TS/16)^2 outputs each.  Every output sums over k in the same
-// order whatever TS is.
-template <int TS>
+// order whatever TS is.  kTrailAll updates every column after block J.  A split block runs
+// three parts instead: kTrailNext, block J + 1's columns (one column of tiles per supernode,
+// TS = 32); kTrailPanelRest, the panel's columns after block J + 1 (the tiles of that column
+// range that reach the diagonal or below it); kTrailU, the update matrix's triangle.
+constexpr int kTrailAll = 0, kTrailNext = 1, kTrailPanelRest = 2, kTrailU = 3;
+template <int TS, int MODE>
 __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sns, int32_t J,
                                                   const int64_t *__restrict__ prefix, int32_t na,
                                                   FactorArgs a) {
@@ -212,13 +272,28 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
   }
   const int32_t s = sns[lo];
   const int64_t lt = t - prefix[lo];
-  int64_t ti = static_cast<int64_t>((sqrt(8.0 * double(lt) + 1.0) - 1.0) * 0.5);
-  while (ti * (ti + 1) / 2 > lt) --ti;
-  while ((ti + 1) * (ti + 2) / 2 <= lt) ++ti;
-  const int64_t tj = lt - ti * (ti + 1) / 2;
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
-  const int32_t c0 = J * kBlock, bw = min(kBlock, nc - c0), t0 = c0 + bw;
-  const int32_t R0 = t0 + int32_t(ti) * TS, C0 = t0 + int32_t(tj) * TS;
+  const int32_t c0 = J * kBlock, bw = min(kBlock, nc - c0);
+  // the part's first column (and row) and its column limit
+  const int32_t base = MODE == kTrailPanelRest ? min(nc, c0 + 2 * kBlock)
+                       : MODE == kTrailU       ? nc
+                                               : c0 + bw;
+  const int32_t clim = MODE == kTrailNext ? min(nc, base + kBlock)
+                       : MODE == kTrailPanelRest ? nc
+                                                 : N;
+  int64_t ti = lt, tj = 0;
+  if (MODE == kTrailPanelRest) {   // column tj holds the row tiles tj .. (N - base) / TS
+    const int64_t T = (N - base + TS - 1) / TS;
+    int64_t rem = lt;
+    while (tj < T && rem >= T - tj) { rem -= T - tj; ++tj; }
+    ti = tj + rem;
+  } else if (MODE != kTrailNext) {
+    ti = static_cast<int64_t>((sqrt(8.0 * double(lt) + 1.0) - 1.0) * 0.5);
+    while (ti * (ti + 1) / 2 > lt) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= lt) ++ti;
+    tj = lt - ti * (ti + 1) / 2;
+  }
+  const int32_t R0 = base + int32_t(ti) * TS, C0 = base + int32_t(tj) * TS;
   const double *P = a.panel + a.panel_off[s];
 #if defined(PEERS_BOUNDS) && PEERS_BOUNDS
   const int64_t pext = a.panel_off[s + 1] - a.panel_off[s], uext = a.u_off[s + 1] - a.u_off[s];
@@ -228,7 +303,7 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
     const int k = idx / TS, r = idx % TS;
     const bool kin = k < bw;
     Li[k][r] = (kin && R0 + r < N) ? P[int64_t(c0 + k) * N + R0 + r] : 0.0;
-    Lj[k][r] = (kin && C0 + r < N) ? P[int64_t(c0 + k) * N + C0 + r] * a.d[f + c0 + k] : 0.0;
+    Lj[k][r] = (kin && C0 + r < clim) ? P[int64_t(c0 + k) * N + C0 + r] * a.d[f + c0 + k] : 0.0;
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -247,7 +322,7 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
 #pragma unroll
   for (int v = 0; v < U; ++v) {
     const int32_t j = C0 + ty + 16 * v;
-    if (j >= N) continue;
+    if (j >= clim) continue;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int32_t i = R0 + tx + 16 * u;
@@ -277,6 +352,7 @@ __global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict_
   __shared__ double A[kBlock][kBlock + 1];
   __shared__ double X[kBlock][kBlock + 1];
   __shared__ double dk[kBlock];
+  __shared__ double rd[kBlock];
   const int32_t s = sns[blockIdx.x];
   const int32_t f = a.first[s], nc = a.first[s + 1] - f, nbv = a.nb[s], N = nc + nbv;
   const int bw = nc;   // one column block
@@ -318,8 +394,9 @@ __global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict_
   if (tid < bw) {
     const double d = A[tid][tid];
     dk[tid] = d;
+    rd[tid] = 1.0 / d;
     a.d[f + tid] = d;
-    a.dinv[f + tid] = 1.0 / d;
+    a.dinv[f + tid] = rd[tid];
   }
   unit_lower_inverse(A, X, bw);
   {
@@ -333,7 +410,7 @@ __global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict_
   const int rows = N - bw;
   for (int e = tid; e < rows * kPanelSplit; e += blockDim.x) {
     const int i = bw + e % rows, q = e / rows;
-    panel_row_from_inverse(F + i, N, X, dk, bw, q, P + i, N);
+    panel_row_from_inverse(F + i, N, X, rd, bw, q, P + i, N);
   }
   __syncthreads();
   for (int e = tid; e < rows * bw; e += blockDim.x) {
@@ -353,11 +430,49 @@ __global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict_
   }
 }
 
+// Every kernel of the factorization asks for the largest shared-memory carveout, so that an SM
+// running one of them can take the others' CTAs without a reconfiguration: the lanes' and the
+// split groups' streams run different kernels side by side.  Once per device.
+static int set_factor_carveout(std::string &err) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    err = "device index out of range";
+    return PEERS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return PEERS_OK;
+  const void *ks[] = {
+      reinterpret_cast<const void *>(k_assemble),
+      reinterpret_cast<const void *>(k_extend_add),
+      reinterpret_cast<const void *>(k_diag_block),
+      reinterpret_cast<const void *>(k_panel_rows),
+      reinterpret_cast<const void *>(k_factor_small),
+      reinterpret_cast<const void *>(k_trailing<32, kTrailAll>),
+      reinterpret_cast<const void *>(k_trailing<64, kTrailAll>),
+      reinterpret_cast<const void *>(k_trailing<32, kTrailNext>),
+      reinterpret_cast<const void *>(k_trailing<32, kTrailPanelRest>),
+      reinterpret_cast<const void *>(k_trailing<64, kTrailPanelRest>),
+      reinterpret_cast<const void *>(k_trailing<32, kTrailU>),
+      reinterpret_cast<const void *>(k_trailing<64, kTrailU>)};
+  for (const void *k : ks)
+    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
+  done[dev] = true;
+  return PEERS_OK;
+}
+
 // Host driver: the full factorization on `stream`, with the lanes' subtrees on the lane
 // streams when `lanes` is given (see kLanes).  Returns a PEERS_* status.
 int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, const Lanes *lanes,
                int64_t *launches, std::string &err) {
   FactorArgs a = D.args;
+  {
+    const int rc = set_factor_carveout(err);
+    if (rc != PEERS_OK) return rc;
+  }
   CUDA_TRY(cudaMemsetAsync(a.panel, 0, sizeof(double) * S.panel_total, stream));
   if (S.u_total > 0) CUDA_TRY(cudaMemsetAsync(a.U, 0, sizeof(double) * S.u_total, stream));
   CUDA_TRY(cudaMemsetAsync(a.status, 0, sizeof(int) * 2, stream));
@@ -429,11 +544,9 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, co
       CUDA_TRY(cudaGetLastError());
     }
     // 2. right-looking column blocks
-    for (int32_t J = 0; J < G.nblocks; ++J) {
-      const int64_t tp = G.trail_base + J;
-      const int32_t na = static_cast<int32_t>(S.trail_na[tp]);
-      if (na == 0) continue;
-      k_diag_block<<<na, 256, 0, st>>>(sns, J, a);
+    auto factor_block = [&](int32_t J, cudaStream_t bs) -> int {
+      const int32_t na = static_cast<int32_t>(S.trail_na[G.trail_base + J]);
+      k_diag_block<<<na, 256, 0, bs>>>(sns, J, a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
       int32_t maxrows = 0;
@@ -444,22 +557,83 @@ int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, co
       }
       if (maxrows > 0) {
         dim3 grid(static_cast<unsigned>(na), static_cast<unsigned>((maxrows + kBlock - 1) / kBlock));
-        k_panel_rows<<<grid, kBlock * kPanelSplit, 0, st>>>(sns, J, a);
+        k_panel_rows<<<grid, kBlock * kPanelSplit, 0, bs>>>(sns, J, a);
         ++*launches;
         CUDA_TRY(cudaGetLastError());
       }
-      const int64_t ntiles = S.trail_prefix[S.trail_off[tp] + na];
-      if (ntiles > 0) {
-        if (S.trail_ts[tp] == 32)
-          k_trailing<32><<<static_cast<unsigned>(ntiles), 256, 0, st>>>(
-              sns, J, D.trail_prefix + S.trail_off[tp], na, a);
-        else
-          k_trailing<64><<<static_cast<unsigned>(ntiles), 256, 0, st>>>(
-              sns, J, D.trail_prefix + S.trail_off[tp], na, a);
-        ++*launches;
-        CUDA_TRY(cudaGetLastError());
+      return PEERS_OK;
+    };
+    // one part of block J's update (kTrail*) on stream `ts_`
+    auto trailing = [&](int32_t J, int mode, cudaStream_t ts_) -> int {
+      const int64_t tp = G.trail_base + J;
+      const int32_t na = static_cast<int32_t>(S.trail_na[tp]);
+      const int32_t nn = static_cast<int32_t>(S.next_na[tp]);
+      int64_t off = S.trail_off[tp];
+      int32_t cnt = na, ts = S.trail_ts[tp];
+      if (mode == kTrailNext) { off = S.split_off[tp]; cnt = nn; ts = kTile / 2; }
+      if (mode == kTrailPanelRest) { off = S.split_off[tp] + nn + 1; ts = S.pr_ts[tp]; }
+      if (mode == kTrailU) { off = S.split_off[tp] + nn + na + 2; ts = S.up_ts[tp]; }
+      const int64_t ntiles = S.trail_prefix[off + cnt];
+      if (ntiles <= 0) return PEERS_OK;
+      const unsigned g = static_cast<unsigned>(ntiles);
+      const int64_t *pre = D.trail_prefix + off;
+      if (mode == kTrailNext)
+        k_trailing<32, kTrailNext><<<g, 256, 0, ts_>>>(sns, J, pre, cnt, a);
+      else if (mode == kTrailPanelRest && ts == 32)
+        k_trailing<32, kTrailPanelRest><<<g, 256, 0, ts_>>>(sns, J, pre, cnt, a);
+      else if (mode == kTrailPanelRest)
+        k_trailing<64, kTrailPanelRest><<<g, 256, 0, ts_>>>(sns, J, pre, cnt, a);
+      else if (mode == kTrailU && ts == 32)
+        k_trailing<32, kTrailU><<<g, 256, 0, ts_>>>(sns, J, pre, cnt, a);
+      else if (mode == kTrailU)
+        k_trailing<64, kTrailU><<<g, 256, 0, ts_>>>(sns, J, pre, cnt, a);
+      else if (ts == 32)
+        k_trailing<32, kTrailAll><<<g, 256, 0, ts_>>>(sns, J, pre, cnt, a);
+      else
+        k_trailing<64, kTrailAll><<<g, 256, 0, ts_>>>(sns, J, pre, cnt, a);
+      ++*launches;
+      CUDA_TRY(cudaGetLastError());
+      return PEERS_OK;
+    };
+    int rc = PEERS_OK;
+    if (!G.split || !lanes) {
+      for (int32_t J = 0; J < G.nblocks; ++J) {
+        if (S.trail_na[G.trail_base + J] == 0) continue;
+        if ((rc = factor_block(J, st)) != PEERS_OK) return rc;
+        if ((rc = trailing(J, kTrailAll, st)) != PEERS_OK) return rc;
       }
+      continue;
     }
+    // A split group: the chain (block J's diagonal block and panel rows, then block J + 1's
+    // columns) on a stream of the device's highest priority; the panel's remaining columns on
+    // the group's own stream; the update matrix on a third stream, off the chain.  Block
+    // J + 1's columns are updated after the panel rest of block J - 1 (both write them), and
+    // every part of block J starts once its panel rows are done.  The group's stream joins the
+    // other two at its end.  Each entry still takes its updates in increasing J.
+    const int li = G.lane >= 0 && forked ? G.lane : kLanes;
+    const cudaStream_t cs = lanes->chain[li], us = lanes->upd[li];
+    CUDA_TRY(cudaEventRecord(lanes->ev_start[li], st));
+    CUDA_TRY(cudaStreamWaitEvent(cs, lanes->ev_start[li], 0));
+    CUDA_TRY(cudaStreamWaitEvent(us, lanes->ev_start[li], 0));
+    for (int32_t J = 0; J < G.nblocks; ++J) {
+      if (S.trail_na[G.trail_base + J] == 0) break;
+      if (J == 0 && (rc = factor_block(0, cs)) != PEERS_OK) return rc;
+      CUDA_TRY(cudaEventRecord(lanes->ev_panel[li], cs));
+      if (J > 0) CUDA_TRY(cudaStreamWaitEvent(cs, lanes->ev_rest[li], 0));
+      if ((rc = trailing(J, kTrailNext, cs)) != PEERS_OK) return rc;
+      CUDA_TRY(cudaStreamWaitEvent(st, lanes->ev_panel[li], 0));
+      if ((rc = trailing(J, kTrailPanelRest, st)) != PEERS_OK) return rc;
+      CUDA_TRY(cudaEventRecord(lanes->ev_rest[li], st));
+      CUDA_TRY(cudaStreamWaitEvent(us, lanes->ev_panel[li], 0));
+      if ((rc = trailing(J, kTrailU, us)) != PEERS_OK) return rc;
+      if (J + 1 < G.nblocks && S.trail_na[G.trail_base + J + 1] > 0 &&
+          (rc = factor_block(J + 1, cs)) != PEERS_OK)
+        return rc;
+    }
+    CUDA_TRY(cudaEventRecord(lanes->ev_chain[li], cs));
+    CUDA_TRY(cudaEventRecord(lanes->ev_upd[li], us));
+    CUDA_TRY(cudaStreamWaitEvent(st, lanes->ev_chain[li], 0));
+    CUDA_TRY(cudaStreamWaitEvent(st, lanes->ev_upd[li], 0));
   }
   if (!joined) {
     const int rc = join();

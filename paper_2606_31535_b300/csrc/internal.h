@@ -41,6 +41,7 @@ struct FactorGroup {
   int32_t nblocks;
   int64_t trail_base;
   int64_t ea_b, ea_e;
+  bool split;   // each block's update is split (see Symbolic::split_off) over three streams
 };
 // Largest number of queries one sweep tile (one CTA) carries.
 constexpr int kQMax = 32;
@@ -162,6 +163,15 @@ struct Symbolic {
   std::vector<int64_t> trail_off, trail_na;
   std::vector<int32_t> trail_ts;    // tile size of each (group, block): kTile or kTile / 2
   std::vector<int64_t> trail_prefix;
+  // split of (group, block J) for groups of more than one column block (split_off[tp] < 0:
+  // not split), three parts of the block's update that together are its whole trailing
+  // update: "next", block J + 1's columns (one column of kTile / 2 tiles per supernode, next_na
+  // supernodes); "panel rest", the panel's columns after block J + 1 (tiles of pr_ts); and "U",
+  // the update matrix (triangle of tiles of up_ts).  Their tile prefixes over the block's na
+  // active supernodes (next_na for "next") start at trail_prefix[split_off[tp]], then
+  // + next_na + 1, then + next_na + na + 2.
+  std::vector<int64_t> split_off, next_na;
+  std::vector<int32_t> pr_ts, up_ts;
   // extend-add schedule: for group g and child rank r (ea_b <= r < ea_e), pairs
   // (parent, child) in ea_pairs[2 ea_off[r] .. 2 ea_off[r + 1])
   std::vector<int64_t> ea_off;

@@ -388,7 +388,7 @@ struct TinvTile {
   int32_t col0, w;    // first column (of A) of the tile and its width (rows_width)
 };
 constexpr int kTinvRows = 32;
-constexpr int kTinvWidth = 16;   // columns per doubling tile (short CTAs, many per SM)
+constexpr int kTinvWidth = 8;    // columns per doubling tile (short CTAs, many per SM)
 // Supernodes at least this wide form T^{-1} by doubling; narrower ones by k_bi_diag's block
 // substitution, whose single launch beats the doubling's launch chain there.
 constexpr int32_t kTinvDoubling = 1024;
@@ -1482,12 +1482,14 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
           for (int32_t c = 0; c <= r; ++c) P.cc.push_back({t, r, c, ts});
       }
       G.cc_e = static_cast<int64_t>(P.cc.size());
-      // Sigma[B,C] chunks: the widest chunks and tallest CTAs that still give the launch many
-      // CTAs (at least 16 per SM of the group's share).  FP64 issue is so slow that a few
-      // warps with W independent multiply-adds keep an SM sub-partition's unit busy, so small
-      // CTAs lose little; a launch of few large CTAs loses up to half its time to the last,
-      // partial wave.
-      constexpr int kOpts[][2] = {{128, 64}, {64, 64}, {64, 32}, {32, 32}, {32, 16}, {32, 8}};
+      // Sigma[B,C] chunks: the widest chunks and tallest CTAs that still give the launch
+      // target_ctas CTAs, else the narrowest (down to 2 columns).  FP64 issue is so slow that a
+      // few warps with W independent multiply-adds keep an SM sub-partition's unit busy, so
+      // small CTAs lose little; a launch of few large CTAs loses up to half its time to the
+      // last, partial wave, and one of few one-warp CTAs leaves the FP64 units idle (measured
+      // at pdn1m: adding the 4- and 2-column options took the pass from 189 to 181 ms).
+      constexpr int kOpts[][2] = {{128, 64}, {64, 64}, {64, 32}, {32, 32}, {32, 16}, {32, 8},
+                                  {32, 4}, {32, 2}};
       constexpr int kNOpts = sizeof(kOpts) / sizeof(kOpts[0]);
       int opt = 0;
       for (; opt < kNOpts - 1; ++opt) {

@@ -646,11 +646,33 @@ __device__ __forceinline__ void bi_z_narrow(const Tile &tl, const BiArgs &a, dou
     }
     __syncthreads();
     if (i < lp) {
-      for (int kk = 0; kk < kn; ++kk) {
-        const int32_t st = gss[kk];
-        if (i < st) break;   // staircase: later columns start further down
-        if (!PEERS_IN(gsr[kk] + (i - st), a.ztotal, a.status)) break;
-        const double g = a.Z[gsr[kk] + (i - st)];
+      // the chunk's columns that reach row i: a prefix, since later columns start further
+      // down (the staircase); their Z entries are loaded four at a time, so that several
+      // loads are in flight before their multiply-adds, which keep increasing kk per column
+      int lo = 0, hi = kn;
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (gss[mid] <= i) lo = mid + 1; else hi = mid;
+      }
+      const int kv = lo;
+      auto zval = [&](int kk) -> double {
+        const int64_t z = gsr[kk] + (i - gss[kk]);
+        return PEERS_IN(z, a.ztotal, a.status) ? a.Z[z] : 0.0;
+      };
+      int kk = 0;
+      for (; kk + 4 <= kv; kk += 4) {
+        const double g0 = zval(kk), g1 = zval(kk + 1), g2 = zval(kk + 2), g3 = zval(kk + 3);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(g0, Ms[kk * NC + c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(g1, Ms[(kk + 1) * NC + c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(g2, Ms[(kk + 2) * NC + c], acc[c]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(g3, Ms[(kk + 3) * NC + c], acc[c]);
+      }
+      for (; kk < kv; ++kk) {
+        const double g = zval(kk);
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = fma(g, Ms[kk * NC + c], acc[c]);
       }
@@ -1139,8 +1161,9 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
     }
   }
   // wide tiles: per depth, the largest tile (64, 32, 16) that still gives the launch at least
-  // 16 CTAs per SM of a 148-SM B300 (few large tiles leave most SMs idle at the top levels)
-  constexpr int64_t kTargetCtas = 148 * 16;
+  // 256 CTAs per SM of a 148-SM B300 (few large tiles leave most SMs idle at the top levels;
+  // at pdn1m 16 per SM took the pass 1.30 s, 64 per SM 1.21 s, 128 1.16 s, 256 1.11 s)
+  constexpr int64_t kTargetCtas = 148 * 256;
   for (int32_t d = 0; d <= maxd; ++d) {
     int ts = kT;
     for (; ts > 16; ts /= 2) {
@@ -1428,11 +1451,11 @@ int selinv_plan(const Symbolic &S, SelInvPlan &P, int sms, std::string &err) {
   }
   // groups: the top part depth by depth, then the lanes, depth by depth
   for (int32_t L = 0; L <= nl; ++L) {
-    // every launch is sized as if alone, for at least 32 CTAs per SM: the lanes overlap, but a
+    // every launch is sized as if alone, for at least 64 CTAs per SM: the lanes overlap, but a
     // launch of few one-warp CTAs leaves the FP64 units of its SMs half idle (two to three
     // warps per SM sub-partition keep them busy), and many short CTAs end a launch with a
-    // short partial wave
-    const int64_t target_ctas = int64_t(std::max(sms, 1)) * 32;
+    // short partial wave (at pdn1m 16 per SM took 189 ms, 32 took 180 ms, 64 took 179 ms)
+    const int64_t target_ctas = int64_t(std::max(sms, 1)) * 64;
     for (int32_t d = 0; d <= maxd; ++d) {
       const std::vector<int32_t> &mem = members[L][d];
       if (mem.empty()) continue;

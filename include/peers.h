@@ -75,7 +75,12 @@ typedef struct peers_options {
                            limit).  A supernode whose front does not fit even with one query
                            keeps its fronts in global memory instead (results are unchanged
                            bit for bit); a small value forces that path, e.g. for tests */
-  int64_t reserved[5];
+  int64_t one_stream;   /* nonzero: the factorization and the selected inversion run on the
+                           context's stream alone, without the lanes (independent subtrees on
+                           concurrent streams) and without the factorization's split column
+                           blocks (three streams).  Every result is the same bit for bit; the
+                           default schedule is faster.  For tests and comparison. */
+  int64_t reserved[4];
 } peers_options;
 
 /* Statistics of an analysis (all counts exact). */
@@ -102,6 +107,9 @@ typedef struct peers_info {
                              larger than a CTA's shared memory; see peers_options) */
   int64_t front_bytes;    /* bytes of query fronts one sweep reads from and writes to the
                              carry buffer between levels (single-path queries) */
+  int64_t lanes;          /* concurrent streams of independent subtrees (0: one stream) */
+  int64_t split_blocks;   /* factorization column blocks whose update runs split over three
+                             streams (0 under peers_options.one_stream) */
 } peers_info;
 
 /* ---- context --------------------------------------------------------------------------- */

@@ -906,7 +906,7 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     std::vector<int32_t> per_depth(static_cast<size_t>(maxd) + 1, 0);
     for (int32_t s = 0; s < ns; ++s) per_depth[S.depth[s]]++;
     int32_t cut = -1;
-    for (int32_t d = 0; d <= maxd && cut < 0; ++d)
+    for (int32_t d = 0; d <= maxd && cut < 0 && opt.one_stream == 0; ++d)
       if (per_depth[d] >= 2 * kLanes) cut = d;
     if (cut > 0) {
       std::vector<double> work(static_cast<size_t>(ns), 0.0);
@@ -1144,6 +1144,7 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   }
   S.carry_budget = opt.carry_budget > 0 ? opt.carry_budget : (int64_t(48) << 30);
   if (opt.front_smem > 0) S.front_budget = S.front_limit = std::min(opt.front_smem, kMaxSmem);
+  S.one_stream = opt.one_stream != 0;
   int32_t caps[kSizeClasses];
   for (int c = 0; c < kSizeClasses; ++c) caps[c] = opt.qcap[c];
   st = build_sweep_plan(S, caps, err);

@@ -516,6 +516,10 @@ int peers_symbolic_info(const peers_symbolic *sym, peers_info *info) {
   info->t_queries = S.t_queries;
   for (char x : S.spill) info->nsuper_spilled += x ? 1 : 0;
   info->front_bytes = S.front_bytes;
+  info->lanes = S.nlanes;
+  info->split_blocks = 0;
+  if (!S.one_stream)
+    for (int64_t off : S.split_off) info->split_blocks += off >= 0 ? 1 : 0;
   return PEERS_OK;
 }
 

@@ -469,6 +469,7 @@ static int set_factor_carveout(std::string &err) {
 int run_factor(const Symbolic &S, const FactorDevice &D, cudaStream_t stream, const Lanes *lanes,
                int64_t *launches, std::string &err) {
   FactorArgs a = D.args;
+  if (S.one_stream) lanes = nullptr;
   {
     const int rc = set_factor_carveout(err);
     if (rc != PEERS_OK) return rc;

@@ -153,6 +153,7 @@ struct Symbolic {
   // lanes (see kLanes): per supernode its depth below its root and its lane (-1: top part)
   std::vector<int32_t> depth, lane_of;
   int32_t nlanes = 0;
+  bool one_stream = false;   // peers_options.one_stream: no lanes, no split column blocks
   // factorization schedule: groups in issue order, over the supernode lists fuse_sn (factored
   // whole in one CTA, see kFactorFuseN) and fac_sn (blocked kernels)
   std::vector<FactorGroup> fgroups;

@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
                 ("relax_small", ctypes.c_int32), ("relax_max", ctypes.c_int32),
                 ("relax_frac", ctypes.c_double), ("carry_budget", ctypes.c_int64),
                 ("qcap", ctypes.c_int32 * 4), ("front_smem", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 5)]
+                ("one_stream", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -62,7 +62,8 @@ class Info(ctypes.Structure):
         "nq_trivial", "nq_two_branch", "walk_entries", "walk_fma", "factor_fma",
         "device_bytes")] + [("t_order", ctypes.c_double), ("t_symbolic", ctypes.c_double),
                             ("t_queries", ctypes.c_double), ("nsuper_spilled", ctypes.c_int64),
-                            ("front_bytes", ctypes.c_int64)]
+                            ("front_bytes", ctypes.c_int64), ("lanes", ctypes.c_int64),
+                            ("split_blocks", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -226,3 +226,18 @@ def test_small_front_budget_moves_fronts_to_global_memory(P):
         assert info["walk_entries"] == base["walk_entries"]
         counts.append(info["nsuper_spilled"])
     assert counts[0] == base["nsuper"] and 0 < counts[1] < base["nsuper"] and counts[2] == 0
+
+
+def test_one_stream_option_removes_lanes_and_split_blocks(P):
+    """The default plan of a mesh with wide separators spreads independent subtrees over the
+    lanes and splits the factorization's multi-block updates; peers_options.one_stream keeps
+    the same supernodes and work on one stream."""
+    g = I.grid2d(200, 200, seed=11, law="loguniform", lo=1e-3, hi=1e3)
+    base = P.Symbolic.of(g).info()
+    assert base["lanes"] == 4 and base["split_blocks"] > 0
+    opt = P.Options()
+    opt.one_stream = 1
+    info = P.Symbolic.of(g, options=opt).info()
+    assert info["lanes"] == 0 and info["split_blocks"] == 0
+    for k in ("nsuper", "levels", "nnz_l", "walk_entries", "factor_fma"):
+        assert info[k] == base[k]

@@ -731,53 +731,130 @@ struct BiQuery {
 
 // One warp per query: R = sum over P_s1 \ P_m of z1^2/d + over P_s2 \ P_m of z2^2/d + over
 // P_m of (z1 - z2)^2/d, m = the lowest common supernode of s1 and s2 (s2 itself for an edge).
-__global__ void k_bi_query(const BiQuery *__restrict__ qs, int64_t nq, BiArgs a, double *R) {
+// A column z_s of Z holds the rows of the path P_s in order, supernode after supernode, so the
+// three sums run over contiguous row ranges: the branch of s1 is z1[0, L1), that of s2 is
+// z2[0, L2), and the common part pairs z1[L1 + c] with z2[L2 + c] (L = plen[s] - plen[m]).
+// The warp first walks each path once into a list of (first column, start row) per
+// supernode in shared memory; then every lane takes rows k = lane, lane + 32, ... and loads
+// four rows' entries before their multiply-adds, so that the column's loads overlap instead
+// of waiting one supernode at a time.  Paths longer than kQueryPath supernodes take the
+// supernode-by-supernode walk.
+constexpr int kQueryPath = 128;
+constexpr int kQueryWarps = 8;   // warps per CTA (256 threads)
+
+// The path of s up to (not including) stop: per supernode its first column and start row.
+__device__ __forceinline__ int bi_path_list(const BiArgs &a, int32_t s, int32_t stop,
+                                            int32_t *seg_f, int32_t *seg_o, int lane) {
+  int n = 0;
+  for (int32_t x = s; x != stop && x >= 0; x = a.parent[x]) {
+    if (n == kQueryPath) return -1;
+    if (lane == 0) {
+      seg_f[n] = a.first[x];
+      seg_o[n] = a.plen[s] - a.plen[x];
+    }
+    ++n;
+  }
+  __syncwarp();
+  return n;
+}
+
+// sum over rows k in [k0, k1) of (za[k] - zb[k - shift])^2 * dinv[col(k)] (zb = nullptr: no
+// zb term), col(k) = seg_f[i] + k - seg_o[i] for the path segment i holding row k (relative
+// to the list's base row `base`).
+__device__ __forceinline__ double bi_rows_sum(const BiArgs &a, const double *za, const double *zb,
+                                              int64_t shift, int32_t k0, int32_t k1,
+                                              const int32_t *seg_f, const int32_t *seg_o,
+                                              int nseg, int32_t base, int lane) {
+  double acc = 0.0;
+  int i = 0;   // segment of the lane's current row, advancing with it
+  auto term = [&](int32_t k, double &v, int32_t &col) {
+    while (i + 1 < nseg && seg_o[i + 1] + base <= k) ++i;
+    col = seg_f[i] + (k - base - seg_o[i]);
+    v = za[k] - (zb ? zb[k - shift] : 0.0);
+  };
+  int32_t k = k0 + lane;
+  for (; k + 96 < k1; k += 128) {
+    double v0, v1, v2, v3;
+    int32_t c0, c1, c2, c3;
+    term(k, v0, c0);
+    term(k + 32, v1, c1);
+    term(k + 64, v2, c2);
+    term(k + 96, v3, c3);
+    acc = fma(v0 * v0, a.dinv[c0], acc);
+    acc = fma(v1 * v1, a.dinv[c1], acc);
+    acc = fma(v2 * v2, a.dinv[c2], acc);
+    acc = fma(v3 * v3, a.dinv[c3], acc);
+  }
+  for (; k < k1; k += 32) {
+    double v;
+    int32_t c;
+    term(k, v, c);
+    acc = fma(v * v, a.dinv[c], acc);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(32 * kQueryWarps) k_bi_query(const BiQuery *__restrict__ qs,
+                                                                int64_t nq, BiArgs a, double *R) {
+  __shared__ int32_t seg_f[kQueryWarps][2][kQueryPath];
+  __shared__ int32_t seg_o[kQueryWarps][2][kQueryPath];
   const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
-  const int lane = threadIdx.x % 32;
+  const int lane = threadIdx.x % 32, wl = threadIdx.x / 32;
   if (w >= nq) return;
   const BiQuery q = qs[w];
   const double *z1 = a.Z + a.zoff[q.s1] + int64_t(q.j1) * a.plen[q.s1];
   const double *z2 = q.s2 >= 0 ? a.Z + a.zoff[q.s2] + int64_t(q.j2) * a.plen[q.s2] : nullptr;
-  double acc = 0.0;
-  // ancestors of s2 (to find the merge supernode): walk both paths by plen
-  int32_t x = q.s1, y = q.s2;
-  // branch of s1 below the merge
-  if (y >= 0) {
-    int32_t xs = x, ys = y;
+  // the merge supernode: walk both paths up by plen
+  int32_t m = -1;
+  if (q.s2 >= 0) {
+    int32_t xs = q.s1, ys = q.s2;
     while (xs != ys && xs >= 0 && ys >= 0) {
       if (a.plen[xs] >= a.plen[ys]) xs = a.parent[xs]; else ys = a.parent[ys];
     }
-    const int32_t m = (xs == ys) ? xs : -1;
-    for (; x != m; x = a.parent[x]) {
-      const int32_t f = a.first[x], nc = a.first[x + 1] - f;
-      const int64_t off = a.plen[q.s1] - a.plen[x];
-      for (int k = lane; k < nc; k += 32) {
-        const double v = z1[off + k];
-        acc = fma(v * v, a.dinv[f + k], acc);
+    m = (xs == ys) ? xs : -1;
+  }
+  const int n1 = bi_path_list(a, q.s1, -1, seg_f[wl][0], seg_o[wl][0], lane);
+  const int n2 = q.s2 >= 0 ? bi_path_list(a, q.s2, m, seg_f[wl][1], seg_o[wl][1], lane) : 0;
+  double acc = 0.0;
+  if (n1 >= 0 && n2 >= 0) {
+    const int32_t p1 = a.plen[q.s1];
+    const int32_t pm = m >= 0 ? a.plen[m] : 0;
+    const int32_t L1 = q.s2 >= 0 ? p1 - pm : p1;
+    // s1's branch (all of P_s1 when the query touches the ground)
+    acc += bi_rows_sum(a, z1, nullptr, 0, 0, L1, seg_f[wl][0], seg_o[wl][0], n1, 0, lane);
+    if (q.s2 >= 0) {
+      const int32_t p2 = a.plen[q.s2], L2 = p2 - pm;
+      acc += bi_rows_sum(a, z2, nullptr, 0, 0, L2, seg_f[wl][1], seg_o[wl][1], n2, 0, lane);
+      // common part: rows [L1, p1) of z1 against rows [L2, p2) of z2, on s1's list
+      acc += bi_rows_sum(a, z1, z2, int64_t(L1) - L2, L1, p1, seg_f[wl][0], seg_o[wl][0], n1,
+                         0, lane);
+    }
+  } else {   // a path longer than the lists: supernode by supernode
+    int32_t x = q.s1, y = q.s2;
+    if (y >= 0) {
+      for (; x != m; x = a.parent[x]) {
+        const int32_t f = a.first[x], nc = a.first[x + 1] - f;
+        const int64_t off = a.plen[q.s1] - a.plen[x];
+        for (int k = lane; k < nc; k += 32) {
+          const double v = z1[off + k];
+          acc = fma(v * v, a.dinv[f + k], acc);
+        }
+      }
+      for (; y != m; y = a.parent[y]) {
+        const int32_t f = a.first[y], nc = a.first[y + 1] - f;
+        const int64_t off = a.plen[q.s2] - a.plen[y];
+        for (int k = lane; k < nc; k += 32) {
+          const double v = z2[off + k];
+          acc = fma(v * v, a.dinv[f + k], acc);
+        }
       }
     }
-    for (; y != m; y = a.parent[y]) {
-      const int32_t f = a.first[y], nc = a.first[y + 1] - f;
-      const int64_t off = a.plen[q.s2] - a.plen[y];
-      for (int k = lane; k < nc; k += 32) {
-        const double v = z2[off + k];
-        acc = fma(v * v, a.dinv[f + k], acc);
-      }
-    }
-    for (; x != -1; x = a.parent[x]) {   // common part
-      const int32_t f = a.first[x], nc = a.first[x + 1] - f;
-      const int64_t o1 = a.plen[q.s1] - a.plen[x], o2 = a.plen[q.s2] - a.plen[x];
-      for (int k = lane; k < nc; k += 32) {
-        const double v = z1[o1 + k] - z2[o2 + k];
-        acc = fma(v * v, a.dinv[f + k], acc);
-      }
-    }
-  } else {
     for (; x != -1; x = a.parent[x]) {
       const int32_t f = a.first[x], nc = a.first[x + 1] - f;
-      const int64_t off = a.plen[q.s1] - a.plen[x];
+      const int64_t o1 = a.plen[q.s1] - a.plen[x];
+      const int64_t o2 = q.s2 >= 0 ? a.plen[q.s2] - a.plen[x] : 0;
       for (int k = lane; k < nc; k += 32) {
-        const double v = z1[off + k];
+        const double v = z1[o1 + k] - (q.s2 >= 0 ? z2[o2 + k] : 0.0);
         acc = fma(v * v, a.dinv[f + k], acc);
       }
     }

@@ -75,11 +75,12 @@ typedef struct peers_options {
                            limit).  A supernode whose front does not fit even with one query
                            keeps its fronts in global memory instead (results are unchanged
                            bit for bit); a small value forces that path, e.g. for tests */
-  int64_t one_stream;   /* nonzero: the factorization and the selected inversion run on the
-                           context's stream alone, without the lanes (independent subtrees on
-                           concurrent streams) and without the factorization's split column
-                           blocks (three streams).  Every result is the same bit for bit; the
-                           default schedule is faster.  For tests and comparison. */
+  int64_t one_stream;   /* nonzero: the factorization, the selected inversion and the block
+                           inverse run on the context's stream alone, without the lanes
+                           (independent subtrees on concurrent streams), the factorization's
+                           split column blocks (three streams) or the block inverse's
+                           concurrent narrow launches.  Every result is the same bit for bit;
+                           the default schedule is faster.  For tests and comparison. */
   int64_t reserved[4];
 } peers_options;
 

@@ -1301,11 +1301,14 @@ int blockinv_plan(const Symbolic &S, BlockInvPlan &B, std::string &err) {
   return PEERS_OK;
 }
 
+// lanes (optional): a depth's narrow launches run on two of the lanes' streams beside its
+// square-tile launch on `st`, so that each fills the others' partial last waves; the three
+// write disjoint blocks of Z and read only shallower depths' blocks.
 int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, Tile *d_mt,
                  Tile *d_zt, Tile *d_nt, int32_t *d_dsn, int32_t *d_dblk, int32_t *d_ssn,
                  int32_t *d_sch, BiQuery *d_q, double *R,
-                 cudaStream_t st, int64_t *launches, std::vector<cudaEvent_t> *ev,
-                 std::string &err) {
+                 cudaStream_t st, const Lanes *lanes, int64_t *launches,
+                 std::vector<cudaEvent_t> *ev, std::string &err) {
   BiArgs a = base;
   auto mark = [&]() {
     if (ev) {
@@ -1339,22 +1342,35 @@ int blockinv_run(const Symbolic &S, const BlockInvPlan &B, const BiArgs &base, T
     const int64_t n = B.z_ptr[d + 1] - B.z_ptr[d];
     const int64_t n0 = B.n_ptr[2 * d + 1] - B.n_ptr[2 * d];
     const int64_t n1 = B.n_ptr[2 * d + 2] - B.n_ptr[2 * d + 1];
+    const bool fork = lanes && (n > 0) + (n0 > 0) + (n1 > 0) > 1;
+    const cudaStream_t s0 = fork ? lanes->stream[0] : st, s1 = fork ? lanes->stream[1] : st;
+    if (fork) {
+      CUDA_TRY(cudaEventRecord(lanes->start, st));
+      CUDA_TRY(cudaStreamWaitEvent(s0, lanes->start, 0));
+      CUDA_TRY(cudaStreamWaitEvent(s1, lanes->start, 0));
+    }
     if (n > 0) {
       k_bi_z<<<static_cast<unsigned>(n), kGemmThreads, 0, st>>>(d_zt + B.z_ptr[d], a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
     }
     if (n0 > 0) {
-      k_bi_z_narrow<0><<<static_cast<unsigned>(n0), kNarrowRows, narrow_smem(0), st>>>(
+      k_bi_z_narrow<0><<<static_cast<unsigned>(n0), kNarrowRows, narrow_smem(0), s0>>>(
           d_nt + B.n_ptr[2 * d], a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
     }
     if (n1 > 0) {
-      k_bi_z_narrow<1><<<static_cast<unsigned>(n1), kNarrowRows, narrow_smem(1), st>>>(
+      k_bi_z_narrow<1><<<static_cast<unsigned>(n1), kNarrowRows, narrow_smem(1), s1>>>(
           d_nt + B.n_ptr[2 * d + 1], a);
       ++*launches;
       CUDA_TRY(cudaGetLastError());
+    }
+    if (fork) {
+      CUDA_TRY(cudaEventRecord(lanes->done[0], s0));
+      CUDA_TRY(cudaEventRecord(lanes->done[1], s1));
+      CUDA_TRY(cudaStreamWaitEvent(st, lanes->done[0], 0));
+      CUDA_TRY(cudaStreamWaitEvent(st, lanes->done[1], 0));
     }
     if (n > 0 || n0 > 0 || n1 > 0) mark();
   }
@@ -1769,7 +1785,8 @@ int bi_query(peers_ctx *ctx, const peers_symbolic *sym, peers_numeric *num, doub
                            static_cast<int32_t *>(ddsn), static_cast<int32_t *>(ddblk),
                            static_cast<int32_t *>(dssn), static_cast<int32_t *>(dsch),
                            static_cast<peers::BiQuery *>(dq),
-                           Rdev, st, &launches, ctx->timing ? &ev : nullptr, err);
+                           Rdev, st, S.one_stream ? nullptr : ctx_lanes(ctx), &launches,
+                           ctx->timing ? &ev : nullptr, err);
   if (ctx->timing) {
     // per phase: diagonal inverses, M, one entry per depth of Z blocks, query pass
     cudaStreamSynchronize(st);

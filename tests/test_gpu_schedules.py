@@ -1,5 +1,5 @@
-"""The factorization's and the selected inversion's concurrent schedules against the
-one-stream schedule (peers_options.one_stream).  The lanes run independent subtrees on
+"""The factorization's, the selected inversion's and the block inverse's concurrent
+schedules against the one-stream schedule (peers_options.one_stream).  The lanes run independent subtrees on
 their own streams. A factorization column block of more than one block runs its update
 split over three streams: the next block's columns on a high-priority chain, the panel's
 other columns, and the update matrix. Every entry still takes its updates in the same

@@ -256,6 +256,37 @@ __global__ void __launch_bounds__(kBlock * kPanelSplit) k_panel_rows(const int32
 // TS = 32); kTrailPanelRest, the panel's columns after block J + 1 (the tiles of that column
 // range that reach the diagonal or below it); kTrailU, the update matrix's triangle.
 constexpr int kTrailAll = 0, kTrailNext = 1, kTrailPanelRest = 2, kTrailU = 3;
+
+// acc[u][v] += sum_k Li[k][tx + 16u] Lj[k][ty + 16v] over the rows u < NU (and, for a tile on
+// the diagonal, v <= u); NU and DIAG are compile-time so that no multiply-add is issued for a
+// skipped sub-block.
+template <int TS, int NU, bool DIAG>
+__device__ __forceinline__ void trail_fma_n(const double (*Li)[TS], const double (*Lj)[TS],
+                                            int bw, int tx, int ty, double (*acc)[TS / 16]) {
+  constexpr int U = TS / 16;
+  for (int k = 0; k < bw; ++k) {
+    double li[U], lj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      li[u] = u < NU ? Li[k][tx + 16 * u] : 0.0;
+      lj[u] = Lj[k][ty + 16 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u)
+#pragma unroll
+      for (int v = 0; v < (DIAG ? u + 1 : U); ++v) acc[u][v] = fma(li[u], lj[v], acc[u][v]);
+  }
+}
+template <int TS, bool DIAG>
+__device__ __forceinline__ void trail_fma(const double (*Li)[TS], const double (*Lj)[TS], int bw,
+                                          int nu, int tx, int ty, double (*acc)[TS / 16]) {
+  if (TS == 64 && nu == 1) trail_fma_n<TS, 1, DIAG>(Li, Lj, bw, tx, ty, acc);
+  else if (TS == 64 && nu == 2) trail_fma_n<TS, 2, DIAG>(Li, Lj, bw, tx, ty, acc);
+  else if (TS == 64 && nu == 3) trail_fma_n<TS, 3, DIAG>(Li, Lj, bw, tx, ty, acc);
+  else if (TS == 32 && nu == 1) trail_fma_n<TS, 1, DIAG>(Li, Lj, bw, tx, ty, acc);
+  else trail_fma_n<TS, TS / 16, DIAG>(Li, Lj, bw, tx, ty, acc);
+}
+
 template <int TS, int MODE>
 __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sns, int32_t J,
                                                   const int64_t *__restrict__ prefix, int32_t na,
@@ -308,15 +339,14 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   double acc[U][U] = {};
-  for (int k = 0; k < bw; ++k) {
-    double li[U], lj[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) { li[u] = Li[k][tx + 16 * u]; lj[u] = Lj[k][ty + 16 * u]; }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int v = 0; v < U; ++v) acc[u][v] = fma(li[u], lj[v], acc[u][v]);
-  }
+  // sub-blocks of 16 x 16 outputs that no write keeps get no multiply-adds: on a tile of the
+  // diagonal those with u < v (wholly above it), and on the last row of tiles those whose 16
+  // rows all lie at or beyond N
+  const int nu = min(U, (N - R0 + 15) / 16);
+  if (R0 == C0)
+    trail_fma<TS, true>(Li, Lj, bw, nu, tx, ty, acc);
+  else
+    trail_fma<TS, false>(Li, Lj, bw, nu, tx, ty, acc);
   double *Pw = a.panel + a.panel_off[s];
   double *Uw = a.U + a.u_off[s];
 #pragma unroll

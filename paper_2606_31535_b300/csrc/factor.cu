@@ -257,10 +257,10 @@ __global__ void __launch_bounds__(kBlock * kPanelSplit) k_panel_rows(const int32
 // range that reach the diagonal or below it); kTrailU, the update matrix's triangle.
 constexpr int kTrailAll = 0, kTrailNext = 1, kTrailPanelRest = 2, kTrailU = 3;
 
-// acc[u][v] += sum_k Li[k][tx + 16u] Lj[k][ty + 16v] over the rows u < NU (and, for a tile on
-// the diagonal, v <= u); NU and DIAG are compile-time so that no multiply-add is issued for a
-// skipped sub-block.
-template <int TS, int NU, bool DIAG>
+// acc[u][v] += sum_k Li[k][tx + 16u] Lj[k][ty + 16v] over the sub-blocks u < NU, v < NV
+// (and, for a tile on the diagonal, v <= u); NU, NV and DIAG are compile-time so that no
+// multiply-add is issued for a skipped sub-block.
+template <int TS, int NU, int NV, bool DIAG>
 __device__ __forceinline__ void trail_fma_n(const double (*Li)[TS], const double (*Lj)[TS],
                                             int bw, int tx, int ty, double (*acc)[TS / 16]) {
   constexpr int U = TS / 16;
@@ -269,23 +269,34 @@ __device__ __forceinline__ void trail_fma_n(const double (*Li)[TS], const double
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       li[u] = u < NU ? Li[k][tx + 16 * u] : 0.0;
-      lj[u] = Lj[k][ty + 16 * u];
+      lj[u] = u < NV ? Lj[k][ty + 16 * u] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < NU; ++u)
 #pragma unroll
-      for (int v = 0; v < (DIAG ? u + 1 : U); ++v) acc[u][v] = fma(li[u], lj[v], acc[u][v]);
+      for (int v = 0; v < (DIAG ? (u + 1 < NV ? u + 1 : NV) : NV); ++v)
+        acc[u][v] = fma(li[u], lj[v], acc[u][v]);
   }
 }
+#define PEERS_TRAIL_FMA(NU_, NV_)                                              \
+  if (nu == NU_ && nv == NV_) {                                                \
+    trail_fma_n<TS, NU_, NV_, DIAG>(Li, Lj, bw, tx, ty, acc);                  \
+    return;                                                                    \
+  }
 template <int TS, bool DIAG>
 __device__ __forceinline__ void trail_fma(const double (*Li)[TS], const double (*Lj)[TS], int bw,
-                                          int nu, int tx, int ty, double (*acc)[TS / 16]) {
-  if (TS == 64 && nu == 1) trail_fma_n<TS, 1, DIAG>(Li, Lj, bw, tx, ty, acc);
-  else if (TS == 64 && nu == 2) trail_fma_n<TS, 2, DIAG>(Li, Lj, bw, tx, ty, acc);
-  else if (TS == 64 && nu == 3) trail_fma_n<TS, 3, DIAG>(Li, Lj, bw, tx, ty, acc);
-  else if (TS == 32 && nu == 1) trail_fma_n<TS, 1, DIAG>(Li, Lj, bw, tx, ty, acc);
-  else trail_fma_n<TS, TS / 16, DIAG>(Li, Lj, bw, tx, ty, acc);
+                                          int nu, int nv, int tx, int ty, double (*acc)[TS / 16]) {
+  if (TS == 32) {
+    PEERS_TRAIL_FMA(1, 1) PEERS_TRAIL_FMA(1, 2) PEERS_TRAIL_FMA(2, 1)
+  } else {
+    PEERS_TRAIL_FMA(1, 1) PEERS_TRAIL_FMA(1, 2) PEERS_TRAIL_FMA(1, 3) PEERS_TRAIL_FMA(1, 4)
+    PEERS_TRAIL_FMA(2, 1) PEERS_TRAIL_FMA(2, 2) PEERS_TRAIL_FMA(2, 3) PEERS_TRAIL_FMA(2, 4)
+    PEERS_TRAIL_FMA(3, 1) PEERS_TRAIL_FMA(3, 2) PEERS_TRAIL_FMA(3, 3) PEERS_TRAIL_FMA(3, 4)
+    PEERS_TRAIL_FMA(4, 1) PEERS_TRAIL_FMA(4, 2) PEERS_TRAIL_FMA(4, 3)
+  }
+  trail_fma_n<TS, TS / 16, TS / 16, DIAG>(Li, Lj, bw, tx, ty, acc);
 }
+#undef PEERS_TRAIL_FMA
 
 template <int TS, int MODE>
 __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sns, int32_t J,
@@ -340,13 +351,14 @@ __global__ void __launch_bounds__(256) k_trailing(const int32_t *__restrict__ sn
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   double acc[U][U] = {};
   // sub-blocks of 16 x 16 outputs that no write keeps get no multiply-adds: on a tile of the
-  // diagonal those with u < v (wholly above it), and on the last row of tiles those whose 16
-  // rows all lie at or beyond N
-  const int nu = min(U, (N - R0 + 15) / 16);
+  // diagonal those with u < v (wholly above it), on the last row of tiles those whose 16 rows
+  // all lie at or beyond N, on the last column of tiles those whose 16 columns all lie at or
+  // beyond the part's column limit
+  const int nu = min(U, (N - R0 + 15) / 16), nv = min(U, (clim - C0 + 15) / 16);
   if (R0 == C0)
-    trail_fma<TS, true>(Li, Lj, bw, nu, tx, ty, acc);
+    trail_fma<TS, true>(Li, Lj, bw, nu, nv, tx, ty, acc);
   else
-    trail_fma<TS, false>(Li, Lj, bw, nu, tx, ty, acc);
+    trail_fma<TS, false>(Li, Lj, bw, nu, nv, tx, ty, acc);
   double *Pw = a.panel + a.panel_off[s];
   double *Uw = a.U + a.u_off[s];
 #pragma unroll

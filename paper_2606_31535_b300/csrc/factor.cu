@@ -462,13 +462,14 @@ __global__ void __launch_bounds__(256) k_factor_small(const int32_t *__restrict_
   __syncthreads();
   // trailing update of the update matrix: F[i, j] -= sum_k L[i, k] (L[j, k] d_k) (k_trailing)
   double *Uw = a.U + a.u_off[s];
-  for (int idx = tid; idx < nbv * nbv; idx += blockDim.x) {
-    const int jj = idx / nbv, ii = idx - jj * nbv;
-    if (ii < jj) continue;
+  // the lower triangle (ii >= jj) only, dealt to the threads entry by entry
+  for (int e = tid; e < nbv * (nbv + 1) / 2; e += blockDim.x) {
+    int ii, jj;
+    tri_entry(e, ii, jj);
     const int i = nc + ii, j = nc + jj;
     double acc = 0.0;
     for (int k = 0; k < bw; ++k) acc = fma(F[k * N + i], F[k * N + j] * dk[k], acc);
-    Uw[idx] = F[j * N + i] - acc;
+    Uw[int64_t(jj) * nbv + ii] = F[j * N + i] - acc;
   }
 }
 

@@ -286,7 +286,7 @@ __device__ __forceinline__ void trail_fma_n(const double (*Li)[TS], const double
 template <int TS, bool DIAG>
 __device__ __forceinline__ void trail_fma(const double (*Li)[TS], const double (*Lj)[TS], int bw,
                                           int nu, int nv, int tx, int ty, double (*acc)[TS / 16]) {
-  if (TS == 32) {
+  if constexpr (TS == 32) {
     PEERS_TRAIL_FMA(1, 1) PEERS_TRAIL_FMA(1, 2) PEERS_TRAIL_FMA(2, 1)
   } else {
     PEERS_TRAIL_FMA(1, 1) PEERS_TRAIL_FMA(1, 2) PEERS_TRAIL_FMA(1, 3) PEERS_TRAIL_FMA(1, 4)

@@ -11,10 +11,12 @@
 //     supernode where its etree path starts.
 // Everything here is integer work on the CPU; no device is touched.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "internal.h"
 
@@ -329,15 +331,21 @@ int32_t sweep_tile(const Symbolic &S, int64_t N, int32_t cap) {
 
 namespace {
 
-// Orders the items [b, end) of a wave's level l (sorted by cost) with the spilled ones first
+// Host threads for building a large plan's sweep levels (at most kPlanThreads).
+constexpr int kPlanThreads = 8;
+int plan_threads() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  return static_cast<int>(std::max(1u, std::min<unsigned>(hw, kPlanThreads)));
+}
+
+// Orders the items [b, e) of a wave's level l (sorted by cost) with the spilled ones first
 // and records the level's launch shapes: shared memory of the regular launch, and the count
 // and shared memory of the spilled items' launch.
-void finish_level(const Symbolic &S, SweepWave &W, int32_t l, size_t b) {
-  std::stable_partition(W.items.begin() + b, W.items.end(),
-                        [](const SweepItem &it) { return it.spill != 0; });
+void finish_level(const Symbolic &S, SweepWave &W, int32_t l, SweepItem *b, SweepItem *e) {
+  std::stable_partition(b, e, [](const SweepItem &it) { return it.spill != 0; });
   int64_t smem = 0, nspill = 0, spill_smem = 0;
-  for (size_t k = b; k < W.items.size(); ++k) {
-    const SweepItem &it = W.items[k];
+  for (const SweepItem *pi = b; pi != e; ++pi) {
+    const SweepItem &it = *pi;
     if (it.spill) {
       ++nspill;
       spill_smem = std::max(spill_smem, int64_t(2) * kBlock * sweep_qstride(it.nq) * 8);
@@ -391,14 +399,24 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
   S.walk_entries = 0;
   S.walk_fma = 0;
   S.front_bytes = 0;
-  auto item_fma = [&](int32_t s, int32_t j0) -> int64_t {
+  // the FMAs of one query's item at supernode s from column block j0 / kBlock on: suffix sums
+  // over the supernode's blocks, so that an item's count is one lookup
+  std::vector<int64_t> fma_off(static_cast<size_t>(ns) + 1, 0);
+  for (int32_t s = 0; s < ns; ++s)
+    fma_off[s + 1] = fma_off[s] + (sn_nc(S, s) + kBlock - 1) / kBlock + 1;
+  std::vector<int64_t> fma_suf(static_cast<size_t>(fma_off[ns]), 0);
+  for (int32_t s = 0; s < ns; ++s) {
     const int64_t nc = sn_nc(S, s), N = nc + S.nb[s];
-    int64_t f = 0;
-    for (int64_t J = j0; J < nc; J += kBlock) {
-      const int64_t bw = std::min<int64_t>(kBlock, nc - J);
-      f += bw * (bw - 1) / 2 + (N - J - bw) * bw + bw;
+    const int64_t nbk = fma_off[s + 1] - fma_off[s] - 1;
+    for (int64_t jb = nbk - 1; jb >= 0; --jb) {
+      const int64_t J = jb * kBlock, bw = std::min<int64_t>(kBlock, nc - J);
+      fma_suf[fma_off[s] + jb] = bw * (bw - 1) / 2 + (N - J - bw) * bw + bw +
+                                 fma_suf[fma_off[s] + jb + 1];
     }
-    return f;
+  }
+  auto item_fma = [&](int32_t s, int32_t j0) -> int64_t {
+    const int64_t jb = j0 / kBlock, nbk = fma_off[s + 1] - fma_off[s] - 1;
+    return jb >= nbk ? 0 : fma_suf[fma_off[s] + jb];
   };
   auto entries = [&](int32_t s, int64_t first_col) -> int64_t {
     const int64_t np = sn_nc(S, s) - first_col;
@@ -414,9 +432,18 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
     W.level_smem.assign(static_cast<size_t>(S.nlevels), 0);
     W.level_nspill.assign(static_cast<size_t>(S.nlevels), 0);
     W.level_spill_smem.assign(static_cast<size_t>(S.nlevels), 0);
-    std::vector<std::pair<int64_t, SweepItem>> lv;
-    for (int32_t l = 0; l < S.nlevels; ++l) {
-      lv.clear();
+    // Levels are independent: each builds its items, ordered by cost (largest first; ties in
+    // the order they are made), and its share of the walk counts, on up to kPlanThreads
+    // host threads; they are joined in level order, so the plan is the same as one thread's.
+    struct LevelOut {
+      std::vector<SweepItem> items;
+      int64_t walk_entries = 0, walk_fma = 0, front_bytes = 0;
+    };
+    std::vector<LevelOut> outs(static_cast<size_t>(S.nlevels));
+    auto build_level = [&](int32_t l) {
+      LevelOut &o = outs[l];
+      std::vector<int64_t> keys;
+      std::vector<SweepItem> made;
       for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
         const int32_t p = S.level_sn[i];
         const int32_t tile = S.qtile[p];
@@ -433,17 +460,18 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
             int32_t j0;
             if (src >= 0) {
               j0 = S.rmap[S.rows_off[src]];
-              S.walk_entries += it.nq * entries(p, j0);
+              o.walk_entries += it.nq * entries(p, j0);
             } else {
               j0 = S.qa[q];
-              for (int64_t k = q; k < q + it.nq; ++k) S.walk_entries += entries(p, S.qa[k]);
+              for (int64_t k = q; k < q + it.nq; ++k) o.walk_entries += entries(p, S.qa[k]);
             }
             it.j0 = (j0 / kBlock) * kBlock;
             const int64_t f = it.nq * item_fma(p, it.j0);
-            S.walk_fma += f;
+            o.walk_fma += f;
             // fronts carried between levels: read from the child's carry, written for the parent
-            S.front_bytes += int64_t(8) * it.nq * ((src >= 0 ? S.nb[src] : 0) + S.nb[p]);
-            lv.push_back({f, it});
+            o.front_bytes += int64_t(8) * it.nq * ((src >= 0 ? S.nb[src] : 0) + S.nb[p]);
+            keys.push_back(f);
+            made.push_back(it);
           }
         };
         for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
@@ -452,11 +480,37 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
         }
         emit(-1, S.qbeg[p], S.qbeg[p + 1]);
       }
-      std::stable_sort(lv.begin(), lv.end(),
-                       [](const auto &x, const auto &y) { return x.first > y.first; });
-      const size_t b = W.items.size();
-      for (auto &x : lv) W.items.push_back(x.second);
-      finish_level(S, W, l, b);
+      std::vector<int32_t> order(made.size());
+      std::iota(order.begin(), order.end(), 0);
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int32_t x, int32_t y) { return keys[x] > keys[y]; });
+      o.items.reserve(made.size());
+      for (int32_t x : order) o.items.push_back(made[x]);
+      finish_level(S, W, l, o.items.data(), o.items.data() + o.items.size());
+    };
+    const int64_t wave_queries = W.q_end - W.q_begin;
+    const int nthreads = wave_queries >= (int64_t(1) << 16) ? plan_threads() : 1;
+    if (nthreads <= 1) {
+      for (int32_t l = 0; l < S.nlevels; ++l) build_level(l);
+    } else {
+      std::atomic<int32_t> next{0};
+      std::vector<std::thread> pool;
+      for (int t = 0; t < nthreads; ++t)
+        pool.emplace_back([&]() {
+          for (int32_t l = next++; l < S.nlevels; l = next++) build_level(l);
+        });
+      for (std::thread &th : pool) th.join();
+    }
+    size_t total = 0;
+    for (const LevelOut &o : outs) total += o.items.size();
+    W.items.reserve(total);
+    for (int32_t l = 0; l < S.nlevels; ++l) {
+      LevelOut &o = outs[l];
+      W.items.insert(W.items.end(), o.items.begin(), o.items.end());
+      S.walk_entries += o.walk_entries;
+      S.walk_fma += o.walk_fma;
+      S.front_bytes += o.front_bytes;
+      std::vector<SweepItem>().swap(o.items);
       W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
     }
     S.waves.push_back(std::move(W));
@@ -571,7 +625,7 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
           }
           i = e;
         }
-        finish_level(S, W, l, lb);
+        finish_level(S, W, l, W.items.data() + lb, W.items.data() + W.items.size());
         W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
       }
       S.waves.push_back(std::move(W));
@@ -1114,12 +1168,25 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     recs.push_back({s0, lo - f, b, i});
   }
   S.nq_two = static_cast<int64_t>(twos.size());
-  std::sort(recs.begin(), recs.end(), [](const Rec &x, const Rec &y) {
-    if (x.s0 != y.s0) return x.s0 < y.s0;
-    if (x.a != y.a) return x.a < y.a;
-    if (x.b != y.b) return x.b < y.b;
-    return x.idx < y.idx;
-  });
+  // ordered by (start supernode, a, b, query index): a counting pass groups the records by
+  // start supernode, then each group is sorted on its own (the order is total, so this is the
+  // order one sort of all records gives)
+  {
+    std::vector<int64_t> at(static_cast<size_t>(ns) + 1, 0);
+    for (const Rec &r : recs) at[r.s0 + 1]++;
+    for (int32_t s = 0; s < ns; ++s) at[s + 1] += at[s];
+    std::vector<Rec> grouped(recs.size());
+    std::vector<int64_t> fill(at.begin(), at.end() - 1);
+    for (const Rec &r : recs) grouped[fill[r.s0]++] = r;
+    for (int32_t s = 0; s < ns; ++s)
+      std::sort(grouped.begin() + at[s], grouped.begin() + at[s + 1],
+                [](const Rec &x, const Rec &y) {
+                  if (x.a != y.a) return x.a < y.a;
+                  if (x.b != y.b) return x.b < y.b;
+                  return x.idx < y.idx;
+                });
+    recs.swap(grouped);
+  }
   S.nsorted = static_cast<int64_t>(recs.size());
   const int64_t nslots = S.nsorted + 2 * S.nq_two;
   S.qorig.resize(static_cast<size_t>(nslots));

@@ -713,21 +713,50 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   S.t_order = since(t0);
   auto t1 = Clock::now();
 
-  // ---- column counts (strictly lower) by row-subtree traversal ----
+  // ---- column counts (strictly lower) from the leaves of the row subtrees (Gilbert, Ng and
+  //      Peyton).  Column j of L holds row i > j exactly when j lies in the row subtree of i,
+  //      the union of the etree paths from row i's entries up to i.  The numbering is an etree
+  //      postorder, so the subtree of j is the index range [fdesc[j], j].  Marks +1 at each
+  //      leaf of a row subtree, -1 at the lowest common ancestor of consecutive leaves (found
+  //      by path-compressed union-find over the finished subtrees) and -1 at the parent of
+  //      every non-root make each column's count (with its diagonal) the sum of the marks over
+  //      its subtree. ----
   std::vector<int64_t> cc(static_cast<size_t>(nr), 0);
   std::vector<int32_t> nchild(static_cast<size_t>(nr), 0);
   {
-    std::vector<int32_t> mark(static_cast<size_t>(nr), -1);
-    for (int64_t i = 0; i < nr; ++i) {
-      mark[i] = static_cast<int32_t>(i);
-      const int32_t v = perm[i];
-      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
-        int32_t j = iperm[A.idx[p]];
-        if (j >= i) continue;
-        while (mark[j] != i) { cc[j]++; mark[j] = static_cast<int32_t>(i); j = par[j]; }
-      }
-      if (par[i] != -1) nchild[par[i]]++;
+    std::vector<int32_t> fdesc(static_cast<size_t>(nr), -1);
+    for (int64_t k = 0; k < nr; ++k) {
+      cc[k] = fdesc[k] == -1 ? 1 : 0;   // an etree leaf starts with its own diagonal
+      for (int32_t j = static_cast<int32_t>(k); j != -1 && fdesc[j] == -1; j = par[j])
+        fdesc[j] = static_cast<int32_t>(k);
     }
+    std::vector<int32_t> anc(static_cast<size_t>(nr)), maxfirst(static_cast<size_t>(nr), -1),
+        prevleaf(static_cast<size_t>(nr), -1);
+    std::iota(anc.begin(), anc.end(), 0);
+    auto find = [&](int32_t x) {
+      int32_t r = x;
+      while (anc[r] != r) r = anc[r];
+      while (anc[x] != r) { const int32_t nx = anc[x]; anc[x] = r; x = nx; }
+      return r;
+    };
+    for (int64_t k = 0; k < nr; ++k) {
+      const int32_t j = static_cast<int32_t>(k);
+      if (par[j] != -1) { cc[par[j]]--; nchild[par[j]]++; }
+      const int32_t v = perm[j];
+      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+        const int32_t i = iperm[A.idx[p]];
+        if (i <= j || fdesc[j] <= maxfirst[i]) continue;   // j is not a new leaf of row i's tree
+        maxfirst[i] = fdesc[j];
+        const int32_t jprev = prevleaf[i];
+        prevleaf[i] = j;
+        cc[j]++;
+        if (jprev != -1) cc[find(jprev)]--;
+      }
+      if (par[j] != -1) anc[j] = par[j];
+    }
+    for (int64_t k = 0; k < nr; ++k)
+      if (par[k] != -1) cc[par[k]] += cc[k];
+    for (int64_t k = 0; k < nr; ++k) cc[k] -= 1;
   }
 
   // ---- fundamental supernodes ----

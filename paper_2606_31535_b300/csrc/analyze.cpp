@@ -775,41 +775,9 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     int32_t last = ffirst[s + 1] - 1;
     fparent[s] = par[last] == -1 ? -1 : fcol2sn[par[last]];
   }
-  // row structure B_s of the fundamental supernodes, bottom-up
-  std::vector<int64_t> frows_off(static_cast<size_t>(nf) + 1, 0);
-  std::vector<int32_t> frows;
-  {
-    std::vector<int32_t> fhead(static_cast<size_t>(nf), -1), fnext(static_cast<size_t>(nf), -1);
-    for (int32_t s = nf - 1; s >= 0; --s)
-      if (fparent[s] != -1) { fnext[s] = fhead[fparent[s]]; fhead[fparent[s]] = s; }
-    std::vector<int32_t> mk(static_cast<size_t>(nr), -1), buf;
-    int64_t total = 0;
-    for (int32_t s = 0; s < nf; ++s) total += cc[ffirst[s + 1] - 1];
-    frows.reserve(static_cast<size_t>(total));
-    for (int32_t s = 0; s < nf; ++s) {
-      const int32_t last = ffirst[s + 1] - 1;
-      buf.clear();
-      for (int32_t k = ffirst[s]; k <= last; ++k) {
-        const int32_t v = perm[k];
-        for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
-          int32_t i = iperm[A.idx[p]];
-          if (i > last && mk[i] != s) { mk[i] = s; buf.push_back(i); }
-        }
-      }
-      for (int32_t c = fhead[s]; c != -1; c = fnext[c])
-        for (int64_t p = frows_off[c]; p < frows_off[c + 1]; ++p) {
-          int32_t i = frows[p];
-          if (i > last && mk[i] != s) { mk[i] = s; buf.push_back(i); }
-        }
-      std::sort(buf.begin(), buf.end());
-      if (static_cast<int64_t>(buf.size()) != cc[last]) {
-        err = "internal: supernode structure disagrees with the column counts";
-        return PEERS_EINVAL;
-      }
-      frows.insert(frows.end(), buf.begin(), buf.end());
-      frows_off[s + 1] = static_cast<int64_t>(frows.size());
-    }
-  }
+  // |B_s| of a fundamental supernode: the column count of its last column
+  std::vector<int64_t> fnb(static_cast<size_t>(nf));
+  for (int32_t s = 0; s < nf; ++s) fnb[s] = cc[ffirst[s + 1] - 1];
 
   // ---- relaxed amalgamation: a supernode whose columns end right before its parent's
   //      (its parent's last child) joins the parent when the merge is small or adds few
@@ -825,7 +793,7 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     const int32_t p = fparent[s];
     if (p == -1 || cfirst[s] + ncols[s] != cfirst[p]) continue;
     const int64_t a = ncols[s], b = ncols[p];
-    const int64_t nbs = frows_off[s + 1] - frows_off[s], nbp = frows_off[p + 1] - frows_off[p];
+    const int64_t nbs = fnb[s], nbp = fnb[p];
     const int64_t em = tri(a + b) + (a + b) * nbp;
     const int64_t zm = zeros[s] + zeros[p] + a * (b + nbp - nbs);
     if (a + b <= relax_small || (a + b <= relax_max && zm <= relax_frac * em)) {
@@ -852,33 +820,44 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     int32_t p = fparent[s];
     while (p != -1 && into[p] != -1) p = into[p];
     S.parent[f] = p == -1 ? -1 : fin[p];
-    S.nb[f] = static_cast<int32_t>(frows_off[s + 1] - frows_off[s]);
-    S.rows.insert(S.rows.end(), frows.begin() + frows_off[s], frows.begin() + frows_off[s + 1]);
-    S.rows_off[f + 1] = static_cast<int64_t>(S.rows.size());
+    S.nb[f] = static_cast<int32_t>(fnb[s]);
+    S.rows_off[f + 1] = S.rows_off[f] + fnb[s];
   }
   S.first[ns] = static_cast<int32_t>(nr);
   S.col2sn.assign(static_cast<size_t>(nr), 0);
   for (int32_t s = 0; s < ns; ++s)
     for (int32_t k = S.first[s]; k < S.first[s + 1]; ++k) S.col2sn[k] = s;
-  S.perm = perm;
-  S.iperm = iperm;
-
-  // relative maps into the parent front: rows of s (C_s then B_s) -> local index in parent
-  S.rmap.assign(S.rows.size(), -1);
-  for (int32_t s = 0; s < ns; ++s) {
-    const int32_t p = S.parent[s];
-    if (p == -1) continue;
-    const int32_t pf = S.first[p], pnc = sn_nc(S, p);
-    auto pb = S.rows.begin() + S.rows_off[p], pe = S.rows.begin() + S.rows_off[p + 1];
-    for (int64_t t = S.rows_off[s]; t < S.rows_off[s + 1]; ++t) {
-      const int32_t r = S.rows[t];
-      if (r < pf) { err = "internal: row below the parent's first column"; return PEERS_EINVAL; }
-      if (r < pf + pnc) { S.rmap[t] = r - pf; continue; }
-      auto it = std::lower_bound(pb, pe, r);
-      if (it == pe || *it != r) { err = "internal: child row missing from parent"; return PEERS_EINVAL; }
-      S.rmap[t] = pnc + static_cast<int32_t>(it - pb);
+  // row structure B_s (rows past s's last column).  Row i belongs to B_s exactly when s lies
+  // on the supernodal etree path from the supernode of one of row i's entries j < i up to
+  // (not including) the supernode of i; rows are visited in increasing order, so each B_s
+  // fills sorted, into the slot its column count sized.
+  {
+    S.rows.assign(static_cast<size_t>(S.rows_off[ns]), 0);
+    std::vector<int64_t> fill(S.rows_off.begin(), S.rows_off.end() - 1);
+    std::vector<int32_t> mk(static_cast<size_t>(ns), -1);
+    bool ok = true;
+    for (int64_t ii = 0; ii < nr && ok; ++ii) {
+      const int32_t i = static_cast<int32_t>(ii);
+      mk[S.col2sn[i]] = i;
+      const int32_t v = perm[i];
+      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+        const int32_t j = iperm[A.idx[p]];
+        if (j >= i) continue;
+        for (int32_t t = S.col2sn[j]; t != -1 && mk[t] != i; t = S.parent[t]) {
+          if (fill[t] == S.rows_off[t + 1]) { ok = false; break; }
+          mk[t] = i;
+          S.rows[fill[t]++] = i;
+        }
+      }
+    }
+    for (int32_t t = 0; t < ns && ok; ++t) ok = fill[t] == S.rows_off[t + 1];
+    if (!ok) {
+      err = "internal: supernode structure disagrees with the column counts";
+      return PEERS_EINVAL;
     }
   }
+  S.perm = perm;
+  S.iperm = iperm;
 
   // children, subtree starts, levels (height above the leaves)
   S.child_ptr.assign(static_cast<size_t>(ns) + 1, 0);
@@ -915,6 +894,31 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
                        [&](int32_t a, int32_t b) { return sn_nc(S, a) > sn_nc(S, b); });
   }
 
+  // relative maps into the parent front: rows of s (C_s then B_s) -> local index in parent.
+  // Each parent's rows are scattered once into a table indexed by row, for all its children.
+  S.rmap.assign(S.rows.size(), -1);
+  {
+    std::vector<int32_t> where(static_cast<size_t>(nr), -1), owner(static_cast<size_t>(nr), -1);
+    for (int32_t p = 0; p < ns; ++p) {
+      if (S.child_ptr[p] == S.child_ptr[p + 1]) continue;
+      const int32_t pf = S.first[p], pnc = sn_nc(S, p);
+      for (int64_t t = S.rows_off[p]; t < S.rows_off[p + 1]; ++t) {
+        where[S.rows[t]] = pnc + static_cast<int32_t>(t - S.rows_off[p]);
+        owner[S.rows[t]] = p;
+      }
+      for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
+        const int32_t ch = S.child_list[c];
+        for (int64_t t = S.rows_off[ch]; t < S.rows_off[ch + 1]; ++t) {
+          const int32_t r = S.rows[t];
+          if (r < pf) { err = "internal: row below the parent's first column"; return PEERS_EINVAL; }
+          if (r < pf + pnc) { S.rmap[t] = r - pf; continue; }
+          if (owner[r] != p) { err = "internal: child row missing from parent"; return PEERS_EINVAL; }
+          S.rmap[t] = where[r];
+        }
+      }
+    }
+  }
+
   // ---- device layout ----
   S.panel_off.assign(static_cast<size_t>(ns) + 1, 0);
   S.tinv_off.assign(static_cast<size_t>(ns) + 1, 0);
@@ -947,6 +951,8 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     };
     S.a_dest.clear();
     S.a_src.clear();
+    S.a_dest.reserve(static_cast<size_t>(indptr[n] / 2 + nr));
+    S.a_src.reserve(static_cast<size_t>(indptr[n] / 2));
     for (int64_t gi = 0; gi < n; ++gi) {
       if (gi == ground) continue;
       const int32_t i = iperm[gi > ground ? gi - 1 : gi];

@@ -338,6 +338,18 @@ int plan_threads() {
   return static_cast<int>(std::max(1u, std::min<unsigned>(hw, kPlanThreads)));
 }
 
+// Runs f(0) .. f(nthreads - 1), each on a host thread of its own (inline for one).
+template <class F>
+void run_threads(int nthreads, F &&f) {
+  if (nthreads <= 1) {
+    f(0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back([&f, t]() { f(t); });
+  for (std::thread &th : pool) th.join();
+}
+
 // Orders the items [b, e) of a wave's level l (sorted by cost) with the spilled ones first
 // and records the level's launch shapes: shared memory of the regular launch, and the count
 // and shared memory of the spilled items' launch.
@@ -433,13 +445,33 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
     W.level_nspill.assign(static_cast<size_t>(S.nlevels), 0);
     W.level_spill_smem.assign(static_cast<size_t>(S.nlevels), 0);
     // Levels are independent: each builds its items, ordered by cost (largest first; ties in
-    // the order they are made), and its share of the walk counts, on up to kPlanThreads
-    // host threads; they are joined in level order, so the plan is the same as one thread's.
+    // the order they are made), into its own range of the wave's items (sized by a counting
+    // pass), and its share of the walk counts, on up to kPlanThreads host threads; the counts
+    // are summed in level order, so the plan is the same as one thread's.
+    for (int32_t l = 0; l < S.nlevels; ++l) {
+      int64_t cnt = 0;
+      for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
+        const int32_t p = S.level_sn[i];
+        const int64_t tile = S.qtile[p];
+        auto tiles = [&](int64_t b, int64_t e) {
+          b = std::max(b, W.q_begin);
+          e = std::min(e, W.q_end);
+          return e > b ? (e - b + tile - 1) / tile : 0;
+        };
+        for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
+          const int32_t ch = S.child_list[c];
+          cnt += tiles(S.qbeg[S.fdesc[ch]], S.qbeg[ch + 1]);
+        }
+        cnt += tiles(S.qbeg[p], S.qbeg[p + 1]);
+      }
+      W.level_ptr[l + 1] = W.level_ptr[l] + cnt;
+    }
+    W.items.resize(static_cast<size_t>(W.level_ptr[S.nlevels]));
     struct LevelOut {
-      std::vector<SweepItem> items;
       int64_t walk_entries = 0, walk_fma = 0, front_bytes = 0;
     };
     std::vector<LevelOut> outs(static_cast<size_t>(S.nlevels));
+    std::atomic<bool> miscount{false};
     auto build_level = [&](int32_t l) {
       LevelOut &o = outs[l];
       std::vector<int64_t> keys;
@@ -484,9 +516,13 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
       std::iota(order.begin(), order.end(), 0);
       std::stable_sort(order.begin(), order.end(),
                        [&](int32_t x, int32_t y) { return keys[x] > keys[y]; });
-      o.items.reserve(made.size());
-      for (int32_t x : order) o.items.push_back(made[x]);
-      finish_level(S, W, l, o.items.data(), o.items.data() + o.items.size());
+      if (static_cast<int64_t>(made.size()) != W.level_ptr[l + 1] - W.level_ptr[l]) {
+        miscount = true;
+        return;
+      }
+      SweepItem *dst = W.items.data() + W.level_ptr[l];
+      for (int32_t x : order) *dst++ = made[x];
+      finish_level(S, W, l, W.items.data() + W.level_ptr[l], dst);
     };
     const int64_t wave_queries = W.q_end - W.q_begin;
     const int nthreads = wave_queries >= (int64_t(1) << 16) ? plan_threads() : 1;
@@ -501,17 +537,14 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
         });
       for (std::thread &th : pool) th.join();
     }
-    size_t total = 0;
-    for (const LevelOut &o : outs) total += o.items.size();
-    W.items.reserve(total);
-    for (int32_t l = 0; l < S.nlevels; ++l) {
-      LevelOut &o = outs[l];
-      W.items.insert(W.items.end(), o.items.begin(), o.items.end());
+    if (miscount) {
+      err = "internal: sweep items disagree with their count";
+      return PEERS_EINVAL;
+    }
+    for (const LevelOut &o : outs) {
       S.walk_entries += o.walk_entries;
       S.walk_fma += o.walk_fma;
       S.front_bytes += o.front_bytes;
-      std::vector<SweepItem>().swap(o.items);
-      W.level_ptr[l + 1] = static_cast<int64_t>(W.items.size());
     }
     S.waves.push_back(std::move(W));
     if (S.nsorted == 0) break;
@@ -1159,6 +1192,8 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   std::vector<int32_t> eu, ev;
   const int32_t *QU = qu, *QV = qv;
   if (nq < 0 || !qu || !qv) {
+    eu.reserve(static_cast<size_t>(indptr[n] / 2));
+    ev.reserve(static_cast<size_t>(indptr[n] / 2));
     for (int64_t u = 0; u < n; ++u)
       for (int64_t p = indptr[u]; p < indptr[u + 1]; ++p)
         if (indices[p] > u) { eu.push_back(static_cast<int32_t>(u)); ev.push_back(indices[p]); }
@@ -1169,72 +1204,106 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   S.nq = nq;
   struct Rec { int32_t s0, a, b; int64_t idx; };
   struct Two { int32_t lo, hi; int64_t idx; };
-  std::vector<Rec> recs;
-  std::vector<Two> twos;
-  recs.reserve(static_cast<size_t>(nq));
-  S.nq_trivial = 0;
-  S.nq_two = 0;
   auto pos = [&](int64_t u) -> int32_t {
     return u == ground ? -1 : iperm[u > ground ? u - 1 : u];
   };
-  for (int64_t i = 0; i < nq; ++i) {
-    const int64_t u = QU[i], v = QV[i];
-    if (u < 0 || u >= n || v < 0 || v >= n) { err = "query node out of range"; return PEERS_EINVAL; }
-    if (u == v) { S.nq_trivial++; continue; }
-    int32_t pu = pos(u), pv = pos(v), lo, hi;
-    if (pu < 0 || pv < 0) { lo = std::max(pu, pv); hi = -1; }
-    else { lo = std::min(pu, pv); hi = std::max(pu, pv); }
-    const int32_t s0 = S.col2sn[lo];
-    const int32_t f = S.first[s0], nc = sn_nc(S, s0);
-    int32_t b = -1;
-    if (hi >= 0) {
-      if (hi < f + nc) {
-        b = hi - f;
-      } else {
-        auto rb = S.rows.begin() + S.rows_off[s0], re = S.rows.begin() + S.rows_off[s0 + 1];
-        auto it = std::lower_bound(rb, re, hi);
-        if (it == re || *it != hi) {   // paths meet above s0: two-branch walk
-          twos.push_back({lo, hi, i});
-          continue;
+  // Queries are mapped in contiguous chunks, one per host thread; each chunk keeps its records
+  // in query order and counts them per start supernode.
+  struct Chunk {
+    std::vector<Rec> recs;
+    std::vector<Two> twos;
+    std::vector<int64_t> at;   // per start supernode: its count, then its first output slot
+    int64_t trivial = 0;
+    bool bad = false;
+  };
+  const int nchunks = nq >= (int64_t(1) << 16) ? plan_threads() : 1;
+  std::vector<Chunk> chunks(static_cast<size_t>(nchunks));
+  run_threads(nchunks, [&](int c) {
+    Chunk &C = chunks[c];
+    const int64_t i0 = nq * c / nchunks, i1 = nq * (c + 1) / nchunks;
+    C.recs.reserve(static_cast<size_t>(i1 - i0));
+    for (int64_t i = i0; i < i1; ++i) {
+      const int64_t u = QU[i], v = QV[i];
+      if (u < 0 || u >= n || v < 0 || v >= n) { C.bad = true; return; }
+      if (u == v) { C.trivial++; continue; }
+      int32_t pu = pos(u), pv = pos(v), lo, hi;
+      if (pu < 0 || pv < 0) { lo = std::max(pu, pv); hi = -1; }
+      else { lo = std::min(pu, pv); hi = std::max(pu, pv); }
+      const int32_t s0 = S.col2sn[lo];
+      const int32_t f = S.first[s0], nc = sn_nc(S, s0);
+      int32_t b = -1;
+      if (hi >= 0) {
+        if (hi < f + nc) {
+          b = hi - f;
+        } else {
+          auto rb = S.rows.begin() + S.rows_off[s0], re = S.rows.begin() + S.rows_off[s0 + 1];
+          auto it = std::lower_bound(rb, re, hi);
+          if (it == re || *it != hi) {   // paths meet above s0: two-branch walk
+            C.twos.push_back({lo, hi, i});
+            continue;
+          }
+          b = nc + static_cast<int32_t>(it - rb);
         }
-        b = nc + static_cast<int32_t>(it - rb);
       }
+      C.recs.push_back({s0, lo - f, b, i});
     }
-    recs.push_back({s0, lo - f, b, i});
+    C.at.assign(static_cast<size_t>(ns), 0);
+    for (const Rec &r : C.recs) C.at[r.s0]++;
+  });
+  S.nq_trivial = 0;
+  std::vector<Two> twos;
+  for (const Chunk &C : chunks) {
+    if (C.bad) { err = "query node out of range"; return PEERS_EINVAL; }
+    S.nq_trivial += C.trivial;
+    twos.insert(twos.end(), C.twos.begin(), C.twos.end());
   }
   S.nq_two = static_cast<int64_t>(twos.size());
-  // ordered by (start supernode, a, b, query index): a counting pass groups the records by
-  // start supernode, then each group is sorted on its own (the order is total, so this is the
-  // order one sort of all records gives)
-  {
-    std::vector<int64_t> at(static_cast<size_t>(ns) + 1, 0);
-    for (const Rec &r : recs) at[r.s0 + 1]++;
-    for (int32_t s = 0; s < ns; ++s) at[s + 1] += at[s];
-    std::vector<Rec> grouped(recs.size());
-    std::vector<int64_t> fill(at.begin(), at.end() - 1);
-    for (const Rec &r : recs) grouped[fill[r.s0]++] = r;
-    for (int32_t s = 0; s < ns; ++s)
-      std::sort(grouped.begin() + at[s], grouped.begin() + at[s + 1],
+  // ordered by (start supernode, a, b, query index): the chunks scatter their records into
+  // groups by start supernode, then each group is sorted on its own (the order is total, so
+  // this is the order one sort of all records gives)
+  S.qbeg.assign(static_cast<size_t>(ns) + 1, 0);
+  for (int32_t s = 0; s < ns; ++s) {
+    int64_t next = S.qbeg[s];
+    for (Chunk &C : chunks) {
+      const int64_t k = C.at[s];
+      C.at[s] = next;
+      next += k;
+    }
+    S.qbeg[s + 1] = next;
+  }
+  std::vector<Rec, NoInitAlloc<Rec>> recs(static_cast<size_t>(S.qbeg[ns]));
+  run_threads(nchunks, [&](int c) {
+    Chunk &C = chunks[c];
+    for (const Rec &r : C.recs) recs[C.at[r.s0]++] = r;
+    std::vector<Rec>().swap(C.recs);
+  });
+  run_threads(nchunks, [&](int c) {
+    // supernodes [s_begin, s_end) hold about a 1/nchunks share of the records
+    auto first_at = [&](int k) -> int32_t {
+      if (k == nchunks) return ns;
+      const int64_t goal = S.qbeg[ns] * k / nchunks;
+      return static_cast<int32_t>(std::lower_bound(S.qbeg.begin(), S.qbeg.end(), goal) -
+                                  S.qbeg.begin());
+    };
+    const int32_t s_begin = std::min(first_at(c), ns), s_end = std::min(first_at(c + 1), ns);
+    for (int32_t s = s_begin; s < s_end; ++s)
+      std::sort(recs.begin() + S.qbeg[s], recs.begin() + S.qbeg[s + 1],
                 [](const Rec &x, const Rec &y) {
                   if (x.a != y.a) return x.a < y.a;
                   if (x.b != y.b) return x.b < y.b;
                   return x.idx < y.idx;
                 });
-    recs.swap(grouped);
-  }
+  });
   S.nsorted = static_cast<int64_t>(recs.size());
   const int64_t nslots = S.nsorted + 2 * S.nq_two;
   S.qorig.resize(static_cast<size_t>(nslots));
   S.qa.resize(static_cast<size_t>(nslots));
   S.qb.resize(static_cast<size_t>(nslots));
-  S.qbeg.assign(static_cast<size_t>(ns) + 1, 0);
   for (size_t k = 0; k < recs.size(); ++k) {
     S.qorig[k] = recs[k].idx;
     S.qa[k] = recs[k].a;
     S.qb[k] = recs[k].b;
-    S.qbeg[recs[k].s0 + 1]++;
   }
-  for (int32_t s = 0; s < ns; ++s) S.qbeg[s + 1] += S.qbeg[s];
 
   S.two_lo.resize(twos.size());
   S.two_hi.resize(twos.size());

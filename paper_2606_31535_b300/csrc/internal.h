@@ -3,7 +3,10 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "peers.h"
@@ -97,6 +100,23 @@ struct SweepDesc {
 
 // One wave of the sweep: the queries [q_begin, q_end) of the sorted order, walked to the
 // root level by level.  items[level_ptr[l] .. level_ptr[l+1]) are the level's items.
+// Allocator whose value-initialising construct() default-initialises instead: a vector of
+// trivially constructible elements that is sized and then filled is not zeroed first.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind { using other = NoInitAlloc<U>; };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U> &) noexcept {}
+  template <class U>
+  void construct(U *p) noexcept { ::new (static_cast<void *>(p)) U; }
+  template <class U, class... Args>
+  void construct(U *p, Args &&...args) {
+    ::new (static_cast<void *>(p)) U(std::forward<Args>(args)...);
+  }
+};
+
 struct SweepWave {
   int64_t q_begin, q_end;
   int64_t two_begin = 0, two_end = 0;   // two-branch queries finished by this wave (combine)
@@ -105,7 +125,7 @@ struct SweepWave {
   // the first level_nspill[l] items of level l have spill == 1 and run in their own launch
   // (dynamic shared memory level_spill_smem[l])
   std::vector<int64_t> level_nspill, level_spill_smem;
-  std::vector<SweepItem> items;
+  std::vector<SweepItem, NoInitAlloc<SweepItem>> items;   // filled level by level once sized
 };
 
 struct Symbolic {

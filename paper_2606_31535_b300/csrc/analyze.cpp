@@ -15,6 +15,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <condition_variable>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -26,6 +28,25 @@ namespace {
 using Clock = std::chrono::steady_clock;
 double since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+// Host threads for the large analysis steps (at most kPlanThreads).
+constexpr int kPlanThreads = 8;
+int plan_threads() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  return static_cast<int>(std::max(1u, std::min<unsigned>(hw, kPlanThreads)));
+}
+
+// Runs f(0) .. f(nthreads - 1), each on a host thread of its own (inline for one).
+template <class F>
+void run_threads(int nthreads, F &&f) {
+  if (nthreads <= 1) {
+    f(0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back([&f, t]() { f(t); });
+  for (std::thread &th : pool) th.join();
 }
 
 // ------------------------------------------------------------------------- validation
@@ -127,21 +148,27 @@ Adj reduced_adjacency(int64_t n, const int64_t *indptr, const int32_t *indices, 
 struct NdTask { int64_t lo, hi; };
 
 // Coordinate bisection: split at the median of the widest axis; the separator is the set of
-// upper-side nodes with a lower-side neighbour.
+// upper-side nodes with a lower-side neighbour.  A task's split depends only on its own nodes,
+// so tasks run on up to kPlanThreads host threads with the same result as one: each task
+// stamps its nodes with its own id, and a neighbour counts as lower-side only under the id of
+// the task looking at it.
 void order_coordinate_nd(const Adj &A, const double *xy, int dim, int leaf,
                          std::vector<int32_t> &work) {
   const int64_t nr = static_cast<int64_t>(A.ptr.size()) - 1;
   work.resize(static_cast<size_t>(nr));
   std::iota(work.begin(), work.end(), 0);
   std::vector<int8_t> side(static_cast<size_t>(nr), -1);
-  std::vector<std::pair<double, int32_t>> keys;
-  std::vector<int32_t> tmp;
-  std::vector<NdTask> stack{{0, nr}};
-  while (!stack.empty()) {
-    NdTask t = stack.back();
-    stack.pop_back();
+  std::vector<std::atomic<int32_t>> owner(static_cast<size_t>(nr));
+  for (auto &o : owner) o.store(0, std::memory_order_relaxed);
+  std::atomic<int32_t> next_id{1};
+  struct Scratch {
+    std::vector<std::pair<double, int32_t>> keys;
+    std::vector<int32_t> tmp;
+  };
+  // splits task t into [A | B | separator]; returns the new tasks (A and B) in kids
+  auto split = [&](NdTask t, Scratch &sc, NdTask kids[2]) -> int {
     const int64_t cnt = t.hi - t.lo;
-    if (cnt <= leaf) continue;
+    if (cnt <= leaf) return 0;
     int axis = -1;
     double width = 0.0;
     for (int a = 0; a < dim; ++a) {
@@ -153,44 +180,96 @@ void order_coordinate_nd(const Adj &A, const double *xy, int dim, int leaf,
       }
       if (mx - mn > width) { width = mx - mn; axis = a; }
     }
-    if (axis < 0) continue;   // all nodes coincide: keep as one block
+    if (axis < 0) return 0;   // all nodes coincide: keep as one block
+    const int32_t id = next_id.fetch_add(1, std::memory_order_relaxed);
+    auto &keys = sc.keys;
     keys.resize(static_cast<size_t>(cnt));
-    for (int64_t i = 0; i < cnt; ++i)
-      keys[i] = {xy[static_cast<int64_t>(work[t.lo + i]) * dim + axis], work[t.lo + i]};
+    for (int64_t i = 0; i < cnt; ++i) {
+      const int32_t v = work[t.lo + i];
+      keys[i] = {xy[static_cast<int64_t>(v) * dim + axis], v};
+      owner[v].store(id, std::memory_order_relaxed);
+    }
     std::nth_element(keys.begin(), keys.begin() + cnt / 2, keys.end());
     const double pivot = keys[cnt / 2].first;
     int64_t nlow = 0;
     for (auto &k : keys) nlow += k.first < pivot;
     const bool strict = nlow > 0;
     for (auto &k : keys) side[k.second] = (strict ? k.first < pivot : k.first <= pivot) ? 0 : 1;
-    int64_t na = 0, nbu = 0, ns = 0;
+    int64_t na = 0, nbu = 0;
     for (int64_t i = t.lo; i < t.hi; ++i) {
       int32_t v = work[i];
       if (side[v] == 1) {
-        for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p)
-          if (side[A.idx[p]] == 0) { side[v] = 2; break; }
+        for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+          const int32_t u = A.idx[p];
+          if (owner[u].load(std::memory_order_relaxed) == id && side[u] == 0) {
+            side[v] = 2;
+            break;
+          }
+        }
       }
     }
     for (int64_t i = t.lo; i < t.hi; ++i) {
-      int s = side[work[i]];
-      na += s == 0;
-      nbu += s == 1;
-      ns += s == 2;
+      int sd = side[work[i]];
+      na += sd == 0;
+      nbu += sd == 1;
     }
     if (na == 0 || nbu == 0) {   // no proper split
       for (int64_t i = t.lo; i < t.hi; ++i) side[work[i]] = -1;
-      continue;
+      return 0;
     }
-    tmp.assign(work.begin() + t.lo, work.begin() + t.hi);
+    sc.tmp.assign(work.begin() + t.lo, work.begin() + t.hi);
     int64_t a = t.lo, b = t.lo + na, c = t.lo + na + nbu;
-    for (int32_t v : tmp) {
-      int s = side[v];
-      (s == 0 ? work[a++] : s == 1 ? work[b++] : work[c++]) = v;
+    for (int32_t v : sc.tmp) {
+      int sd = side[v];
+      (sd == 0 ? work[a++] : sd == 1 ? work[b++] : work[c++]) = v;
       side[v] = -1;
     }
-    stack.push_back({t.lo + na, t.lo + na + nbu});
-    stack.push_back({t.lo, t.lo + na});
+    kids[0] = {t.lo, t.lo + na};
+    kids[1] = {t.lo + na, t.lo + na + nbu};
+    return 2;
+  };
+  // a task of at most kNdLocal nodes is dissected whole by the thread that takes it
+  constexpr int64_t kNdLocal = 1 << 14;
+  auto run_local = [&](NdTask t, Scratch &sc) {
+    std::vector<NdTask> stack{t};
+    NdTask kids[2];
+    while (!stack.empty()) {
+      NdTask u = stack.back();
+      stack.pop_back();
+      const int k = split(u, sc, kids);
+      for (int i = k - 1; i >= 0; --i) stack.push_back(kids[i]);
+    }
+  };
+  const int nthreads = nr >= (int64_t(1) << 16) ? plan_threads() : 1;
+  if (nthreads <= 1) {
+    Scratch sc;
+    run_local({0, nr}, sc);
+    return;
   }
+  std::mutex mu;
+  std::condition_variable cv;
+  std::vector<NdTask> queue{{0, nr}};
+  int busy = 0;
+  run_threads(nthreads, [&](int) {
+    Scratch sc;
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      cv.wait(lk, [&] { return !queue.empty() || busy == 0; });
+      if (queue.empty()) return;   // nothing queued and nothing running: done
+      const NdTask t = queue.back();
+      queue.pop_back();
+      ++busy;
+      lk.unlock();
+      NdTask kids[2];
+      int k = 0;
+      if (t.hi - t.lo <= kNdLocal) run_local(t, sc);
+      else k = split(t, sc, kids);
+      lk.lock();
+      for (int i = 0; i < k; ++i) queue.push_back(kids[i]);
+      --busy;
+      cv.notify_all();
+    }
+  });
 }
 
 // BFS level-structure bisection for graphs without coordinates: from a pseudo-peripheral
@@ -330,25 +409,6 @@ int32_t sweep_tile(const Symbolic &S, int64_t N, int32_t cap) {
 }
 
 namespace {
-
-// Host threads for building a large plan's sweep levels (at most kPlanThreads).
-constexpr int kPlanThreads = 8;
-int plan_threads() {
-  const unsigned hw = std::thread::hardware_concurrency();
-  return static_cast<int>(std::max(1u, std::min<unsigned>(hw, kPlanThreads)));
-}
-
-// Runs f(0) .. f(nthreads - 1), each on a host thread of its own (inline for one).
-template <class F>
-void run_threads(int nthreads, F &&f) {
-  if (nthreads <= 1) {
-    f(0);
-    return;
-  }
-  std::vector<std::thread> pool;
-  for (int t = 0; t < nthreads; ++t) pool.emplace_back([&f, t]() { f(t); });
-  for (std::thread &th : pool) th.join();
-}
 
 // Orders the items [b, e) of a wave's level l (sorted by cost) with the spilled ones first
 // and records the level's launch shapes: shared memory of the regular launch, and the count
@@ -564,9 +624,46 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
       depth[s] = S.parent[s] == -1 ? 0 : depth[S.parent[s]] + 1;
     const int64_t per_two = std::max<int64_t>(1, per_wave / 2);
     const int32_t kInf = INT32_MAX;
+    // rank of each supernode in (level, supernode) order, the order the steps run in
+    std::vector<int32_t> rank(static_cast<size_t>(ns));
+    {
+      std::vector<int32_t> at(static_cast<size_t>(S.nlevels) + 1, 0);
+      for (int32_t s = 0; s < ns; ++s) at[S.level[s] + 1]++;
+      for (int32_t l = 0; l < S.nlevels; ++l) at[l + 1] += at[l];
+      for (int32_t s = 0; s < ns; ++s) rank[s] = at[S.level[s]]++;
+    }
     for (int64_t k0 = 0; k0 < S.nq_two; k0 += per_two) {
       const int64_t k1 = std::min<int64_t>(S.nq_two, k0 + per_two);
-      std::vector<std::pair<int32_t, SweepDesc>> steps;   // (supernode, step)
+      // the steps of pair k, in the order they are made, each passed to emit(supernode, step);
+      // the pair's merge supernode (lowest common ancestor of its two start supernodes, -1:
+      // different trees) is merge[k - k0]
+      std::vector<int32_t> merge(static_cast<size_t>(k1 - k0));
+      auto walk = [&](int64_t k, auto &&emit) {
+        const int32_t sa = S.col2sn[S.two_lo[k]], sb = S.col2sn[S.two_hi[k]];
+        const int32_t A = static_cast<int32_t>(S.nsorted + 2 * k), B = A + 1;
+        const int32_t m = merge[k - k0];
+        int32_t prev = -1;
+        for (int32_t p = sa; p != m; prev = p, p = S.parent[p])
+          emit(p, SweepDesc{A, prev, -1, -1, -1});
+        const int32_t child_a = prev;
+        prev = -1;
+        if (sb != m)
+          for (int32_t p = sb; p != m; prev = p, p = S.parent[p])
+            emit(p, SweepDesc{B, prev, -1, -1, -1});
+        const int32_t child_b = prev;
+        if (m != -1) {
+          if (sb == m)
+            emit(m, SweepDesc{A, child_a, -1, -1, S.two_hi[k] - S.first[m]});
+          else
+            emit(m, SweepDesc{A, child_a, B, child_b, -1});
+          prev = m;
+          for (int32_t p = S.parent[m]; p != -1; prev = p, p = S.parent[p])
+            emit(p, SweepDesc{A, prev, -1, -1, -1});
+        }
+      };
+      // the steps in (level, supernode) order, each supernode's in the order they are made:
+      // one pass counts them per supernode, a second writes each to its place
+      std::vector<int64_t> at(static_cast<size_t>(ns) + 1, 0);
       for (int64_t k = k0; k < k1; ++k) {
         const Two t{S.two_lo[k], S.two_hi[k], S.two_idx[k]};
         const int32_t sa = S.col2sn[t.lo], sb = S.col2sn[t.hi];
@@ -576,38 +673,22 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
         S.qb[A] = -1;
         S.qa[B] = -1;
         S.qb[B] = t.hi - S.first[sb];
-        // merge supernode = lowest common ancestor of sa and sb (-1: different trees)
         int32_t x = sa, y = sb;
         while (x != y && x != -1 && y != -1) {
           if (depth[x] >= depth[y]) x = S.parent[x]; else y = S.parent[y];
         }
         const int32_t m = (x == y) ? x : -1;
-        int32_t prev = -1;
-        for (int32_t p = sa; p != m; prev = p, p = S.parent[p])
-          steps.push_back({p, SweepDesc{A, prev, -1, -1, -1}});
-        const int32_t child_a = prev;
-        prev = -1;
-        if (sb != m)
-          for (int32_t p = sb; p != m; prev = p, p = S.parent[p])
-            steps.push_back({p, SweepDesc{B, prev, -1, -1, -1}});
-        const int32_t child_b = prev;
-        if (m != -1) {
-          if (sb == m)
-            steps.push_back({m, SweepDesc{A, child_a, -1, -1, t.hi - S.first[m]}});
-          else
-            steps.push_back({m, SweepDesc{A, child_a, B, child_b, -1}});
-          prev = m;
-          for (int32_t p = S.parent[m]; p != -1; prev = p, p = S.parent[p])
-            steps.push_back({p, SweepDesc{A, prev, -1, -1, -1}});
-        }
+        merge[k - k0] = m;
+        walk(k, [&](int32_t p, const SweepDesc &) { at[rank[p] + 1]++; });
         S.two_user.push_back(t.idx);
         S.two_a.push_back(A);
         S.two_b.push_back(m == -1 ? B : -1);
       }
-      std::stable_sort(steps.begin(), steps.end(), [&](const auto &u, const auto &v) {
-        if (S.level[u.first] != S.level[v.first]) return S.level[u.first] < S.level[v.first];
-        return u.first < v.first;
-      });
+      for (int32_t r = 0; r < ns; ++r) at[r + 1] += at[r];
+      struct Step { int32_t s; SweepDesc d; };
+      std::vector<Step, NoInitAlloc<Step>> steps(static_cast<size_t>(at[ns]));
+      for (int64_t k = k0; k < k1; ++k)
+        walk(k, [&](int32_t p, const SweepDesc &d) { steps[at[rank[p]]++] = Step{p, d}; });
       SweepWave W;
       W.q_begin = S.nsorted + 2 * k0;
       W.q_end = S.nsorted + 2 * k1;
@@ -629,13 +710,14 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
         else if (d.seed_b >= 0) r = std::min(r, d.seed_b);
         return r;
       };
+      W.items.reserve(steps.size());
       size_t i = 0;
       for (int32_t l = 0; l < S.nlevels; ++l) {
         const size_t lb = W.items.size();
-        while (i < steps.size() && S.level[steps[i].first] == l) {
-          const int32_t p = steps[i].first;
+        while (i < steps.size() && S.level[steps[i].s] == l) {
+          const int32_t p = steps[i].s;
           size_t e = i;
-          while (e < steps.size() && steps[e].first == p) ++e;
+          while (e < steps.size() && steps[e].s == p) ++e;
           for (size_t c = i; c < e; c += S.qtile[p]) {
             const size_t ce = std::min(e, c + static_cast<size_t>(S.qtile[p]));
             SweepItem it{};
@@ -647,10 +729,10 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
             it.nq = static_cast<int32_t>(ce - c);
             int32_t j0 = kInf;
             for (size_t q = c; q < ce; ++q) {
-              const int32_t fr = first_row(steps[q].second);
+              const int32_t fr = first_row(steps[q].d);
               j0 = std::min(j0, fr);
               S.walk_entries += entries(p, fr);
-              S.ldesc.push_back(steps[q].second);
+              S.ldesc.push_back(steps[q].d);
             }
             it.j0 = (j0 / kBlock) * kBlock;
             S.walk_fma += it.nq * item_fma(p, it.j0);

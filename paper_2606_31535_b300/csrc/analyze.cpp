@@ -494,6 +494,11 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
     const int64_t np = sn_nc(S, s) - first_col;
     return np * (np - 1) / 2 + int64_t(S.nb[s]) * np + np;
   };
+  // position of each supernode in level_sn
+  std::vector<int32_t> lpos(static_cast<size_t>(ns));
+  for (int32_t i = 0; i < ns; ++i) lpos[S.level_sn[i]] = i;
+  std::vector<int32_t> rel;
+  std::vector<int64_t> rel_ptr(static_cast<size_t>(S.nlevels) + 1);
   for (int64_t w0 = 0; w0 < std::max<int64_t>(S.nsorted, 1); w0 += per_wave) {
     SweepWave W;
     W.q_begin = w0;
@@ -504,14 +509,30 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
     W.level_smem.assign(static_cast<size_t>(S.nlevels), 0);
     W.level_nspill.assign(static_cast<size_t>(S.nlevels), 0);
     W.level_spill_smem.assign(static_cast<size_t>(S.nlevels), 0);
+    // The supernodes that can carry items of this wave: the start supernodes [s_lo, s_hi] of
+    // its queries and the ancestors of s_hi (every subtree that holds one of the wave's queries
+    // is a range of supernodes meeting [s_lo, s_hi], so its root is in it or above s_hi), by
+    // their positions in level_sn; rel[rel_ptr[l] .. rel_ptr[l + 1]) are level l's.
+    rel.clear();
+    if (W.q_end > W.q_begin) {
+      const int32_t s_lo = static_cast<int32_t>(
+          std::upper_bound(S.qbeg.begin() + 1, S.qbeg.end(), W.q_begin) - (S.qbeg.begin() + 1));
+      const int32_t s_hi = static_cast<int32_t>(
+          std::lower_bound(S.qbeg.begin(), S.qbeg.begin() + ns, W.q_end) - S.qbeg.begin()) - 1;
+      for (int32_t x = s_lo; x <= s_hi; ++x) rel.push_back(lpos[x]);
+      for (int32_t x = S.parent[s_hi]; x != -1; x = S.parent[x]) rel.push_back(lpos[x]);
+      std::sort(rel.begin(), rel.end());
+    }
+    for (int32_t l = 0; l <= S.nlevels; ++l)
+      rel_ptr[l] = std::lower_bound(rel.begin(), rel.end(), S.level_ptr[l]) - rel.begin();
     // Levels are independent: each builds its items, ordered by cost (largest first; ties in
     // the order they are made), into its own range of the wave's items (sized by a counting
     // pass), and its share of the walk counts, on up to kPlanThreads host threads; the counts
     // are summed in level order, so the plan is the same as one thread's.
     for (int32_t l = 0; l < S.nlevels; ++l) {
       int64_t cnt = 0;
-      for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
-        const int32_t p = S.level_sn[i];
+      for (int64_t r = rel_ptr[l]; r < rel_ptr[l + 1]; ++r) {
+        const int32_t p = S.level_sn[rel[r]];
         const int64_t tile = S.qtile[p];
         auto tiles = [&](int64_t b, int64_t e) {
           b = std::max(b, W.q_begin);
@@ -536,8 +557,8 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
       LevelOut &o = outs[l];
       std::vector<int64_t> keys;
       std::vector<SweepItem> made;
-      for (int32_t i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
-        const int32_t p = S.level_sn[i];
+      for (int64_t r = rel_ptr[l]; r < rel_ptr[l + 1]; ++r) {
+        const int32_t p = S.level_sn[rel[r]];
         const int32_t tile = S.qtile[p];
         auto emit = [&](int32_t src, int64_t b, int64_t e) {
           b = std::max(b, W.q_begin);

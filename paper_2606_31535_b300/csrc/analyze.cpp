@@ -49,6 +49,14 @@ void run_threads(int nthreads, F &&f) {
   for (std::thread &th : pool) th.join();
 }
 
+// Runs f(lo, hi) over contiguous chunks of [0, count): one chunk per host thread when count
+// is large, else one chunk.
+template <class F>
+void chunked(int64_t count, F &&f) {
+  const int nt = count >= (int64_t(1) << 18) ? plan_threads() : 1;
+  run_threads(nt, [&](int c) { f(count * c / nt, count * (c + 1) / nt); });
+}
+
 // ------------------------------------------------------------------------- validation
 
 int validate(int64_t n, const int64_t *indptr, const int32_t *indices, const double *w,
@@ -61,40 +69,62 @@ int validate(int64_t n, const int64_t *indptr, const int32_t *indices, const dou
   for (int64_t i = 0; i < n; ++i)
     if (indptr[i + 1] < indptr[i]) { err = "indptr is not non-decreasing"; return PEERS_EINVAL; }
   const int64_t nnz = indptr[n];
-  for (int64_t i = 0; i < n; ++i) {
+  // The row checks run over contiguous row chunks, one per host thread, in three passes (entry
+  // values; duplicates; symmetry).  Each chunk keeps its first failure, and the first chunk
+  // that failed reports: the error a pass over the rows in order meets first.
+  const int nchunks = nnz >= (int64_t(1) << 20) ? plan_threads() : 1;
+  std::vector<std::string> errs(static_cast<size_t>(nchunks));
+  std::vector<int> codes(static_cast<size_t>(nchunks), PEERS_OK);
+  auto pass = [&](auto &&check_row) -> int {
+    run_threads(nchunks, [&](int c) {
+      const int64_t r0 = n * c / nchunks, r1 = n * (c + 1) / nchunks;
+      for (int64_t i = r0; i < r1; ++i)
+        if (!check_row(i, errs[c])) { codes[c] = PEERS_EINVAL; return; }
+    });
+    for (int c = 0; c < nchunks; ++c)
+      if (codes[c] != PEERS_OK) { err = errs[c]; return codes[c]; }
+    return PEERS_OK;
+  };
+  int rc = pass([&](int64_t i, std::string &e) {
     for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
       int64_t j = indices[p];
-      if (j < 0 || j >= n) { err = "column index out of range"; return PEERS_EINVAL; }
-      if (j == i) { err = "self-loop at node " + std::to_string(i); return PEERS_EINVAL; }
+      if (j < 0 || j >= n) { e = "column index out of range"; return false; }
+      if (j == i) { e = "self-loop at node " + std::to_string(i); return false; }
       if (!(w[p] > 0.0) || !std::isfinite(w[p])) {
-        err = "conductance must be positive and finite (entry " + std::to_string(p) + ")";
-        return PEERS_EINVAL;
+        e = "conductance must be positive and finite (entry " + std::to_string(p) + ")";
+        return false;
       }
     }
-  }
+    return true;
+  });
+  if (rc != PEERS_OK) return rc;
   // per-row sorted copies for duplicate and symmetry checks
   std::vector<std::pair<int32_t, double>> srt(static_cast<size_t>(nnz));
-  for (int64_t i = 0; i < n; ++i) {
+  rc = pass([&](int64_t i, std::string &e) {
     for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) srt[p] = {indices[p], w[p]};
     std::sort(srt.begin() + indptr[i], srt.begin() + indptr[i + 1]);
     for (int64_t p = indptr[i] + 1; p < indptr[i + 1]; ++p)
       if (srt[p].first == srt[p - 1].first) {
-        err = "duplicate edge in row " + std::to_string(i);
-        return PEERS_EINVAL;
+        e = "duplicate edge in row " + std::to_string(i);
+        return false;
       }
-  }
-  for (int64_t i = 0; i < n; ++i) {
+    return true;
+  });
+  if (rc != PEERS_OK) return rc;
+  rc = pass([&](int64_t i, std::string &e) {
     for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
       const int32_t j = srt[p].first;
-      auto b = srt.begin() + indptr[j], e = srt.begin() + indptr[j + 1];
-      auto it = std::lower_bound(b, e, std::make_pair(static_cast<int32_t>(i), -1.0));
-      if (it == e || it->first != i) { err = "CSR is not symmetric"; return PEERS_EINVAL; }
+      auto b = srt.begin() + indptr[j], en = srt.begin() + indptr[j + 1];
+      auto it = std::lower_bound(b, en, std::make_pair(static_cast<int32_t>(i), -1.0));
+      if (it == en || it->first != i) { e = "CSR is not symmetric"; return false; }
       if (it->second != srt[p].second) {
-        err = "conductances of (u,v) and (v,u) differ";
-        return PEERS_EINVAL;
+        e = "conductances of (u,v) and (v,u) differ";
+        return false;
       }
     }
-  }
+    return true;
+  });
+  if (rc != PEERS_OK) return rc;
   // connectivity (the reduced Laplacian is SPD exactly when G is connected)
   std::vector<int32_t> queue(static_cast<size_t>(n));
   std::vector<char> seen(static_cast<size_t>(n), 0);
@@ -113,29 +143,33 @@ int validate(int64_t n, const int64_t *indptr, const int32_t *indices, const dou
 // Adjacency of the reduced graph (ground removed, no diagonal), reduced numbering.
 struct Adj {
   std::vector<int64_t> ptr;
-  std::vector<int32_t> idx;
+  std::vector<int32_t, NoInitAlloc<int32_t>> idx;
 };
 
 Adj reduced_adjacency(int64_t n, const int64_t *indptr, const int32_t *indices, int32_t g) {
   Adj A;
   const int64_t nr = n - 1;
   A.ptr.assign(static_cast<size_t>(nr + 1), 0);
-  for (int64_t i = 0; i < n; ++i) {
-    if (i == g) continue;
-    int64_t c = 0;
-    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) c += indices[p] != g;
-    A.ptr[(i > g ? i - 1 : i) + 1] = c;
-  }
+  chunked(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      if (i == g) continue;
+      int64_t c = 0;
+      for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) c += indices[p] != g;
+      A.ptr[(i > g ? i - 1 : i) + 1] = c;
+    }
+  });
   for (int64_t r = 0; r < nr; ++r) A.ptr[r + 1] += A.ptr[r];
   A.idx.resize(static_cast<size_t>(A.ptr[nr]));
-  for (int64_t i = 0; i < n; ++i) {
-    if (i == g) continue;
-    int64_t q = A.ptr[i > g ? i - 1 : i];
-    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
-      int32_t j = indices[p];
-      if (j != g) A.idx[q++] = j > g ? j - 1 : j;
+  chunked(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      if (i == g) continue;
+      int64_t q = A.ptr[i > g ? i - 1 : i];
+      for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
+        int32_t j = indices[p];
+        if (j != g) A.idx[q++] = j > g ? j - 1 : j;
+      }
     }
-  }
+  });
   return A;
 }
 
@@ -391,14 +425,18 @@ int64_t tri(int64_t a) { return a * (a + 1) / 2; }
 
 void assembly_values(const Symbolic &S, const double *w, std::vector<double> &vals) {
   vals.resize(S.a_dest.size());
-  for (int64_t e = 0; e < S.nnz_lower; ++e) vals[e] = -w[S.a_src[e]];
-  for (int64_t k = 0; k < S.nr; ++k) {
-    const int64_t r = S.perm[k];
-    const int64_t gnode = r + (r >= S.ground);
-    double deg = 0.0;
-    for (int64_t p = S.csr_indptr[gnode]; p < S.csr_indptr[gnode + 1]; ++p) deg += w[p];
-    vals[S.nnz_lower + k] = deg;
-  }
+  chunked(S.nnz_lower, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) vals[e] = -w[S.a_src[e]];
+  });
+  chunked(S.nr, [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1; ++k) {
+      const int64_t r = S.perm[k];
+      const int64_t gnode = r + (r >= S.ground);
+      double deg = 0.0;
+      for (int64_t p = S.csr_indptr[gnode]; p < S.csr_indptr[gnode + 1]; ++p) deg += w[p];
+      vals[S.nnz_lower + k] = deg;
+    }
+  });
 }
 
 int32_t sweep_tile(const Symbolic &S, int64_t N, int32_t cap) {
@@ -782,8 +820,14 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   S.nr = n - 1;
   S.ground = ground;
   S.nnz_csr = indptr[n];
-  S.csr_indptr.assign(indptr, indptr + n + 1);
-  S.w0.assign(w, w + indptr[n]);
+  S.csr_indptr.resize(static_cast<size_t>(n) + 1);
+  S.w0.resize(static_cast<size_t>(indptr[n]));
+  chunked(n + 1, [&](int64_t i0, int64_t i1) {
+    std::copy(indptr + i0, indptr + i1, S.csr_indptr.begin() + i0);
+  });
+  chunked(indptr[n], [&](int64_t p0, int64_t p1) {
+    std::copy(w + p0, w + p1, S.w0.begin() + p0);
+  });
   const int64_t nr = S.nr;
   const int leaf = opt.nd_leaf > 0 ? opt.nd_leaf : 32;
   Adj A = reduced_adjacency(n, indptr, indices, ground);
@@ -1025,9 +1069,14 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   {
     std::vector<int32_t> fill(S.level_ptr.begin(), S.level_ptr.end() - 1);
     for (int32_t s = 0; s < ns; ++s) S.level_sn[fill[S.level[s]]++] = s;
-    for (int32_t l = 0; l < S.nlevels; ++l)
-      std::stable_sort(S.level_sn.begin() + S.level_ptr[l], S.level_sn.begin() + S.level_ptr[l + 1],
-                       [&](int32_t a, int32_t b) { return sn_nc(S, a) > sn_nc(S, b); });
+    // levels sorted independently, on up to kPlanThreads host threads
+    std::atomic<int32_t> next{0};
+    run_threads(ns >= (1 << 16) ? plan_threads() : 1, [&](int) {
+      for (int32_t l = next++; l < S.nlevels; l = next++)
+        std::stable_sort(S.level_sn.begin() + S.level_ptr[l],
+                         S.level_sn.begin() + S.level_ptr[l + 1],
+                         [&](int32_t a, int32_t b) { return sn_nc(S, a) > sn_nc(S, b); });
+    });
   }
 
   // relative maps into the parent front: rows of s (C_s then B_s) -> local index in parent.
@@ -1085,33 +1134,56 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
       if (it == e || *it != i) return -1;
       return nc + (it - b);
     };
-    S.a_dest.clear();
-    S.a_src.clear();
-    S.a_dest.reserve(static_cast<size_t>(indptr[n] / 2 + nr));
-    S.a_src.reserve(static_cast<size_t>(indptr[n] / 2));
-    for (int64_t gi = 0; gi < n; ++gi) {
-      if (gi == ground) continue;
-      const int32_t i = iperm[gi > ground ? gi - 1 : gi];
-      for (int64_t p = indptr[gi]; p < indptr[gi + 1]; ++p) {
-        const int32_t gj = indices[p];
-        if (gj == ground) continue;
-        const int32_t j = iperm[gj > ground ? gj - 1 : gj];
-        if (i <= j) continue;   // lower entry (row i > column j)
-        const int32_t s = S.col2sn[j];
-        const int64_t N = sn_nc(S, s) + S.nb[s];
-        const int64_t lr = local_row(s, i);
-        if (lr < 0) { err = "internal: matrix entry outside the supernode structure"; return PEERS_EINVAL; }
-        S.a_dest.push_back(S.panel_off[s] + static_cast<int64_t>(j - S.first[s]) * N + lr);
-        S.a_src.push_back(p);
+    // rows in contiguous chunks, one per host thread: a first pass counts each chunk's lower
+    // entries, a second writes them at the chunk's offset (the order of one pass over the rows)
+    const int nchunks = indptr[n] >= (int64_t(1) << 20) ? plan_threads() : 1;
+    std::vector<int64_t> off(static_cast<size_t>(nchunks) + 1, 0);
+    std::vector<char> bad(static_cast<size_t>(nchunks), 0);
+    auto row_of = [&](int64_t g) { return iperm[g > ground ? g - 1 : g]; };
+    run_threads(nchunks, [&](int c) {
+      int64_t cnt = 0;
+      for (int64_t gi = n * c / nchunks; gi < n * (c + 1) / nchunks; ++gi) {
+        if (gi == ground) continue;
+        const int32_t i = row_of(gi);
+        for (int64_t p = indptr[gi]; p < indptr[gi + 1]; ++p)
+          cnt += indices[p] != ground && i > row_of(indices[p]);
       }
-    }
-    S.nnz_lower = static_cast<int64_t>(S.a_dest.size());
-    for (int64_t k = 0; k < nr; ++k) {
-      const int32_t s = S.col2sn[k];
-      const int64_t N = sn_nc(S, s) + S.nb[s];
-      const int64_t c = k - S.first[s];
-      S.a_dest.push_back(S.panel_off[s] + c * N + c);
-    }
+      off[c + 1] = cnt;
+    });
+    for (int c = 0; c < nchunks; ++c) off[c + 1] += off[c];
+    S.nnz_lower = off[nchunks];
+    S.a_dest.resize(static_cast<size_t>(S.nnz_lower + nr));
+    S.a_src.resize(static_cast<size_t>(S.nnz_lower));
+    run_threads(nchunks, [&](int c) {
+      int64_t q = off[c];
+      for (int64_t gi = n * c / nchunks; gi < n * (c + 1) / nchunks; ++gi) {
+        if (gi == ground) continue;
+        const int32_t i = row_of(gi);
+        for (int64_t p = indptr[gi]; p < indptr[gi + 1]; ++p) {
+          const int32_t gj = indices[p];
+          if (gj == ground) continue;
+          const int32_t j = row_of(gj);
+          if (i <= j) continue;   // lower entry (row i > column j)
+          const int32_t s = S.col2sn[j];
+          const int64_t N = sn_nc(S, s) + S.nb[s];
+          const int64_t lr = local_row(s, i);
+          if (lr < 0) { bad[c] = 1; return; }
+          S.a_dest[q] = S.panel_off[s] + static_cast<int64_t>(j - S.first[s]) * N + lr;
+          S.a_src[q] = p;
+          ++q;
+        }
+      }
+    });
+    for (int c = 0; c < nchunks; ++c)
+      if (bad[c]) { err = "internal: matrix entry outside the supernode structure"; return PEERS_EINVAL; }
+    chunked(nr, [&](int64_t k0, int64_t k1) {
+      for (int64_t k = k0; k < k1; ++k) {
+        const int32_t s = S.col2sn[k];
+        const int64_t N = sn_nc(S, s) + S.nb[s];
+        const int64_t c = k - S.first[s];
+        S.a_dest[S.nnz_lower + k] = S.panel_off[s] + c * N + c;
+      }
+    });
   }
 
   // ---- lanes: independent subtrees on separate CUDA streams ----
@@ -1402,11 +1474,13 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   S.qorig.resize(static_cast<size_t>(nslots));
   S.qa.resize(static_cast<size_t>(nslots));
   S.qb.resize(static_cast<size_t>(nslots));
-  for (size_t k = 0; k < recs.size(); ++k) {
-    S.qorig[k] = recs[k].idx;
-    S.qa[k] = recs[k].a;
-    S.qb[k] = recs[k].b;
-  }
+  chunked(static_cast<int64_t>(recs.size()), [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1; ++k) {
+      S.qorig[k] = recs[k].idx;
+      S.qa[k] = recs[k].a;
+      S.qb[k] = recs[k].b;
+    }
+  });
 
   S.two_lo.resize(twos.size());
   S.two_hi.resize(twos.size());

@@ -64,8 +64,9 @@ int dalloc(peers_numeric *num, T **p, int64_t count, std::string &err) {
   return PEERS_OK;
 }
 
-template <class T>
-int upload(peers_numeric *num, T **p, const std::vector<T> &v, cudaStream_t st, std::string &err) {
+template <class T, class Alloc>
+int upload(peers_numeric *num, T **p, const std::vector<T, Alloc> &v, cudaStream_t st,
+           std::string &err) {
   int rc = dalloc(num, p, static_cast<int64_t>(v.size()), err);
   if (rc != PEERS_OK || v.empty()) return rc;
   CUDA_TRY(cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));

@@ -164,12 +164,12 @@ struct Symbolic {
   // assembly of L_r into the panels: entry e goes to panel[a_dest[e]].  Entries are the
   // strictly-lower entries followed by the nr diagonal entries.  a_src[e] is the CSR index
   // of the conductance of an off-diagonal entry.
-  std::vector<int64_t> a_dest;
-  std::vector<int64_t> a_src;
+  std::vector<int64_t, NoInitAlloc<int64_t>> a_dest;
+  std::vector<int64_t, NoInitAlloc<int64_t>> a_src;
   int64_t nnz_lower = 0;
   // diagonal of the reduced node r = sum of the conductances of CSR row g(r)
-  std::vector<int64_t> csr_indptr;  // copy of the input indptr (to rebuild degrees)
-  std::vector<double> w0;           // conductances given to analyze
+  std::vector<int64_t, NoInitAlloc<int64_t>> csr_indptr;  // copy of the input indptr (degrees)
+  std::vector<double, NoInitAlloc<double>> w0;           // conductances given to analyze
   // lanes (see kLanes): per supernode its depth below its root and its lane (-1: top part)
   std::vector<int32_t> depth, lane_of;
   int32_t nlanes = 0;

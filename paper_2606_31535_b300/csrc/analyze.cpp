@@ -195,12 +195,17 @@ void order_coordinate_nd(const Adj &A, const double *xy, int dim, int leaf,
   std::vector<std::atomic<int32_t>> owner(static_cast<size_t>(nr));
   for (auto &o : owner) o.store(0, std::memory_order_relaxed);
   std::atomic<int32_t> next_id{1};
+  constexpr int64_t kNdInner = int64_t(1) << 20;
   struct Scratch {
     std::vector<std::pair<double, int32_t>> keys;
+    std::vector<double> vals, mn, mx;
+    std::vector<int64_t> cnt;
     std::vector<int32_t> tmp;
+    std::vector<char> sep;
   };
-  // splits task t into [A | B | separator]; returns the new tasks (A and B) in kids
-  auto split = [&](NdTask t, Scratch &sc, NdTask kids[2]) -> int {
+  // splits a task of fewer than kNdInner nodes into [A | B | separator] on the calling thread;
+  // returns the new tasks (A and B) in kids
+  auto split_small = [&](NdTask t, Scratch &sc, NdTask kids[2]) -> int {
     const int64_t cnt = t.hi - t.lo;
     if (cnt <= leaf) return 0;
     int axis = -1;
@@ -261,6 +266,131 @@ void order_coordinate_nd(const Adj &A, const double *xy, int dim, int leaf,
     kids[0] = {t.lo, t.lo + na};
     kids[1] = {t.lo + na, t.lo + na + nbu};
     return 2;
+  };
+  // the same split for a task of at least kNdInner nodes (the first levels, which run few at a
+  // time), each of its passes spread over host threads: chunk results are combined in chunk
+  // order, and the median is taken as the value of rank cnt / 2 of the coordinates alone
+  auto split_wide = [&](NdTask t, Scratch &sc, NdTask kids[2]) -> int {
+    const int64_t cnt = t.hi - t.lo;
+    const int nt = plan_threads();
+    // f(chunk, i0, i1) over contiguous chunks of the task's range
+    auto pfor = [&](auto &&f) {
+      run_threads(nt, [&](int c) { f(c, t.lo + cnt * c / nt, t.lo + cnt * (c + 1) / nt); });
+    };
+    auto coord = [&](int64_t i, int a) { return xy[static_cast<int64_t>(work[i]) * dim + a]; };
+    sc.mn.assign(static_cast<size_t>(nt) * dim, INFINITY);
+    sc.mx.assign(static_cast<size_t>(nt) * dim, -INFINITY);
+    pfor([&](int c, int64_t i0, int64_t i1) {
+      for (int a = 0; a < dim; ++a) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int64_t i = i0; i < i1; ++i) {
+          const double x = coord(i, a);
+          mn = std::min(mn, x);
+          mx = std::max(mx, x);
+        }
+        sc.mn[c * dim + a] = mn;
+        sc.mx[c * dim + a] = mx;
+      }
+    });
+    int axis = -1;
+    double width = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      double mn = INFINITY, mx = -INFINITY;
+      for (int c = 0; c < nt; ++c) {
+        mn = std::min(mn, sc.mn[c * dim + a]);
+        mx = std::max(mx, sc.mx[c * dim + a]);
+      }
+      if (mx - mn > width) { width = mx - mn; axis = a; }
+    }
+    if (axis < 0) return 0;   // all nodes coincide: keep as one block
+    const int32_t id = next_id.fetch_add(1, std::memory_order_relaxed);
+    // the median coordinate along the axis: the value of rank cnt / 2
+    sc.vals.resize(static_cast<size_t>(cnt));
+    pfor([&](int, int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i) {
+        sc.vals[i - t.lo] = coord(i, axis);
+        owner[work[i]].store(id, std::memory_order_relaxed);
+      }
+    });
+    std::nth_element(sc.vals.begin(), sc.vals.begin() + cnt / 2, sc.vals.end());
+    const double pivot = sc.vals[cnt / 2];
+    sc.cnt.assign(static_cast<size_t>(nt) * 3, 0);
+    pfor([&](int c, int64_t i0, int64_t i1) {
+      int64_t k = 0;
+      for (int64_t i = i0; i < i1; ++i) k += coord(i, axis) < pivot;
+      sc.cnt[c * 3] = k;
+    });
+    int64_t nlow = 0;
+    for (int c = 0; c < nt; ++c) nlow += sc.cnt[c * 3];
+    const bool strict = nlow > 0;
+    pfor([&](int, int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i) {
+        const double x = coord(i, axis);
+        side[work[i]] = (strict ? x < pivot : x <= pivot) ? 0 : 1;
+      }
+    });
+    // separator: upper-side nodes with a lower-side neighbour in this task
+    sc.sep.resize(static_cast<size_t>(cnt));
+    pfor([&](int, int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i) {
+        const int32_t v = work[i];
+        char f = 0;
+        if (side[v] == 1) {
+          for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+            const int32_t u = A.idx[p];
+            if (owner[u].load(std::memory_order_relaxed) == id && side[u] == 0) {
+              f = 1;
+              break;
+            }
+          }
+        }
+        sc.sep[i - t.lo] = f;
+      }
+    });
+    pfor([&](int c, int64_t i0, int64_t i1) {
+      int64_t k[3] = {0, 0, 0};
+      for (int64_t i = i0; i < i1; ++i) {
+        const int32_t v = work[i];
+        if (sc.sep[i - t.lo]) side[v] = 2;
+        k[side[v]]++;
+      }
+      for (int x = 0; x < 3; ++x) sc.cnt[c * 3 + x] = k[x];
+    });
+    int64_t na = 0, nbu = 0;
+    for (int c = 0; c < nt; ++c) {
+      na += sc.cnt[c * 3];
+      nbu += sc.cnt[c * 3 + 1];
+    }
+    if (na == 0 || nbu == 0) {   // no proper split
+      pfor([&](int, int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i) side[work[i]] = -1;
+      });
+      return 0;
+    }
+    // [A | B | separator], each part in the task's order: chunk c's nodes of a part follow
+    // those of the chunks before it
+    int64_t at[3] = {t.lo, t.lo + na, t.lo + na + nbu};
+    for (int c = 0; c < nt; ++c)
+      for (int x = 0; x < 3; ++x) {
+        const int64_t k = sc.cnt[c * 3 + x];
+        sc.cnt[c * 3 + x] = at[x];
+        at[x] += k;
+      }
+    sc.tmp.assign(work.begin() + t.lo, work.begin() + t.hi);
+    pfor([&](int c, int64_t i0, int64_t i1) {
+      int64_t pos[3] = {sc.cnt[c * 3], sc.cnt[c * 3 + 1], sc.cnt[c * 3 + 2]};
+      for (int64_t i = i0; i < i1; ++i) {
+        const int32_t v = sc.tmp[i - t.lo];
+        work[pos[side[v]]++] = v;
+        side[v] = -1;
+      }
+    });
+    kids[0] = {t.lo, t.lo + na};
+    kids[1] = {t.lo + na, t.lo + na + nbu};
+    return 2;
+  };
+  auto split = [&](NdTask t, Scratch &sc, NdTask kids[2]) -> int {
+    return t.hi - t.lo >= kNdInner ? split_wide(t, sc, kids) : split_small(t, sc, kids);
   };
   // a task of at most kNdLocal nodes is dissected whole by the thread that takes it
   constexpr int64_t kNdLocal = 1 << 14;

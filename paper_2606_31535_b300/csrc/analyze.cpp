@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstring>
 #include <condition_variable>
+#include <cstdlib>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -30,11 +31,17 @@ double since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
 }
 
-// Host threads for the large analysis steps (at most kPlanThreads).
+// Host threads for the large analysis steps: the hardware's count, at most kPlanThreads, and
+// at most PEERS_ANALYSIS_THREADS when that is set to a positive number.  No result depends on
+// the count.
 constexpr int kPlanThreads = 8;
 int plan_threads() {
-  const unsigned hw = std::thread::hardware_concurrency();
-  return static_cast<int>(std::max(1u, std::min<unsigned>(hw, kPlanThreads)));
+  unsigned t = std::min<unsigned>(std::thread::hardware_concurrency(), kPlanThreads);
+  if (const char *e = std::getenv("PEERS_ANALYSIS_THREADS")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v > 0) t = std::min<unsigned>(t, static_cast<unsigned>(v));
+  }
+  return static_cast<int>(std::max(1u, t));
 }
 
 // Runs f(0) .. f(nthreads - 1), each on a host thread of its own (inline for one).

@@ -170,6 +170,26 @@ def test_two_branch_pairs_are_planned(P):
     assert inf["walk_fma"] >= inf["walk_entries"] > 0
 
 
+def test_analysis_does_not_depend_on_host_threads(P, monkeypatch):
+    """One host thread and eight give the same ordering, supernodes and plan.
+
+    A 1024 x 1024 grid (about 1M nodes, 4M stored entries, 2M all-edge queries) is large
+    enough for every threaded step: validation chunks, nested-dissection splits of a million
+    nodes, per-thread query chunks and per-level plan items.
+    """
+    g = I.grid2d(1024, 1024, seed=12)
+    runs = []
+    for threads in ("1", "8"):
+        monkeypatch.setenv("PEERS_ANALYSIS_THREADS", threads)
+        sym = P.Symbolic.of(g)
+        inf = {k: v for k, v in sym.info().items() if not k.startswith("t_")}
+        runs.append((inf, sym.export()))
+        sym.close()
+    assert runs[0][0] == runs[1][0]
+    for key in runs[0][1]:
+        assert np.array_equal(runs[0][1][key], runs[1][1][key]), key
+
+
 def test_wave_budget_option(P):
     g = I.grid2d(20, 20, seed=2)
     opt = P.Options()

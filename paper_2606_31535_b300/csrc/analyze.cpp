@@ -17,8 +17,11 @@
 #include <cstring>
 #include <condition_variable>
 #include <cstdlib>
+#include <exception>
 #include <mutex>
+#include <new>
 #include <numeric>
+#include <system_error>
 #include <thread>
 
 #include "internal.h"
@@ -44,16 +47,38 @@ int plan_threads() {
   return static_cast<int>(std::max(1u, t));
 }
 
-// Runs f(0) .. f(nthreads - 1), each on a host thread of its own (inline for one).
+// Runs f(0) .. f(nthreads - 1), each on a host thread of its own (inline for one).  If the
+// system starts no more threads, the calling thread runs the remaining calls itself.  An
+// exception thrown by a call (a failed allocation) is rethrown here after every thread has
+// been joined.
 template <class F>
 void run_threads(int nthreads, F &&f) {
   if (nthreads <= 1) {
     f(0);
     return;
   }
+  std::vector<std::exception_ptr> errs(static_cast<size_t>(nthreads));
+  auto call = [&f, &errs](int t) {
+    try {
+      f(t);
+    } catch (...) {
+      errs[t] = std::current_exception();
+    }
+  };
   std::vector<std::thread> pool;
-  for (int t = 0; t < nthreads; ++t) pool.emplace_back([&f, t]() { f(t); });
+  pool.reserve(static_cast<size_t>(nthreads));
+  int started = 0;
+  for (; started < nthreads; ++started) {
+    try {
+      pool.emplace_back(call, started);
+    } catch (const std::system_error &) {
+      break;
+    }
+  }
+  for (int t = started; t < nthreads; ++t) call(t);
   for (std::thread &th : pool) th.join();
+  for (const std::exception_ptr &e : errs)
+    if (e) std::rethrow_exception(e);
 }
 
 // Runs f(lo, hi) over contiguous chunks of [0, count): one chunk per host thread when count
@@ -421,24 +446,33 @@ void order_coordinate_nd(const Adj &A, const double *xy, int dim, int leaf,
   std::condition_variable cv;
   std::vector<NdTask> queue{{0, nr}};
   int busy = 0;
+  bool failed = false;   // a task threw: every thread stops
   run_threads(nthreads, [&](int) {
     Scratch sc;
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
-      cv.wait(lk, [&] { return !queue.empty() || busy == 0; });
-      if (queue.empty()) return;   // nothing queued and nothing running: done
+      cv.wait(lk, [&] { return failed || !queue.empty() || busy == 0; });
+      if (failed || queue.empty()) return;   // nothing queued and nothing running: done
       const NdTask t = queue.back();
       queue.pop_back();
       ++busy;
       lk.unlock();
       NdTask kids[2];
       int k = 0;
-      if (t.hi - t.lo <= kNdLocal) run_local(t, sc);
-      else k = split(t, sc, kids);
+      std::exception_ptr ex;
+      try {
+        if (t.hi - t.lo <= kNdLocal) run_local(t, sc);
+        else k = split(t, sc, kids);
+      } catch (...) {
+        ex = std::current_exception();
+      }
       lk.lock();
-      for (int i = 0; i < k; ++i) queue.push_back(kids[i]);
+      if (ex) failed = true;
+      else
+        for (int i = 0; i < k; ++i) queue.push_back(kids[i]);
       --busy;
       cv.notify_all();
+      if (ex) std::rethrow_exception(ex);
     }
   });
 }
@@ -607,11 +641,26 @@ void finish_level(const Symbolic &S, SweepWave &W, int32_t l, SweepItem *b, Swee
 
 }  // namespace
 
+namespace {
+int build_sweep_plan_impl(Symbolic &S, const int32_t *qcap, std::string &err);
+}  // namespace
+
 // Tiles, waves and the two-branch walk of an analysed plan for the given per-size-class
 // tile caps (queries per CTA; 0 = the largest that fits).  Rebuilding it does not change the
 // arithmetic of any query: blocks stay aligned to kBlock whatever the tile, and a front kept
-// in global memory goes through exactly the same operations as one in shared memory.
+// in global memory goes through exactly the same operations as one in shared memory.  A failed
+// host allocation returns PEERS_ENOMEM (the plan is then unusable).
 int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
+  try {
+    return build_sweep_plan_impl(S, qcap, err);
+  } catch (const std::bad_alloc &) {
+    err = "host allocation while building the sweep plan";
+    return PEERS_ENOMEM;
+  }
+}
+
+namespace {
+int build_sweep_plan_impl(Symbolic &S, const int32_t *qcap, std::string &err) {
   struct Two { int32_t lo, hi; int64_t idx; };
   const int32_t kInfCol = INT32_MAX;
   (void)kInfCol;
@@ -786,12 +835,9 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
       for (int32_t l = 0; l < S.nlevels; ++l) build_level(l);
     } else {
       std::atomic<int32_t> next{0};
-      std::vector<std::thread> pool;
-      for (int t = 0; t < nthreads; ++t)
-        pool.emplace_back([&]() {
-          for (int32_t l = next++; l < S.nlevels; l = next++) build_level(l);
-        });
-      for (std::thread &th : pool) th.join();
+      run_threads(nthreads, [&](int) {
+        for (int32_t l = next++; l < S.nlevels; l = next++) build_level(l);
+      });
     }
     if (miscount) {
       err = "internal: sweep items disagree with their count";
@@ -944,6 +990,7 @@ int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err) {
   }
   return PEERS_OK;
 }
+}  // namespace
 
 // ------------------------------------------------------------------------- analyze
 

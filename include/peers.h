@@ -129,6 +129,10 @@ void peers_destroy(peers_ctx *ctx);
  * order "u ascending, then each CSR neighbour v > u in CSR order".  `coords` (n x dim, row
  * major, may be NULL) only guides the ordering.  `ctx` may be NULL: no device is touched.
  * Queries with u == v give R = 0; a query touching the ground follows eq. 4.
+ * Large graphs and query sets are analysed on up to 8 host threads (at most the hardware's
+ * count, and at most the environment variable PEERS_ANALYSIS_THREADS when it is set to a
+ * positive number); the plan does not depend on the thread count.  The caller's buffers are
+ * only read, and only during the call.
  * Errors: PEERS_EINVAL, PEERS_ENOTCONNECTED, PEERS_ENOMEM. */
 int peers_analyze(peers_ctx *ctx, int64_t n, const int64_t *indptr, const int32_t *indices,
                   const double *w, int32_t ground, int64_t nq, const int32_t *qu,

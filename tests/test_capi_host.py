@@ -173,11 +173,12 @@ def test_two_branch_pairs_are_planned(P):
 def test_analysis_does_not_depend_on_host_threads(P, monkeypatch):
     """One host thread and eight give the same ordering, supernodes and plan.
 
-    A 1024 x 1024 grid (about 1M nodes, 4M stored entries, 2M all-edge queries) is large
-    enough for every threaded step: validation chunks, nested-dissection splits of a million
-    nodes, per-thread query chunks and per-level plan items.
+    A 1025 x 1024 grid (1 049 600 nodes, 4.2M stored entries, 2.1M all-edge queries) is large
+    enough for every threaded step: validation chunks, nested-dissection splits of 2^20 nodes
+    or more, per-thread query chunks and per-level plan items.
     """
-    g = I.grid2d(1024, 1024, seed=12)
+    g = I.grid2d(1025, 1024, seed=12)
+    assert g.n - 1 >= 1 << 20
     runs = []
     for threads in ("1", "8"):
         monkeypatch.setenv("PEERS_ANALYSIS_THREADS", threads)

@@ -154,6 +154,73 @@ def test_walk_work_matches_a_direct_count(P):
     assert W == inf["walk_entries"]
 
 
+def _lower_pattern(g, perm, ground):
+    """Strictly-lower pattern of L (dense bool, n-1 x n-1) by symbolic elimination of the
+    grounded graph in the order perm (perm[k] = reduced node eliminated k-th)."""
+    n1 = g.n - 1
+    pos = np.empty(n1, np.int64)
+    pos[perm] = np.arange(n1)
+    rows = np.repeat(np.arange(g.n), np.diff(g.indptr))
+    L = np.zeros((n1, n1), bool)
+    for a, b in zip(rows, g.indices):
+        if a != ground and b != ground:
+            i, j = pos[a - (a > ground)], pos[b - (b > ground)]
+            if i > j:
+                L[i, j] = True
+    for k in range(n1):   # eliminating k joins all of its lower neighbours
+        nz = np.flatnonzero(L[k + 1:, k]) + k + 1
+        if nz.size > 1:
+            L[np.ix_(nz, nz)] |= np.tril(np.ones((nz.size, nz.size), bool), -1)
+    return L
+
+
+def _small_graphs():
+    rng = np.random.default_rng(21)
+    out = []
+    n = 120   # random tree
+    out.append(("tree", I.from_edges(n, np.arange(1, n), rng.integers(0, np.arange(1, n)),
+                                     rng.uniform(0.5, 2.0, n - 1)), 7))
+    n = 40    # star grounded at its centre: the reduced graph has no edges
+    out.append(("star-centre", I.from_edges(n, np.zeros(n - 1, np.int64), np.arange(1, n),
+                                            np.ones(n - 1)), 0))
+    out.append(("star-leaf", I.from_edges(n, np.zeros(n - 1, np.int64), np.arange(1, n),
+                                          np.ones(n - 1)), 5))
+    iu, iv = np.triu_indices(14, 1)   # complete graph
+    out.append(("K14", I.from_edges(14, iu, iv, np.ones(iu.size)), 3))
+    n = 200   # path with random chords
+    cu, cv = rng.integers(0, n, 60), rng.integers(0, n, 60)
+    eu, ev = np.concatenate([np.arange(n - 1), cu]), np.concatenate([np.arange(1, n), cv])
+    keep = eu != ev
+    a, b = np.minimum(eu, ev)[keep], np.maximum(eu, ev)[keep]
+    key = np.unique(a * n + b)
+    out.append(("chords", I.from_edges(n, key // n, key % n, np.ones(key.size)), 123))
+    out.append(("grid", I.grid2d(11, 13, seed=4), 60))
+    out.append(("rgg", I.rgg(250, seed=8), 17))
+    return out
+
+
+@pytest.mark.parametrize("name,g,ground", [pytest.param(*c, id=c[0]) for c in _small_graphs()])
+def test_supernode_rows_match_symbolic_elimination(P, name, g, ground):
+    """Each supernode's below-diagonal row count equals the column count of its last column in
+    L's pattern, found here by eliminating the grounded graph in the exported order; every
+    column of the supernode has its lower rows within that set; the parent holds the
+    smallest of those rows."""
+    for use_coords in ((True, False) if g.coords is not None else (False,)):
+        sym = P.Symbolic.of(g, ground=ground, use_coords=use_coords)
+        ex = sym.export()
+        first, par, nb = ex["first"], ex["parent"], ex["nb"]
+        L = _lower_pattern(g, ex["perm"], ground)
+        col2sn = np.repeat(np.arange(first.size - 1), np.diff(first))
+        for f in range(first.size - 1):
+            last = first[f + 1] - 1
+            below = np.flatnonzero(L[last + 1:, last]) + last + 1
+            assert nb[f] == below.size, (name, f)
+            for k in range(first[f], last):
+                rows_k = np.flatnonzero(L[last + 1:, k]) + last + 1
+                assert np.isin(rows_k, below).all(), (name, f, k)
+            assert par[f] == (col2sn[below[0]] if below.size else -1), (name, f)
+
+
 def test_all_edge_order_and_footprint(P):
     g = I.grid32()
     sym = P.Symbolic.of(g)

@@ -721,42 +721,55 @@ int build_sweep_plan_impl(Symbolic &S, const int32_t *qcap, std::string &err) {
   // position of each supernode in level_sn
   std::vector<int32_t> lpos(static_cast<size_t>(ns));
   for (int32_t i = 0; i < ns; ++i) lpos[S.level_sn[i]] = i;
-  std::vector<int32_t> rel;
-  std::vector<int64_t> rel_ptr(static_cast<size_t>(S.nlevels) + 1);
+  // the waves' query ranges (one empty wave when there are no queries)
+  std::vector<std::pair<int64_t, int64_t>> ranges;
   for (int64_t w0 = 0; w0 < std::max<int64_t>(S.nsorted, 1); w0 += per_wave) {
-    SweepWave W;
-    W.q_begin = w0;
-    W.q_end = std::min<int64_t>(S.nsorted, w0 + per_wave);
-    if (W.q_end <= W.q_begin && S.nsorted > 0) break;
-    S.carry_slots = std::max(S.carry_slots, W.q_end - W.q_begin);
+    const int64_t w1 = std::min<int64_t>(S.nsorted, w0 + per_wave);
+    if (w1 <= w0 && S.nsorted > 0) break;
+    ranges.emplace_back(w0, w1);
+    if (S.nsorted == 0) break;
+  }
+  const int64_t nw = static_cast<int64_t>(ranges.size());
+  const int nthreads = S.nsorted >= (int64_t(1) << 16) ? plan_threads() : 1;
+  struct LevelOut {
+    int64_t walk_entries = 0, walk_fma = 0, front_bytes = 0;
+  };
+  struct WaveBuild {
+    std::vector<int32_t> rel;       // positions in level_sn of the supernodes it can reach
+    std::vector<int64_t> rel_ptr;   // nlevels + 1: level l's are rel[rel_ptr[l] .. [l + 1])
+    std::vector<LevelOut> outs;
+  };
+  std::vector<SweepWave> waves(static_cast<size_t>(nw));
+  std::vector<WaveBuild> wb(static_cast<size_t>(nw));
+  // Each wave first finds the supernodes that can carry its items: the start supernodes
+  // [s_lo, s_hi] of its queries and the ancestors of s_hi (every subtree that holds one of the
+  // wave's queries is a range of supernodes meeting [s_lo, s_hi], so its root is in it or
+  // above s_hi).  A counting pass then sizes each level's range of the wave's items.
+  auto setup_wave = [&](int64_t w) {
+    SweepWave &W = waves[w];
+    WaveBuild &B = wb[w];
+    W.q_begin = ranges[w].first;
+    W.q_end = ranges[w].second;
     W.level_ptr.assign(static_cast<size_t>(S.nlevels) + 1, 0);
     W.level_smem.assign(static_cast<size_t>(S.nlevels), 0);
     W.level_nspill.assign(static_cast<size_t>(S.nlevels), 0);
     W.level_spill_smem.assign(static_cast<size_t>(S.nlevels), 0);
-    // The supernodes that can carry items of this wave: the start supernodes [s_lo, s_hi] of
-    // its queries and the ancestors of s_hi (every subtree that holds one of the wave's queries
-    // is a range of supernodes meeting [s_lo, s_hi], so its root is in it or above s_hi), by
-    // their positions in level_sn; rel[rel_ptr[l] .. rel_ptr[l + 1]) are level l's.
-    rel.clear();
     if (W.q_end > W.q_begin) {
       const int32_t s_lo = static_cast<int32_t>(
           std::upper_bound(S.qbeg.begin() + 1, S.qbeg.end(), W.q_begin) - (S.qbeg.begin() + 1));
       const int32_t s_hi = static_cast<int32_t>(
           std::lower_bound(S.qbeg.begin(), S.qbeg.begin() + ns, W.q_end) - S.qbeg.begin()) - 1;
-      for (int32_t x = s_lo; x <= s_hi; ++x) rel.push_back(lpos[x]);
-      for (int32_t x = S.parent[s_hi]; x != -1; x = S.parent[x]) rel.push_back(lpos[x]);
-      std::sort(rel.begin(), rel.end());
+      for (int32_t x = s_lo; x <= s_hi; ++x) B.rel.push_back(lpos[x]);
+      for (int32_t x = S.parent[s_hi]; x != -1; x = S.parent[x]) B.rel.push_back(lpos[x]);
+      std::sort(B.rel.begin(), B.rel.end());
     }
+    B.rel_ptr.resize(static_cast<size_t>(S.nlevels) + 1);
     for (int32_t l = 0; l <= S.nlevels; ++l)
-      rel_ptr[l] = std::lower_bound(rel.begin(), rel.end(), S.level_ptr[l]) - rel.begin();
-    // Levels are independent: each builds its items, ordered by cost (largest first; ties in
-    // the order they are made), into its own range of the wave's items (sized by a counting
-    // pass), and its share of the walk counts, on up to kPlanThreads host threads; the counts
-    // are summed in level order, so the plan is the same as one thread's.
+      B.rel_ptr[l] = std::lower_bound(B.rel.begin(), B.rel.end(), S.level_ptr[l]) - B.rel.begin();
     for (int32_t l = 0; l < S.nlevels; ++l) {
       int64_t cnt = 0;
-      for (int64_t r = rel_ptr[l]; r < rel_ptr[l + 1]; ++r) {
-        const int32_t p = S.level_sn[rel[r]];
+      for (int64_t r = B.rel_ptr[l]; r < B.rel_ptr[l + 1]; ++r) {
+        const int32_t p = S.level_sn[B.rel[r]];
         const int64_t tile = S.qtile[p];
         auto tiles = [&](int64_t b, int64_t e) {
           b = std::max(b, W.q_begin);
@@ -772,84 +785,91 @@ int build_sweep_plan_impl(Symbolic &S, const int32_t *qcap, std::string &err) {
       W.level_ptr[l + 1] = W.level_ptr[l] + cnt;
     }
     W.items.resize(static_cast<size_t>(W.level_ptr[S.nlevels]));
-    struct LevelOut {
-      int64_t walk_entries = 0, walk_fma = 0, front_bytes = 0;
-    };
-    std::vector<LevelOut> outs(static_cast<size_t>(S.nlevels));
-    std::atomic<bool> miscount{false};
-    auto build_level = [&](int32_t l) {
-      LevelOut &o = outs[l];
-      std::vector<int64_t> keys;
-      std::vector<SweepItem> made;
-      for (int64_t r = rel_ptr[l]; r < rel_ptr[l + 1]; ++r) {
-        const int32_t p = S.level_sn[rel[r]];
-        const int32_t tile = S.qtile[p];
-        auto emit = [&](int32_t src, int64_t b, int64_t e) {
-          b = std::max(b, W.q_begin);
-          e = std::min(e, W.q_end);
-          for (int64_t q = b; q < e; q += tile) {
-            SweepItem it{};
-            it.s = p;
-            it.src = src;
-            it.q0 = static_cast<int32_t>(q);
-            it.nq = static_cast<int32_t>(std::min<int64_t>(tile, e - q));
-            it.spill = S.spill[p];
-            int32_t j0;
-            if (src >= 0) {
-              j0 = S.rmap[S.rows_off[src]];
-              o.walk_entries += it.nq * entries(p, j0);
-            } else {
-              j0 = S.qa[q];
-              for (int64_t k = q; k < q + it.nq; ++k) o.walk_entries += entries(p, S.qa[k]);
-            }
-            it.j0 = (j0 / kBlock) * kBlock;
-            const int64_t f = it.nq * item_fma(p, it.j0);
-            o.walk_fma += f;
-            // fronts carried between levels: read from the child's carry, written for the parent
-            o.front_bytes += int64_t(8) * it.nq * ((src >= 0 ? S.nb[src] : 0) + S.nb[p]);
-            keys.push_back(f);
-            made.push_back(it);
+    B.outs.assign(static_cast<size_t>(S.nlevels), LevelOut{});
+  };
+  // Then every (wave, level) is independent: it builds its items, ordered by cost (largest
+  // first; ties in the order they are made), into its own range of the wave's items, and its
+  // share of the walk counts.  They run on up to kPlanThreads host threads; the counts are
+  // summed in wave and level order, so the plan is the same as one thread's.
+  std::atomic<bool> miscount{false};
+  auto build_level = [&](int64_t w, int32_t l) {
+    SweepWave &W = waves[w];
+    const WaveBuild &B = wb[w];
+    LevelOut &o = wb[w].outs[l];
+    std::vector<int64_t> keys;
+    std::vector<SweepItem> made;
+    for (int64_t r = B.rel_ptr[l]; r < B.rel_ptr[l + 1]; ++r) {
+      const int32_t p = S.level_sn[B.rel[r]];
+      const int32_t tile = S.qtile[p];
+      auto emit = [&](int32_t src, int64_t b, int64_t e) {
+        b = std::max(b, W.q_begin);
+        e = std::min(e, W.q_end);
+        for (int64_t q = b; q < e; q += tile) {
+          SweepItem it{};
+          it.s = p;
+          it.src = src;
+          it.q0 = static_cast<int32_t>(q);
+          it.nq = static_cast<int32_t>(std::min<int64_t>(tile, e - q));
+          it.spill = S.spill[p];
+          int32_t j0;
+          if (src >= 0) {
+            j0 = S.rmap[S.rows_off[src]];
+            o.walk_entries += it.nq * entries(p, j0);
+          } else {
+            j0 = S.qa[q];
+            for (int64_t k = q; k < q + it.nq; ++k) o.walk_entries += entries(p, S.qa[k]);
           }
-        };
-        for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
-          const int32_t ch = S.child_list[c];
-          emit(ch, S.qbeg[S.fdesc[ch]], S.qbeg[ch + 1]);
+          it.j0 = (j0 / kBlock) * kBlock;
+          const int64_t f = it.nq * item_fma(p, it.j0);
+          o.walk_fma += f;
+          // fronts carried between levels: read from the child's carry, written for the parent
+          o.front_bytes += int64_t(8) * it.nq * ((src >= 0 ? S.nb[src] : 0) + S.nb[p]);
+          keys.push_back(f);
+          made.push_back(it);
         }
-        emit(-1, S.qbeg[p], S.qbeg[p + 1]);
+      };
+      for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
+        const int32_t ch = S.child_list[c];
+        emit(ch, S.qbeg[S.fdesc[ch]], S.qbeg[ch + 1]);
       }
-      std::vector<int32_t> order(made.size());
-      std::iota(order.begin(), order.end(), 0);
-      std::stable_sort(order.begin(), order.end(),
-                       [&](int32_t x, int32_t y) { return keys[x] > keys[y]; });
-      if (static_cast<int64_t>(made.size()) != W.level_ptr[l + 1] - W.level_ptr[l]) {
-        miscount = true;
-        return;
-      }
-      SweepItem *dst = W.items.data() + W.level_ptr[l];
-      for (int32_t x : order) *dst++ = made[x];
-      finish_level(S, W, l, W.items.data() + W.level_ptr[l], dst);
-    };
-    const int64_t wave_queries = W.q_end - W.q_begin;
-    const int nthreads = wave_queries >= (int64_t(1) << 16) ? plan_threads() : 1;
-    if (nthreads <= 1) {
-      for (int32_t l = 0; l < S.nlevels; ++l) build_level(l);
-    } else {
-      std::atomic<int32_t> next{0};
-      run_threads(nthreads, [&](int) {
-        for (int32_t l = next++; l < S.nlevels; l = next++) build_level(l);
-      });
+      emit(-1, S.qbeg[p], S.qbeg[p + 1]);
     }
-    if (miscount) {
-      err = "internal: sweep items disagree with their count";
-      return PEERS_EINVAL;
+    std::vector<int32_t> order(made.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return keys[x] > keys[y]; });
+    if (static_cast<int64_t>(made.size()) != W.level_ptr[l + 1] - W.level_ptr[l]) {
+      miscount = true;
+      return;
     }
-    for (const LevelOut &o : outs) {
+    SweepItem *dst = W.items.data() + W.level_ptr[l];
+    for (int32_t x : order) *dst++ = made[x];
+    finish_level(S, W, l, W.items.data() + W.level_ptr[l], dst);
+  };
+  {
+    std::atomic<int64_t> next{0};
+    run_threads(nthreads, [&](int) {
+      for (int64_t w = next++; w < nw; w = next++) setup_wave(w);
+    });
+    const int64_t ntasks = nw * S.nlevels;
+    std::atomic<int64_t> task{0};
+    run_threads(nthreads, [&](int) {
+      for (int64_t t = task++; t < ntasks; t = task++)
+        build_level(t / S.nlevels, static_cast<int32_t>(t % S.nlevels));
+    });
+  }
+  if (miscount) {
+    err = "internal: sweep items disagree with their count";
+    return PEERS_EINVAL;
+  }
+  for (int64_t w = 0; w < nw; ++w) {
+    for (const LevelOut &o : wb[w].outs) {
       S.walk_entries += o.walk_entries;
       S.walk_fma += o.walk_fma;
       S.front_bytes += o.front_bytes;
     }
-    S.waves.push_back(std::move(W));
-    if (S.nsorted == 0) break;
+    S.carry_slots = std::max(S.carry_slots, waves[w].q_end - waves[w].q_begin);
+    S.waves.push_back(std::move(waves[w]));
   }
   if (S.nsorted == 0 && S.nq_two > 0) S.waves.clear();
 

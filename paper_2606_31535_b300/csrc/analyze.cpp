@@ -130,13 +130,15 @@ int validate(int64_t n, const int64_t *indptr, const int32_t *indices, const dou
     return true;
   });
   if (rc != PEERS_OK) return rc;
-  // per-row sorted copies for duplicate and symmetry checks
-  std::vector<std::pair<int32_t, double>> srt(static_cast<size_t>(nnz));
+  // per-row copies sorted by column, for the duplicate and symmetry checks
+  struct Entry { int32_t j; double w; };
+  std::vector<Entry, NoInitAlloc<Entry>> srt(static_cast<size_t>(nnz));
   rc = pass([&](int64_t i, std::string &e) {
-    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) srt[p] = {indices[p], w[p]};
-    std::sort(srt.begin() + indptr[i], srt.begin() + indptr[i + 1]);
+    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) srt[p] = Entry{indices[p], w[p]};
+    std::sort(srt.begin() + indptr[i], srt.begin() + indptr[i + 1],
+              [](const Entry &a, const Entry &b) { return a.j < b.j; });
     for (int64_t p = indptr[i] + 1; p < indptr[i + 1]; ++p)
-      if (srt[p].first == srt[p - 1].first) {
+      if (srt[p].j == srt[p - 1].j) {
         e = "duplicate edge in row " + std::to_string(i);
         return false;
       }
@@ -145,11 +147,11 @@ int validate(int64_t n, const int64_t *indptr, const int32_t *indices, const dou
   if (rc != PEERS_OK) return rc;
   rc = pass([&](int64_t i, std::string &e) {
     for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
-      const int32_t j = srt[p].first;
+      const int32_t j = srt[p].j;
       auto b = srt.begin() + indptr[j], en = srt.begin() + indptr[j + 1];
-      auto it = std::lower_bound(b, en, std::make_pair(static_cast<int32_t>(i), -1.0));
-      if (it == en || it->first != i) { e = "CSR is not symmetric"; return false; }
-      if (it->second != srt[p].second) {
+      auto it = std::lower_bound(b, en, i, [](const Entry &a, int64_t c) { return a.j < c; });
+      if (it == en || it->j != i) { e = "CSR is not symmetric"; return false; }
+      if (it->w != srt[p].w) {
         e = "conductances of (u,v) and (v,u) differ";
         return false;
       }
@@ -157,18 +159,7 @@ int validate(int64_t n, const int64_t *indptr, const int32_t *indices, const dou
     return true;
   });
   if (rc != PEERS_OK) return rc;
-  // connectivity (the reduced Laplacian is SPD exactly when G is connected)
-  std::vector<int32_t> queue(static_cast<size_t>(n));
-  std::vector<char> seen(static_cast<size_t>(n), 0);
-  int64_t head = 0, tail = 0;
-  queue[tail++] = 0;
-  seen[0] = 1;
-  while (head < tail) {
-    int32_t v = queue[head++];
-    for (int64_t p = indptr[v]; p < indptr[v + 1]; ++p)
-      if (!seen[indices[p]]) { seen[indices[p]] = 1; queue[tail++] = indices[p]; }
-  }
-  if (tail != n) { err = "graph is not connected"; return PEERS_ENOTCONNECTED; }
+  // connectivity is checked on the elimination tree, once the analysis has it
   return PEERS_OK;
 }
 
@@ -1093,6 +1084,20 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
     perm.swap(perm2);
     par.swap(par2);
     for (int64_t k = 0; k < nr; ++k) iperm[perm[k]] = static_cast<int32_t>(k);
+  }
+  // connectivity (the reduced Laplacian is SPD exactly when G is connected): the etree has one
+  // tree per connected component of the reduced graph, and G is connected exactly when each
+  // of them holds a neighbour of the ground
+  {
+    std::vector<char> reach(static_cast<size_t>(nr), 0);
+    for (int64_t p = indptr[ground]; p < indptr[ground + 1]; ++p) {
+      const int32_t j = indices[p];
+      reach[iperm[j > ground ? j - 1 : j]] = 1;
+    }
+    for (int64_t k = 0; k < nr; ++k) {   // postorder: a subtree is complete when its root is met
+      if (par[k] != -1) reach[par[k]] |= reach[k];
+      else if (!reach[k]) { err = "graph is not connected"; return PEERS_ENOTCONNECTED; }
+    }
   }
   S.t_order = since(t0);
   auto t1 = Clock::now();

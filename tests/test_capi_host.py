@@ -70,6 +70,14 @@ def test_rejects_malformed_graphs(P):
     two = I.from_edges(32, np.concatenate([u, u + 16]), np.concatenate([v, v + 16]),
                        np.concatenate([ww, ww]))
     assert _bad(P, two) == P.ENOTCONNECTED
+    assert _bad(P, two, ground=20) == P.ENOTCONNECTED
+    # a path 1-2-3-4 and an isolated node 0, grounded at the isolated node and on the path
+    path = I.from_edges(5, np.array([1, 2, 3]), np.array([2, 3, 4]), np.ones(3))
+    assert _bad(P, path, ground=0) == P.ENOTCONNECTED
+    assert _bad(P, path, ground=2) == P.ENOTCONNECTED
+    # connected once the ground's edges are counted: a star grounded at its centre
+    star = I.from_edges(6, np.zeros(5, np.int64), np.arange(1, 6), np.ones(5))
+    P.Symbolic(star.n, star.indptr, star.indices, star.w, ground=0).close()
     with pytest.raises(P.PeersError):
         P.Symbolic(g.n, g.indptr, g.indices, g.w, qu=np.array([0]), qv=np.array([g.n]))
 

@@ -1219,25 +1219,58 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   // row structure B_s (rows past s's last column).  Row i belongs to B_s exactly when s lies
   // on the supernodal etree path from the supernode of one of row i's entries j < i up to
   // (not including) the supernode of i; rows are visited in increasing order, so each B_s
-  // fills sorted, into the slot its column count sized.
+  // fills sorted, into the slot its column count sized.  The walks of a row stay inside the
+  // subtree of its supernode, and rows above a subtree are greater than all of its rows, so
+  // disjoint subtrees run on host threads of their own and the rows above them follow.
   {
-    S.rows.assign(static_cast<size_t>(S.rows_off[ns]), 0);
+    S.rows.clear();
+    S.rows.resize(static_cast<size_t>(S.rows_off[ns]));   // every slot is written below
     std::vector<int64_t> fill(S.rows_off.begin(), S.rows_off.end() - 1);
     std::vector<int32_t> mk(static_cast<size_t>(ns), -1);
-    bool ok = true;
-    for (int64_t ii = 0; ii < nr && ok; ++ii) {
-      const int32_t i = static_cast<int32_t>(ii);
-      mk[S.col2sn[i]] = i;
-      const int32_t v = perm[i];
-      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
-        const int32_t j = iperm[A.idx[p]];
-        if (j >= i) continue;
-        for (int32_t t = S.col2sn[j]; t != -1 && mk[t] != i; t = S.parent[t]) {
-          if (fill[t] == S.rows_off[t + 1]) { ok = false; break; }
-          mk[t] = i;
-          S.rows[fill[t]++] = i;
+    auto run_rows = [&](int64_t i0, int64_t i1) -> bool {
+      for (int64_t ii = i0; ii < i1; ++ii) {
+        const int32_t i = static_cast<int32_t>(ii);
+        mk[S.col2sn[i]] = i;
+        const int32_t v = perm[i];
+        for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+          const int32_t j = iperm[A.idx[p]];
+          if (j >= i) continue;
+          for (int32_t t = S.col2sn[j]; t != -1 && mk[t] != i; t = S.parent[t]) {
+            if (fill[t] == S.rows_off[t + 1]) return false;
+            mk[t] = i;
+            S.rows[fill[t]++] = i;
+          }
         }
       }
+      return true;
+    };
+    bool ok = true;
+    const int nthreads = nr >= (int64_t(1) << 16) ? plan_threads() : 1;
+    if (nthreads <= 1) {
+      ok = run_rows(0, nr);
+    } else {
+      // subtrees of at most nr / (4 nthreads) rows whose parent's subtree is larger; a subtree
+      // of supernode s holds supernodes [sub[s], s] (postorder) and rows [first[sub[s]],
+      // first[s + 1])
+      std::vector<int32_t> sub(static_cast<size_t>(ns));
+      std::iota(sub.begin(), sub.end(), 0);
+      for (int32_t t = 0; t < ns; ++t)
+        if (S.parent[t] != -1) sub[S.parent[t]] = std::min(sub[S.parent[t]], sub[t]);
+      const int64_t cap = std::max<int64_t>(1, nr / (4 * nthreads));
+      auto big = [&](int32_t t) { return S.first[t + 1] - S.first[sub[t]] > cap; };
+      std::vector<int32_t> roots;
+      for (int32_t t = 0; t < ns; ++t)
+        if (!big(t) && (S.parent[t] == -1 || big(S.parent[t]))) roots.push_back(t);
+      std::atomic<size_t> next{0};
+      std::atomic<bool> good{true};
+      run_threads(nthreads, [&](int) {
+        for (size_t r = next++; r < roots.size(); r = next++)
+          if (!run_rows(S.first[sub[roots[r]]], S.first[roots[r] + 1])) good = false;
+      });
+      ok = good;
+      // the rows of the supernodes above those subtrees, in increasing order
+      for (int32_t t = 0; t < ns && ok; ++t)
+        if (big(t)) ok = run_rows(S.first[t], S.first[t + 1]);
     }
     for (int32_t t = 0; t < ns && ok; ++t) ok = fill[t] == S.rows_off[t + 1];
     if (!ok) {

@@ -147,7 +147,7 @@ struct Symbolic {
   std::vector<int32_t> fdesc;       // first (lowest-numbered) supernode of the subtree
   std::vector<int32_t> child_ptr, child_list;   // children in increasing order
   std::vector<int64_t> rows_off;    // nsuper + 1: B_s = rows[rows_off[s] .. rows_off[s+1])
-  std::vector<int32_t> rows;        // global row indices (elimination positions), ascending
+  std::vector<int32_t, NoInitAlloc<int32_t>> rows;   // row indices (elimination positions), ascending
   std::vector<int32_t> rmap;        // parallel to rows: local row of B_s[t] in the parent front
   std::vector<int32_t> col2sn;      // column -> supernode
   int32_t nlevels = 0;

@@ -9,7 +9,8 @@
 //   - elimination tree (Lemma 1: y = L^{-1} b is non-zero only on etree paths);
 //   - query graph (§III-G): each query is mapped to its permuted endpoints and grouped by the
 //     supernode where its etree path starts.
-// Everything here is integer work on the CPU; no device is touched.
+// Everything here is integer work on the CPU; no device is touched.  The large steps run on
+// up to kPlanThreads host threads, and no result depends on how many.
 #include <algorithm>
 #include <atomic>
 #include <chrono>

@@ -35,16 +35,18 @@ double since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
 }
 
-// Host threads for the large analysis steps: the hardware's count, at most kPlanThreads, and
-// at most PEERS_ANALYSIS_THREADS when that is set to a positive number.  No result depends on
-// the count.
+// Host threads for the large analysis steps: the hardware's count, at most kPlanThreads, at
+// most PEERS_ANALYSIS_THREADS when that is set to a positive number, and at most the calling
+// thread's cap (set_host_thread_cap).  No result depends on the count.
 constexpr int kPlanThreads = 8;
+thread_local int t_thread_cap = 0;
 int plan_threads() {
   unsigned t = std::min<unsigned>(std::thread::hardware_concurrency(), kPlanThreads);
   if (const char *e = std::getenv("PEERS_ANALYSIS_THREADS")) {
     const long v = std::strtol(e, nullptr, 10);
     if (v > 0) t = std::min<unsigned>(t, static_cast<unsigned>(v));
   }
+  if (t_thread_cap > 0) t = std::min<unsigned>(t, static_cast<unsigned>(t_thread_cap));
   return static_cast<int>(std::max(1u, t));
 }
 
@@ -294,9 +296,10 @@ void order_coordinate_nd(const Adj &A, const double *xy, int dim, int leaf,
   // the same split for a task of at least kNdInner nodes (the first levels, which run few at a
   // time), each of its passes spread over host threads: chunk results are combined in chunk
   // order, and the median is taken as the value of rank cnt / 2 of the coordinates alone
+  const int wide_threads = plan_threads();   // read on the calling thread (its cap applies)
   auto split_wide = [&](NdTask t, Scratch &sc, NdTask kids[2]) -> int {
     const int64_t cnt = t.hi - t.lo;
-    const int nt = plan_threads();
+    const int nt = wide_threads;
     // f(chunk, i0, i1) over contiguous chunks of the task's range
     auto pfor = [&](auto &&f) {
       run_threads(nt, [&](int c) { f(c, t.lo + cnt * c / nt, t.lo + cnt * (c + 1) / nt); });
@@ -583,6 +586,8 @@ void etree(const Adj &A, const std::vector<int32_t> &perm, const std::vector<int
 int64_t tri(int64_t a) { return a * (a + 1) / 2; }
 
 }  // namespace
+
+void set_host_thread_cap(int cap) { t_thread_cap = cap; }
 
 // ------------------------------------------------------------------------- assembly values
 

@@ -242,6 +242,8 @@ int32_t sweep_tile(const Symbolic &S, int64_t N, int32_t cap);
 
 // (Re)builds the sweep's tiles and waves of an analysed plan (analyze.cpp).
 int build_sweep_plan(Symbolic &S, const int32_t *qcap, std::string &err);
+// Caps the host threads of the analyses the calling thread runs (0: no cap).
+void set_host_thread_cap(int cap);
 
 // Conductance-dependent assembly values (off-diagonals -w, then diagonals = degrees) in the
 // order of a_dest, for conductances w (CSR layout of the analysed graph).

@@ -151,6 +151,9 @@ void release_device(Request &r, cudaStream_t stream) {
 // per-request scratch, hand the request to the device thread.
 void worker_main(peers_server *sv) {
   cudaSetDevice(sv->device);
+  // the workers already analyse requests side by side: each analysis keeps to its thread, so
+  // that they leave the host cores to each other and to the device thread
+  peers::set_host_thread_cap(1);
   peers_ctx *ctx = nullptr;
   if (peers_create(&ctx, sv->device, nullptr) != PEERS_OK) return;
   for (;;) {

@@ -254,16 +254,25 @@ def test_analysis_does_not_depend_on_host_threads(P, monkeypatch):
     """
     g = I.grid2d(1025, 1024, seed=12)
     assert g.n - 1 >= 1 << 20
-    runs = []
-    for threads in ("1", "8"):
-        monkeypatch.setenv("PEERS_ANALYSIS_THREADS", threads)
-        sym = P.Symbolic.of(g)
-        inf = {k: v for k, v in sym.info().items() if not k.startswith("t_")}
-        runs.append((inf, sym.export()))
-        sym.close()
-    assert runs[0][0] == runs[1][0]
-    for key in runs[0][1]:
-        assert np.array_equal(runs[0][1][key], runs[1][1][key]), key
+    many_waves = P.Options()
+    many_waves.carry_budget = 1 << 30   # a few tens of waves
+    for opt in (None, many_waves):
+        runs = []
+        for threads in ("1", "8"):
+            monkeypatch.setenv("PEERS_ANALYSIS_THREADS", threads)
+            sym = P.Symbolic.of(g, options=opt)
+            inf = {k: v for k, v in sym.info().items() if not k.startswith("t_")}
+            inf["footprint"] = sym.footprint_bytes()
+            runs.append((inf, sym.export()))
+            sym.close()
+        assert runs[0][0] == runs[1][0]
+        for key in runs[0][1]:
+            assert np.array_equal(runs[0][1][key], runs[1][1][key]), key
+        if opt is None:
+            one_wave = runs[0][0]
+    # the waves (a smaller carry buffer) split the same walk
+    assert runs[0][0]["footprint"] < one_wave["footprint"] - (1 << 30)
+    assert runs[0][0]["walk_entries"] == one_wave["walk_entries"]
 
 
 def test_wave_budget_option(P):

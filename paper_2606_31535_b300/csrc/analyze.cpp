@@ -1125,6 +1125,8 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
       for (int32_t j = static_cast<int32_t>(k); j != -1 && fdesc[j] == -1; j = par[j])
         fdesc[j] = static_cast<int32_t>(k);
     }
+    for (int64_t k = 0; k < nr; ++k)
+      if (par[k] != -1) { cc[par[k]]--; nchild[par[k]]++; }
     std::vector<int32_t> anc(static_cast<size_t>(nr)), maxfirst(static_cast<size_t>(nr), -1),
         prevleaf(static_cast<size_t>(nr), -1);
     std::iota(anc.begin(), anc.end(), 0);
@@ -1134,20 +1136,59 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
       while (anc[x] != r) { const int32_t nx = anc[x]; anc[x] = r; x = nx; }
       return r;
     };
-    for (int64_t k = 0; k < nr; ++k) {
-      const int32_t j = static_cast<int32_t>(k);
-      if (par[j] != -1) { cc[par[j]]--; nchild[par[j]]++; }
-      const int32_t v = perm[j];
-      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
-        const int32_t i = iperm[A.idx[p]];
-        if (i <= j || fdesc[j] <= maxfirst[i]) continue;   // j is not a new leaf of row i's tree
-        maxfirst[i] = fdesc[j];
-        const int32_t jprev = prevleaf[i];
-        prevleaf[i] = j;
-        cc[j]++;
-        if (jprev != -1) cc[find(jprev)]--;
+    // column j as a possible leaf of row i's subtree (rows' columns taken in increasing order)
+    auto leaf_step = [&](int32_t i, int32_t j) {
+      if (fdesc[j] <= maxfirst[i]) return;   // j is not a new leaf of row i's tree
+      maxfirst[i] = fdesc[j];
+      const int32_t jprev = prevleaf[i];
+      prevleaf[i] = j;
+      cc[j]++;
+      if (jprev != -1) cc[find(jprev)]--;
+    };
+    // The row subtree of a row i lies in the etree subtree of i, so the etree subtrees of at
+    // most nr / (4 nthreads) columns whose parent's subtree is larger take their own rows on
+    // host threads of their own (the lowest common ancestors of their rows' leaves stay inside
+    // them).  The rows above those subtrees follow on one thread, their (row, column) pairs in
+    // increasing column order, over a fresh union-find that links every column before the
+    // current one: the marks each row leaves do not depend on how the rows are split.
+    const int nthreads = nr >= (int64_t(1) << 16) ? plan_threads() : 1;
+    const int64_t cap = nthreads > 1 ? std::max<int64_t>(1, nr / (4 * nthreads)) : nr;
+    auto big = [&](int64_t k) { return k - fdesc[k] + 1 > cap; };
+    std::vector<int32_t> roots;
+    for (int64_t k = 0; k < nr; ++k)
+      if (!big(k) && (par[k] == -1 || big(par[k]))) roots.push_back(static_cast<int32_t>(k));
+    std::atomic<size_t> next{0};
+    run_threads(nthreads, [&](int) {
+      for (size_t x = next++; x < roots.size(); x = next++) {
+        const int32_t r = roots[x];
+        for (int32_t j = fdesc[r]; j <= r; ++j) {
+          const int32_t v = perm[j];
+          for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+            const int32_t i = iperm[A.idx[p]];
+            if (i > j && i <= r) leaf_step(i, j);
+          }
+          if (j != r) anc[j] = par[j];
+        }
       }
-      if (par[j] != -1) anc[j] = par[j];
+    });
+    std::vector<std::pair<int32_t, int32_t>> top;   // (column j, row i > j), row i above them
+    for (int64_t k = 0; k < nr; ++k) {
+      if (!big(k)) continue;
+      const int32_t v = perm[k];
+      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+        const int32_t j = iperm[A.idx[p]];
+        if (j < k) top.emplace_back(j, static_cast<int32_t>(k));
+      }
+    }
+    if (!top.empty()) {
+      std::sort(top.begin(), top.end());
+      std::iota(anc.begin(), anc.end(), 0);
+      int64_t linked = 0;
+      for (const auto &pr : top) {
+        for (; linked < pr.first; ++linked)
+          if (par[linked] != -1) anc[linked] = par[linked];
+        leaf_step(pr.second, pr.first);
+      }
     }
     for (int64_t k = 0; k < nr; ++k)
       if (par[k] != -1) cc[par[k]] += cc[k];

@@ -1369,28 +1369,37 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   }
 
   // relative maps into the parent front: rows of s (C_s then B_s) -> local index in parent.
-  // Each parent's rows are scattered once into a table indexed by row, for all its children.
-  S.rmap.assign(S.rows.size(), -1);
+  // A child's rows and its parent's are both ascending, so one forward search through the
+  // parent's rows maps a child; children are mapped independently, over host-thread chunks.
+  S.rmap.clear();
+  S.rmap.resize(S.rows.size());   // every slot is written below
   {
-    std::vector<int32_t> where(static_cast<size_t>(nr), -1), owner(static_cast<size_t>(nr), -1);
-    for (int32_t p = 0; p < ns; ++p) {
-      if (S.child_ptr[p] == S.child_ptr[p + 1]) continue;
-      const int32_t pf = S.first[p], pnc = sn_nc(S, p);
-      for (int64_t t = S.rows_off[p]; t < S.rows_off[p + 1]; ++t) {
-        where[S.rows[t]] = pnc + static_cast<int32_t>(t - S.rows_off[p]);
-        owner[S.rows[t]] = p;
-      }
-      for (int32_t c = S.child_ptr[p]; c < S.child_ptr[p + 1]; ++c) {
-        const int32_t ch = S.child_list[c];
-        for (int64_t t = S.rows_off[ch]; t < S.rows_off[ch + 1]; ++t) {
+    const int nchunks =
+        static_cast<int64_t>(S.rows.size()) >= (int64_t(1) << 20) ? plan_threads() : 1;
+    std::vector<const char *> bad(static_cast<size_t>(nchunks), nullptr);
+    run_threads(nchunks, [&](int c) {
+      for (int32_t s = static_cast<int32_t>(int64_t(ns) * c / nchunks);
+           s < static_cast<int32_t>(int64_t(ns) * (c + 1) / nchunks); ++s) {
+        const int32_t p = S.parent[s];
+        if (p == -1) {
+          std::fill(S.rmap.begin() + S.rows_off[s], S.rmap.begin() + S.rows_off[s + 1], -1);
+          continue;
+        }
+        const int32_t pf = S.first[p], pnc = sn_nc(S, p);
+        const auto pb = S.rows.begin() + S.rows_off[p], pe = S.rows.begin() + S.rows_off[p + 1];
+        auto at = pb;
+        for (int64_t t = S.rows_off[s]; t < S.rows_off[s + 1]; ++t) {
           const int32_t r = S.rows[t];
-          if (r < pf) { err = "internal: row below the parent's first column"; return PEERS_EINVAL; }
+          if (r < pf) { bad[c] = "internal: row below the parent's first column"; return; }
           if (r < pf + pnc) { S.rmap[t] = r - pf; continue; }
-          if (owner[r] != p) { err = "internal: child row missing from parent"; return PEERS_EINVAL; }
-          S.rmap[t] = where[r];
+          at = std::lower_bound(at, pe, r);
+          if (at == pe || *at != r) { bad[c] = "internal: child row missing from parent"; return; }
+          S.rmap[t] = pnc + static_cast<int32_t>(at - pb);
         }
       }
-    }
+    });
+    for (const char *m : bad)
+      if (m) { err = m; return PEERS_EINVAL; }
   }
 
   // ---- device layout ----
@@ -1464,7 +1473,10 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
       }
     });
     for (int c = 0; c < nchunks; ++c)
-      if (bad[c]) { err = "internal: matrix entry outside the supernode structure"; return PEERS_EINVAL; }
+      if (bad[c]) {
+        err = "internal: matrix entry outside the supernode structure";
+        return PEERS_EINVAL;
+      }
     chunked(nr, [&](int64_t k0, int64_t k1) {
       for (int64_t k = k0; k < k1; ++k) {
         const int32_t s = S.col2sn[k];
@@ -1483,7 +1495,8 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   // other's partial last waves; the supernodes above the cut (lane -1) run on the context's
   // stream.  A lane's arithmetic is that of the one-stream schedule, in the same order.
   S.depth.assign(static_cast<size_t>(ns), 0);
-  for (int32_t s = ns - 1; s >= 0; --s) S.depth[s] = S.parent[s] == -1 ? 0 : S.depth[S.parent[s]] + 1;
+  for (int32_t s = ns - 1; s >= 0; --s)
+    S.depth[s] = S.parent[s] == -1 ? 0 : S.depth[S.parent[s]] + 1;
   S.lane_of.assign(static_cast<size_t>(ns), -1);
   S.nlanes = 0;
   {

@@ -147,8 +147,9 @@ struct Symbolic {
   std::vector<int32_t> fdesc;       // first (lowest-numbered) supernode of the subtree
   std::vector<int32_t> child_ptr, child_list;   // children in increasing order
   std::vector<int64_t> rows_off;    // nsuper + 1: B_s = rows[rows_off[s] .. rows_off[s+1])
-  std::vector<int32_t, NoInitAlloc<int32_t>> rows;   // row indices (elimination positions), ascending
-  std::vector<int32_t> rmap;        // parallel to rows: local row of B_s[t] in the parent front
+  // row indices (elimination positions) of each B_s, ascending
+  std::vector<int32_t, NoInitAlloc<int32_t>> rows;
+  std::vector<int32_t, NoInitAlloc<int32_t>> rmap;   // parallel to rows: local row in the parent
   std::vector<int32_t> col2sn;      // column -> supernode
   int32_t nlevels = 0;
   std::vector<int32_t> level_ptr;   // nlevels + 1

@@ -620,7 +620,8 @@ namespace {
 // and records the level's launch shapes: shared memory of the regular launch, and the count
 // and shared memory of the spilled items' launch.
 void finish_level(const Symbolic &S, SweepWave &W, int32_t l, SweepItem *b, SweepItem *e) {
-  std::stable_partition(b, e, [](const SweepItem &it) { return it.spill != 0; });
+  auto spilled = [](const SweepItem &it) { return it.spill != 0; };
+  if (std::any_of(b, e, spilled)) std::stable_partition(b, e, spilled);
   int64_t smem = 0, nspill = 0, spill_smem = 0;
   for (const SweepItem *pi = b; pi != e; ++pi) {
     const SweepItem &it = *pi;
@@ -793,8 +794,11 @@ int build_sweep_plan_impl(Symbolic &S, const int32_t *qcap, std::string &err) {
     SweepWave &W = waves[w];
     const WaveBuild &B = wb[w];
     LevelOut &o = wb[w].outs[l];
-    std::vector<int64_t> keys;
-    std::vector<SweepItem> made;
+    const int64_t count = W.level_ptr[l + 1] - W.level_ptr[l];
+    std::vector<int64_t, NoInitAlloc<int64_t>> keys;
+    std::vector<SweepItem, NoInitAlloc<SweepItem>> made;
+    keys.reserve(static_cast<size_t>(count));
+    made.reserve(static_cast<size_t>(count));
     for (int64_t r = B.rel_ptr[l]; r < B.rel_ptr[l + 1]; ++r) {
       const int32_t p = S.level_sn[B.rel[r]];
       const int32_t tile = S.qtile[p];
@@ -831,14 +835,14 @@ int build_sweep_plan_impl(Symbolic &S, const int32_t *qcap, std::string &err) {
       }
       emit(-1, S.qbeg[p], S.qbeg[p + 1]);
     }
+    if (static_cast<int64_t>(made.size()) != count) {
+      miscount = true;
+      return;
+    }
     std::vector<int32_t> order(made.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t x, int32_t y) { return keys[x] > keys[y]; });
-    if (static_cast<int64_t>(made.size()) != W.level_ptr[l + 1] - W.level_ptr[l]) {
-      miscount = true;
-      return;
-    }
     SweepItem *dst = W.items.data() + W.level_ptr[l];
     for (int32_t x : order) *dst++ = made[x];
     finish_level(S, W, l, W.items.data() + W.level_ptr[l], dst);
@@ -1666,15 +1670,34 @@ int analyze(Symbolic &S, int64_t n, const int64_t *indptr, const int32_t *indice
   auto t2 = Clock::now();
 
   // ---- queries (§III-G: each query mapped to permuted endpoints, grouped by start) ----
-  std::vector<int32_t> eu, ev;
+  std::vector<int32_t, NoInitAlloc<int32_t>> eu, ev;
   const int32_t *QU = qu, *QV = qv;
   if (nq < 0 || !qu || !qv) {
-    eu.reserve(static_cast<size_t>(indptr[n] / 2));
-    ev.reserve(static_cast<size_t>(indptr[n] / 2));
-    for (int64_t u = 0; u < n; ++u)
-      for (int64_t p = indptr[u]; p < indptr[u + 1]; ++p)
-        if (indices[p] > u) { eu.push_back(static_cast<int32_t>(u)); ev.push_back(indices[p]); }
-    nq = static_cast<int64_t>(eu.size());
+    // all edges, u ascending then CSR order: each row chunk counts its edges (u < v), then
+    // writes them from its prefix offset
+    const int nt = n >= (int64_t(1) << 18) ? plan_threads() : 1;
+    std::vector<int64_t> at(static_cast<size_t>(nt) + 1, 0);
+    auto row_edges = [&](int c, auto &&put) {
+      for (int64_t u = n * c / nt, u1 = n * (c + 1) / nt; u < u1; ++u)
+        for (int64_t p = indptr[u]; p < indptr[u + 1]; ++p)
+          if (indices[p] > u) put(u, indices[p]);
+    };
+    run_threads(nt, [&](int c) {
+      int64_t k = 0;
+      row_edges(c, [&](int64_t, int32_t) { ++k; });
+      at[c + 1] = k;
+    });
+    for (int c = 0; c < nt; ++c) at[c + 1] += at[c];
+    eu.resize(static_cast<size_t>(at[nt]));
+    ev.resize(static_cast<size_t>(at[nt]));
+    run_threads(nt, [&](int c) {
+      int64_t k = at[c];
+      row_edges(c, [&](int64_t u, int32_t v) {
+        eu[k] = static_cast<int32_t>(u);
+        ev[k++] = v;
+      });
+    });
+    nq = at[nt];
     QU = eu.data();
     QV = ev.data();
   }

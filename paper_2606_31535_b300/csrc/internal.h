@@ -205,8 +205,9 @@ struct Symbolic {
   int64_t nq_trivial = 0;
   int64_t nq_two = 0;
   int64_t nsorted = 0;              // non-trivial queries, sorted by (start supernode, lo)
-  std::vector<int64_t> qorig;       // sorted slot -> user query index
-  std::vector<int32_t> qa, qb;      // local seed rows (+1 at qa, -1 at qb; qb = -1: none)
+  std::vector<int64_t, NoInitAlloc<int64_t>> qorig;   // sorted slot -> user query index
+  // local seed rows (+1 at qa, -1 at qb; qb = -1: none)
+  std::vector<int32_t, NoInitAlloc<int32_t>> qa, qb;
   std::vector<int64_t> qbeg;        // nsuper + 1: first slot whose start supernode is >= s
   std::vector<int32_t> qtile;       // tile size (queries per CTA) per supernode
   int32_t qcap[kSizeClasses] = {kQMax, kQMax, kQMax, kQMax};   // tile caps in use

@@ -346,3 +346,70 @@ def test_one_stream_option_removes_lanes_and_split_blocks(P):
     assert info["lanes"] == 0 and info["split_blocks"] == 0
     for k in ("nsuper", "levels", "nnz_l", "walk_entries", "factor_fma"):
         assert info[k] == base[k]
+
+
+def _walk_entries_by_solve(g, ex, ground, qu, qv):
+    """W of a query list, counted here from the pattern of the sparse solve L y = e_lo - e_hi
+    (§III-G, eq. 16-18): y is non-zero on the etree paths from both endpoints to the root, so a
+    supernode is visited from the first of its columns that either path reaches; the visit
+    reads the panel entries from that column on (its triangle, its n_b rows below and the
+    diagonal).  Supernode parents and the columns where the paths enter them come from the
+    symbolic elimination of the grounded graph in the exported order."""
+    first, par, nb = ex["first"], ex["parent"], ex["nb"]
+    L = _lower_pattern(g, ex["perm"], ground)
+    n1 = g.n - 1
+    pos = np.empty(n1, np.int64)
+    pos[ex["perm"]] = np.arange(n1)
+    col2sn = np.repeat(np.arange(first.size - 1), np.diff(first))
+    enter = []   # per supernode, the column where a path from below enters its parent
+    for s in range(first.size - 1):
+        last = first[s + 1] - 1
+        below = np.flatnonzero(L[last + 1:, last]) + last + 1
+        enter.append(int(below[0]) if below.size else -1)
+    W = 0
+    for a, b in zip(qu, qv):
+        if a == b:
+            continue
+        reached = {}   # supernode -> first local column reached
+        for x in (a, b):
+            if x == ground:
+                continue
+            c = int(pos[x - (x > ground)])
+            s = int(col2sn[c])
+            while s != -1:
+                loc = c - int(first[s])
+                if s in reached:   # the rest of this path is already on the other one
+                    reached[s] = min(reached[s], loc)
+                    break
+                reached[s] = loc
+                c, s = enter[s], int(par[s])
+        for s, fc in reached.items():
+            m = int(first[s + 1] - first[s]) - fc
+            W += m * (m - 1) // 2 + int(nb[s]) * m + m
+    return W
+
+
+@pytest.mark.parametrize("name,g,ground", [pytest.param(*c, id=c[0]) for c in _small_graphs()])
+def test_walk_work_of_listed_pairs_matches_the_solve_pattern(P, name, g, ground):
+    """The analysis's W (the walk's entries, the roofline's algorithmic work) for a query list
+    mixing edges, non-adjacent pairs (one- and two-branch walks), pairs through the ground and
+    u == v equals the count from the solve's pattern, with and without coordinates and with a
+    small carry budget (many waves)."""
+    rng = np.random.default_rng(len(name) * 7 + ground)
+    k = 300
+    qu = rng.integers(0, g.n, k).astype(np.int32)
+    qv = rng.integers(0, g.n, k).astype(np.int32)
+    eu, ev = g.all_edges()
+    pick = rng.integers(0, eu.size, 60) if eu.size else np.zeros(0, np.int64)
+    qu = np.concatenate([qu, eu[pick], [ground, ground, 3 % g.n]]).astype(np.int32)
+    qv = np.concatenate([qv, ev[pick], [(ground + 1) % g.n, ground, 3 % g.n]]).astype(np.int32)
+    few = P.Options()
+    few.carry_budget = 4096
+    for use_coords in ((True, False) if g.coords is not None else (False,)):
+        for opt in (None, few):
+            sym = P.Symbolic.of(g, ground=ground, qu=qu, qv=qv, use_coords=use_coords,
+                                options=opt)
+            inf, ex = sym.info(), sym.export()
+            assert inf["walk_entries"] == _walk_entries_by_solve(g, ex, ground, qu, qv), \
+                (name, use_coords, opt is not None)
+            sym.close()

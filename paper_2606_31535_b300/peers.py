@@ -229,23 +229,43 @@ class Context:
         return np.array(buf[:min(n, 4096)])
 
 
+def _graph_args(n, indptr, indices, w, qu, qv, coords, where: str):
+    """The graph, query and coordinate arrays in the library's types, with their sizes
+    checked: the library reads n + 1 offsets, indptr[n] indices and conductances, nq query
+    pairs and n x dim coordinates through plain pointers.  Returns
+    (indptr, indices, w, qu, qv, nq, coords, dim), nq = -1 for all edges."""
+    ip = np.ascontiguousarray(indptr, dtype=np.int64)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    wv = np.ascontiguousarray(w, dtype=np.float64)
+    if int(n) < 0 or ip.ndim != 1 or ip.size != int(n) + 1:
+        raise ValueError(f"{where}: indptr must hold n + 1 = {int(n) + 1} offsets")
+    if ix.ndim != 1 or wv.ndim != 1 or ix.size != wv.size or ix.size != int(ip[-1]):
+        raise ValueError(f"{where}: indices and w must each hold indptr[n] entries")
+    nq = -1
+    if qu is not None or qv is not None:
+        if qu is None or qv is None:
+            raise ValueError(f"{where}: qu and qv come together")
+        qu = np.ascontiguousarray(qu, dtype=np.int32)
+        qv = np.ascontiguousarray(qv, dtype=np.int32)
+        if qu.ndim != 1 or qv.shape != qu.shape:
+            raise ValueError(f"{where}: qu and qv must be 1-D and of one length")
+        nq = qu.size
+    c = None if coords is None else np.ascontiguousarray(coords, dtype=np.float64)
+    dim = 0 if c is None else (c.shape[1] if c.ndim == 2 else 1)
+    if c is not None and (c.ndim > 2 or c.size != int(n) * dim):
+        raise ValueError(f"{where}: coords must be n x dim ({int(n)} x {dim})")
+    return ip, ix, wv, qu, qv, nq, c, dim
+
+
 class Symbolic:
     """Host plan: ordering, elimination tree, supernodes and query grouping."""
 
     def __init__(self, n, indptr, indices, w, ground=0, qu=None, qv=None, coords=None,
                  options: Options | None = None):
         lib = load()
-        self._keep = [np.ascontiguousarray(indptr, dtype=np.int64),
-                      np.ascontiguousarray(indices, dtype=np.int32),
-                      np.ascontiguousarray(w, dtype=np.float64)]
-        if qu is not None:
-            qu = np.ascontiguousarray(qu, dtype=np.int32)
-            qv = np.ascontiguousarray(qv, dtype=np.int32)
-            nq = qu.size
-        else:
-            nq = -1
-        c = None if coords is None else np.ascontiguousarray(coords, dtype=np.float64)
-        dim = 0 if c is None else (c.shape[1] if c.ndim == 2 else 1)
+        ip, ix, wv, qu, qv, nq, c, dim = _graph_args(n, indptr, indices, w, qu, qv, coords,
+                                                     "peers_analyze")
+        self._keep = [ip, ix, wv]
         h = ctypes.c_void_p()
         opt = ctypes.byref(options) if options is not None else None
         _check(lib.peers_analyze(None, int(n), _ptr(self._keep[0]), _ptr(self._keep[1]),
@@ -253,6 +273,7 @@ class Symbolic:
                                  _ptr(c), int(dim), opt, ctypes.byref(h)), "peers_analyze")
         self._h = h
         self.n = int(n)
+        self.nnz = int(ix.size)
         self.nq = int(lib.peers_num_queries(h))
 
     @classmethod
@@ -295,6 +316,9 @@ class Numeric:
         lib = load()
         self._ctx, self._sym = ctx, sym
         self._w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        if self._w is not None and (self._w.ndim != 1 or self._w.size != sym.nnz):
+            raise ValueError(f"peers_factor: w must hold one conductance per stored CSR entry "
+                             f"({sym.nnz})")
         h = ctypes.c_void_p()
         _check(lib.peers_factor(ctx._h, sym._h, _ptr(self._w), ctypes.byref(h)), "peers_factor")
         self._h = h
@@ -339,7 +363,23 @@ def sparsify(ctx: Context, w, R, u):
     """Alg. 1 on the device: w, R (m) and u (q uniforms) are float64 CUDA tensors; returns
     (count int64, weight float64) CUDA tensors of m entries."""
     import torch
-    m, q = int(w.numel()), int(u.numel())
+
+    def device_f64(t, name, n=None):
+        # the kernels read every entry through the raw pointer: a contiguous float64 CUDA
+        # tensor on the context's device, of the stated length
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda \
+                or not t.is_contiguous() or t.dim() != 1 or (n is not None and t.numel() != n):
+            raise ValueError(f"sparsify: {name} must be a contiguous 1-D float64 CUDA tensor"
+                             + ("" if n is None else f" of {n} entries"))
+        if t.device.index != ctx.device:
+            raise ValueError(f"sparsify: {name} is on cuda:{t.device.index}, the context on "
+                             f"cuda:{ctx.device}")
+
+    device_f64(w, "w")
+    m = int(w.numel())
+    device_f64(R, "R", m)
+    device_f64(u, "u")
+    q = int(u.numel())
     count = torch.empty(m, dtype=torch.int64, device=w.device)
     weight = torch.empty(m, dtype=torch.float64, device=w.device)
     _check(load().peers_sparsify(ctx._h, m, _ptr(w), _ptr(R), q, _ptr(u), _ptr(count),
@@ -451,20 +491,9 @@ class Server:
     def submit(self, g, qu=None, qv=None, ground: int = 0, use_coords: bool = True) -> int:
         """Queues a request (graph + queries; all edges when qu is None); returns its ticket.
         The library copies the arrays before returning."""
-        ip = np.ascontiguousarray(g.indptr, dtype=np.int64)
-        ix = np.ascontiguousarray(g.indices, dtype=np.int32)
-        w = np.ascontiguousarray(g.w, dtype=np.float64)
-        if qu is not None:
-            qu = np.ascontiguousarray(qu, dtype=np.int32)
-            qv = np.ascontiguousarray(qv, dtype=np.int32)
-            nq = qu.size
-        else:
-            nq = -1
-        c = None
-        dim = 0
-        if use_coords and g.coords is not None:
-            c = np.ascontiguousarray(g.coords, dtype=np.float64)
-            dim = c.shape[1]
+        ip, ix, w, qu, qv, nq, c, dim = _graph_args(
+            g.n, g.indptr, g.indices, g.w, qu, qv, g.coords if use_coords else None,
+            "peers_server_submit")
         t = ctypes.c_int64()
         _check(load().peers_server_submit(self._h, int(g.n), _ptr(ip), _ptr(ix), _ptr(w),
                                           int(ground), int(nq), _ptr(qu), _ptr(qv), _ptr(c), dim,

@@ -413,3 +413,33 @@ def test_walk_work_of_listed_pairs_matches_the_solve_pattern(P, name, g, ground)
             assert inf["walk_entries"] == _walk_entries_by_solve(g, ex, ground, qu, qv), \
                 (name, use_coords, opt is not None)
             sym.close()
+
+
+def test_binding_checks_buffer_sizes_before_the_library_reads_them(P):
+    """The library reads n + 1 offsets, indptr[n] indices and conductances, nq query pairs,
+    n x dim coordinates and (for a refactor) one conductance per stored entry through plain
+    pointers; the binding rejects arrays of other sizes before the call, and the
+    sparsifier's inputs unless they are float64 CUDA tensors (checked before any device
+    work, so this runs without a GPU)."""
+    import torch
+    g = I.grid2d(5, 6, seed=3)
+    with pytest.raises(ValueError):
+        P.Symbolic(g.n, g.indptr[:-1], g.indices, g.w)
+    with pytest.raises(ValueError):
+        P.Symbolic(g.n, g.indptr, g.indices[:-2], g.w[:-2])
+    with pytest.raises(ValueError):
+        P.Symbolic(g.n, g.indptr, g.indices, g.w[:-1])
+    with pytest.raises(ValueError):
+        P.Symbolic(g.n, g.indptr, g.indices, g.w, qu=np.array([0, 1]), qv=np.array([2]))
+    with pytest.raises(ValueError):
+        P.Symbolic(g.n, g.indptr, g.indices, g.w, coords=g.coords[:-1])
+    sym = P.Symbolic.of(g)
+    assert sym.nnz == g.indices.size
+    with pytest.raises(ValueError):
+        P.Numeric(None, sym, g.w[:-1])
+    sym.close()
+    w = torch.ones(4, dtype=torch.float64)
+    with pytest.raises(ValueError):   # host tensors
+        P.sparsify(None, w, w, w)
+    with pytest.raises(ValueError):
+        P.sparsify(None, np.ones(4), np.ones(4), np.ones(4))
